@@ -1,0 +1,176 @@
+"""Seeded synthetic graph inputs (edge lists of int32 vertex ids).
+
+Only inputs live here: nothing in this package orders, orients, sorts or
+intersects adjacency lists.  Both the GPU library and the CPU oracle consume
+these edge lists; neither imports the other.
+
+The heavy generators are C (``graphgen.c``, SplitMix64 counter-based
+randomness, deterministic for any thread count and host); ``families.py``
+holds the small closed-form graphs used by the oracle's pins.
+
+Named workloads (the paper evaluates on SNAP/DIMACS graphs, R-MAT Kronecker
+graphs, Barabasi-Albert and Watts-Strogatz networks, Table 1; those datasets
+are not available, so seeded synthetic graphs of the same families stand in):
+
+  er16k     Erdos-Renyi n=16384, m=131072 distinct edges
+  rmat20    R-MAT scale 20, 16,777,216 raw draws (a,b,c,d)=(.57,.19,.19,.05),
+            permuted ids, self-loops and duplicates kept in the input
+  rgg4m     random geometric graph, n=4,194,304, r=sqrt(32/(pi n))
+  rmat24    R-MAT scale 24, draws until 180,000,000 distinct edges
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "graphgen.c")
+_SO = os.path.join(_HERE, "_build", "libgraphgen.so")
+_lib = None
+_lock = threading.Lock()
+
+RMAT_ABC = (0.57, 0.19, 0.19)
+
+
+def build(force: bool = False) -> str:
+    """Compile libgraphgen.so with gcc (host code only, portable flags)."""
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp.%d" % os.getpid()
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-pthread",
+             "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_SO)
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            lib.gg_er.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, i32p, i32p]
+            lib.gg_er.restype = ctypes.c_int64
+            lib.gg_rmat.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_uint64, ctypes.c_int, i32p, i32p]
+            lib.gg_rmat.restype = ctypes.c_int
+            lib.gg_rmat_distinct.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                             i32p, i32p]
+            lib.gg_rmat_distinct.restype = ctypes.c_int64
+            lib.gg_rgg.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, i32p, i32p,
+                                   ctypes.c_int64]
+            lib.gg_rgg.restype = ctypes.c_int64
+            f64p = ctypes.POINTER(ctypes.c_double)
+            lib.gg_rgg_point_coords.argtypes = [ctypes.c_int32, ctypes.c_uint64, f64p, f64p]
+            lib.gg_rgg_point_coords.restype = None
+            lib.gg_rgg_permutation.argtypes = [ctypes.c_int32, ctypes.c_uint64, i32p]
+            lib.gg_rgg_permutation.restype = None
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def er(n: int, m: int, seed: int):
+    """G(n, m): m distinct non-loop undirected edges, each listed once."""
+    src = np.empty(m, np.int32)
+    dst = np.empty(m, np.int32)
+    rc = _load().gg_er(n, m, seed, _ptr(src), _ptr(dst))
+    if rc < 0:
+        raise ValueError("gg_er(n=%d, m=%d) failed: %d" % (n, m, rc))
+    return src, dst
+
+
+def rmat(scale: int, draws: int, seed: int, abc=RMAT_ABC, permute: bool = True):
+    """Raw R-MAT draws over 2**scale vertices (loops/duplicates kept)."""
+    src = np.empty(draws, np.int32)
+    dst = np.empty(draws, np.int32)
+    rc = _load().gg_rmat(scale, draws, abc[0], abc[1], abc[2], seed, int(permute),
+                         _ptr(src), _ptr(dst))
+    if rc < 0:
+        raise ValueError("gg_rmat failed: %d" % rc)
+    return src, dst
+
+
+def rmat_distinct(scale: int, m: int, seed: int, abc=RMAT_ABC):
+    """R-MAT draws until m distinct non-loop undirected edges; each once."""
+    src = np.empty(m, np.int32)
+    dst = np.empty(m, np.int32)
+    rc = _load().gg_rmat_distinct(scale, m, abc[0], abc[1], abc[2], seed, _ptr(src), _ptr(dst))
+    if rc < 0:
+        raise ValueError("gg_rmat_distinct failed: %d" % rc)
+    return src, dst
+
+
+def rgg_radius(n: int, mean_degree: float = 32.0) -> float:
+    """Radius giving the requested mean degree, r = sqrt(d / (pi n))."""
+    return math.sqrt(mean_degree / (math.pi * n))
+
+
+def rgg(n: int, r: float, seed: int):
+    """Random geometric graph on n uniform points of the unit square."""
+    expect = 0.5 * n * (n - 1) * math.pi * r * r
+    cap = int(expect * 1.05 + 6.0 * math.sqrt(expect + 1.0) + 1024)
+    while True:
+        src = np.empty(cap, np.int32)
+        dst = np.empty(cap, np.int32)
+        rc = _load().gg_rgg(n, r, seed, _ptr(src), _ptr(dst), cap)
+        if rc >= 0:
+            return src[:rc].copy(), dst[:rc].copy()
+        if rc <= -3:
+            cap = -rc - 3
+            continue
+        raise ValueError("gg_rgg failed: %d" % rc)
+
+
+def rgg_points(n: int, seed: int):
+    """(x, y, perm): the points of rgg(n, r, seed) and the id each one gets."""
+    x = np.empty(n, np.float64)
+    y = np.empty(n, np.float64)
+    perm = np.empty(n, np.int32)
+    lib = _load()
+    f64p = ctypes.POINTER(ctypes.c_double)
+    lib.gg_rgg_point_coords(n, seed, x.ctypes.data_as(f64p), y.ctypes.data_as(f64p))
+    lib.gg_rgg_permutation(n, seed, _ptr(perm))
+    return x, y, perm
+
+
+# name -> (description, builder)
+def _w_er16k():
+    return er(16384, 131072, 1001) + (16384,)
+
+
+def _w_rmat20():
+    return rmat(20, 16 * (1 << 20), 1002) + (1 << 20,)
+
+
+def _w_rgg4m():
+    n = 4194304
+    return rgg(n, rgg_radius(n), 1003) + (n,)
+
+
+def _w_rmat24():
+    return rmat_distinct(24, 180_000_000, 1004) + (1 << 24,)
+
+
+WORKLOADS = {
+    "er16k": ("Erdos-Renyi G(n=16384, m=131072), seed 1001", _w_er16k),
+    "rmat20": ("R-MAT scale 20, 16,777,216 raw draws, permuted ids, seed 1002", _w_rmat20),
+    "rgg4m": ("random geometric graph n=4,194,304, r=sqrt(32/(pi n)), seed 1003", _w_rgg4m),
+    "rmat24": ("R-MAT scale 24, draws until 180,000,000 distinct edges, seed 1004", _w_rmat24),
+}
+
+
+def workload(name: str):
+    """Return (src, dst, n) numpy int32 arrays for a named workload."""
+    return WORKLOADS[name][1]()

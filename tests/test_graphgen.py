@@ -1,0 +1,112 @@
+"""The seeded input generators: determinism and the family definitions."""
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import graphgen
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "workloads.json")
+
+
+def _canon(s, d):
+    a = np.minimum(s, d).astype(np.int64)
+    b = np.maximum(s, d).astype(np.int64)
+    return a << 32 | b
+
+
+def test_er_exact_m_no_loops():
+    s, d = graphgen.er(1000, 20000, 5)
+    assert len(s) == 20000
+    assert np.all(s != d)
+    assert len(np.unique(_canon(s, d))) == 20000
+    assert s.min() >= 0 and max(s.max(), d.max()) < 1000
+
+
+def test_er_complete_limit():
+    s, d = graphgen.er(20, 190, 9)
+    assert len(np.unique(_canon(s, d))) == 190
+    with pytest.raises(ValueError):
+        graphgen.er(20, 191, 9)
+
+
+def test_rmat_range_and_skew():
+    s, d = graphgen.rmat(12, 1 << 16, 3, permute=False)
+    assert s.min() >= 0 and max(s.max(), d.max()) < 4096
+    deg = np.bincount(np.concatenate([s, d]), minlength=4096)
+    # with a = 0.57 the all-zero-bits vertex is the heaviest
+    assert deg[0] == deg.max()
+
+
+def test_rmat_distinct():
+    s, d = graphgen.rmat_distinct(13, 50000, 4)
+    assert len(s) == 50000
+    assert np.all(s != d)
+    assert len(np.unique(_canon(s, d))) == 50000
+    raw_s, raw_d = graphgen.rmat(13, 60000, 4)
+    keep = raw_s != raw_d
+    # the output is the first-occurrence subsequence of the raw draw stream
+    key = _canon(raw_s[keep], raw_d[keep])
+    _, first = np.unique(key, return_index=True)
+    first = np.sort(first)[:50000]
+    assert np.array_equal(s, raw_s[keep][first]) and np.array_equal(d, raw_d[keep][first])
+
+
+def test_rgg_distance_rule():
+    n, seed = 3000, 11
+    r = graphgen.rgg_radius(n, 20.0)
+    s, d = graphgen.rgg(n, r, seed)
+    x, y, perm = graphgen.rgg_points(n, seed)
+    inv = np.empty(n, np.int64)
+    inv[perm] = np.arange(n)
+    # brute force over all pairs, same float64 expression
+    dx = x[:, None] - x[None, :]
+    dy = y[:, None] - y[None, :]
+    close = (dx * dx + dy * dy) < r * r
+    iu = np.triu_indices(n, 1)
+    sel = close[iu]
+    want = np.sort(_canon(perm[iu[0][sel]], perm[iu[1][sel]]))
+    got = np.sort(_canon(s, d))
+    assert np.array_equal(got, want)
+    assert len(np.unique(got)) == len(got)
+
+
+@pytest.mark.parametrize("threads", ["1", "3"])
+def test_thread_count_independent(threads):
+    code = ("import hashlib, graphgen as g\n"
+            "h = hashlib.sha256()\n"
+            "for a in (g.rmat(14, 300000, 5), g.rmat_distinct(14, 100000, 6), "
+            "g.rgg(20000, g.rgg_radius(20000), 7)):\n"
+            "    h.update(a[0].tobytes()); h.update(a[1].tobytes())\n"
+            "print(h.hexdigest())\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = []
+    for t in (threads, "8"):
+        env = dict(os.environ, GG_THREADS=t)
+        outs.append(subprocess.check_output([sys.executable, "-c", code], cwd=root, env=env))
+    assert outs[0] == outs[1]
+
+
+@pytest.mark.parametrize("name", ["er16k", "rmat20", "rgg4m"])
+def test_workload_hash_matches_golden(name):
+    """The stored input hashes pin the generator across hosts."""
+    with open(GOLDEN) as f:
+        gold = json.load(f)[name]
+    s, d, n = graphgen.workload(name)
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(s, "<i4").tobytes())
+    h.update(np.ascontiguousarray(d, "<i4").tobytes())
+    assert h.hexdigest() == gold["input_sha256"]
+    assert n == gold["n"] and len(s) == gold["m_in"]
+
+
+def test_rgg_mean_degree():
+    n = 200000
+    s, d = graphgen.rgg(n, graphgen.rgg_radius(n), 3)
+    mean = 2 * len(s) / n
+    assert 31.0 < mean < 32.0  # boundary effects lower it slightly below 32
