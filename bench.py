@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Throughput of exact triangle counting (forward algorithm) on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload rmat24|rmat20|rgg4m|er16k]
+
+One step = the whole path (validation, cleaning, degree-ordered orientation,
+two LSD radix sorts, node array, counting with per-vertex counts) over one
+graph whose edge array is already resident in HBM.  The default workload is
+the R-MAT graph of scale 24 with 180,000,000 distinct undirected edges
+(a=.57, b=.19, c=.19, d=.05, seed 1004), whose per-vertex counts feed the
+clustering coefficient and transitivity.  Its inputs (1.44 GB) and key
+buffers (2.9 GB) are far larger than the 126 MB L2, so no flush is needed
+between steps.
+
+Printed: one JSON line on rank 0.  `value` is input pairs per second over
+all ranks (each rank counts its own replica of the graph: the graph fits one
+GPU and the path needs no exchange, so N GPUs run N independent copies).
+`--impl reference` times the CPU oracle (the paper's own baseline is a
+single-threaded CPU forward algorithm, Sec. IV) on a bounded sample of the
+same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "input edges/s"
+UNIT = "edges/s"
+CPU_SAMPLE_PAIRS = 24_000_000      # cpu_baseline: first pairs of the workload
+REF_SAMPLE_PAIRS = 6_000_000       # reference arm: per step
+KERNEL_OF_PHASE = {"canon": "k_canon", "sort1": "k_radix_pass", "degree": "k_unique_degree",
+                   "orient": "k_orient", "sort2": "k_radix_pass", "offsets": "k_offsets",
+                   "count": "k_count"}
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="rmat24")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------- distributed
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg, dev=None):
+    if pg is not None:
+        if dev is not None:
+            pg.barrier(device_ids=[dev])
+        else:
+            pg.barrier()
+
+
+def max_over_ranks(pg, x: float, dev=None) -> float:
+    if pg is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dev is not None else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of this GPU's clocks and throttle reasons."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                if self.uuid and parts[0] != self.uuid:
+                    continue
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def gpu_uuid(dev) -> str | None:
+    try:
+        import torch
+
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------- roofline
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("preprocess.cu", "count.cu", "tc_common.cuh"):
+        with open(os.path.join(ROOT, "paper_1503_00576_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        data = json.load(f)
+    rec = data.get(workload, {}).get(kernel)
+    if not rec or rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def roofline(prof: dict, steps: int, m_in: int, m: int, n: int, workload: str) -> dict:
+    """Dominant kernel by device time; achieved = algorithmic bytes per
+    launch / average launch duration (CUDA events on the launch stream)."""
+    b = max(1, (max(n, 2) - 1).bit_length())
+    passes1, passes2 = (2 * b + 7) // 8, (b + 7) // 8
+    per_kernel = {}
+    for phase, (ms, launches) in prof.items():
+        k = KERNEL_OF_PHASE[phase]
+        a = per_kernel.setdefault(k, [0.0, 0])
+        a[0] += ms
+        a[1] += launches
+    kernel = max(per_kernel, key=lambda k: per_kernel[k][0])
+    ms_total, launches = per_kernel[kernel]
+    if kernel == "k_count":
+        # compulsory: the CSR read once (col 4m, offsets 4(n+1)) and t[] written once (8n)
+        bytes_per_launch = 4 * m + 4 * (n + 1) + 8 * n
+        how = "CSR read once (4m + 4(n+1)) + t written once (8n)"
+    elif kernel == "k_radix_pass":
+        total = passes1 * 16 * m_in + (passes2 - 1) * 16 * m + 12 * m
+        bytes_per_launch = total / (passes1 + passes2)
+        how = "8-byte key read + 8-byte key write per key per pass (last pass writes 4 bytes)"
+    else:
+        bytes_per_launch = 16 * m_in
+        how = "16 bytes per input pair"
+    per_launch_s = ms_total / 1e3 / max(launches, 1)
+    achieved = bytes_per_launch / per_launch_s / 1e9
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs")
+    src = "measured"
+    if not peak:
+        peak, src = 6800.0, "fallback"
+    return {"bound": "hbm", "kernel": kernel, "achieved": round(achieved, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": src,
+            "traffic": committed_traffic(kernel, workload),
+            "algorithmic_bytes_per_launch": int(bytes_per_launch), "bytes_rule": how,
+            "launches_timed": launches, "ms_per_launch": round(per_launch_s * 1e3, 4)}
+
+
+# ---------------------------------------------------------------- CPU oracle timing
+def time_oracle(src, dst, n, pairs: int) -> tuple[float, int]:
+    import oracle
+
+    pairs = min(pairs, len(src))
+    t0 = time.perf_counter()
+    oracle.forward(src[:pairs], dst[:pairs], n)
+    return time.perf_counter() - t0, pairs
+
+
+# ---------------------------------------------------------------- arms
+def run_reference(args, world, rank, pg):
+    import graphgen
+
+    if rank != 0:
+        return
+    src, dst, n = graphgen.workload(args.workload)
+    times = []
+    for i in range(args.warmup + args.steps):
+        dt, pairs = time_oracle(src, dst, n, REF_SAMPLE_PAIRS)
+        if i >= args.warmup:
+            times.append(dt)
+    mean = statistics.mean(times)
+    value = pairs / mean
+    sample = "first %d pairs of the %s edge array per step (oracle: single-threaded C " \
+             "forward algorithm)" % (pairs, args.workload)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": mean * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": graphgen.WORKLOADS[args.workload][0], "n": n,
+                       "m_in": int(len(src))},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local, pg):
+    import numpy as np
+    import torch
+
+    import graphgen
+    import paper_1503_00576_gb300 as tc
+
+    torch.cuda.set_device(local)
+    dev = local
+    tc.load_library()
+    t0 = time.time()
+    src, dst, n = graphgen.workload(args.workload)
+    log("rank %d: generated %s (%d pairs) in %.1fs" % (rank, args.workload, len(src),
+                                                      time.time() - t0))
+    m_in = len(src)
+    s = torch.from_numpy(src).cuda()
+    d = torch.from_numpy(dst).cuda()
+    t_out = torch.empty(n, dtype=torch.int64, device="cuda")
+    deg_out = torch.empty(n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return tc.tc_count_per_vertex(s, d, n, stream=stream, t_out=t_out, deg_out=deg_out)[0]
+
+    for _ in range(max(args.warmup, 3)):
+        T = step()
+    torch.cuda.synchronize()
+    m = int((deg_out.to(torch.int64).sum() // 2).item())
+
+    clocks = ClockSampler(gpu_uuid(dev))
+    tc.tc_profile_read(reset=True)
+    tc.tc_profile_enable(True)
+    launches0 = tc.tc_launch_count()
+    clocks.start()
+    time.sleep(0.4)  # let the sampler take a first reading
+    barrier(pg, dev)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        T2 = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg, dev)
+    clk = clocks.stop()
+    launches = tc.tc_launch_count() - launches0
+    tc.tc_profile_enable(False)
+    prof = tc.tc_profile_read(reset=True)
+    assert T2 == T, "count changed between steps"
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    elapsed = max_over_ranks(pg, elapsed, dev)
+    ms_per_step = elapsed / args.steps * 1e3
+    value = world * m_in * args.steps / elapsed
+
+    # end to end through the host-buffer entry point, pinned buffers
+    e2e = None
+    if not args.no_e2e:
+        hs = torch.from_numpy(src).pin_memory()
+        hd = torch.from_numpy(dst).pin_memory()
+        ht = torch.empty(n, dtype=torch.int64).pin_memory()
+        hdeg = torch.empty(n, dtype=torch.int32).pin_memory()
+        tc.tc_count_per_vertex_host(hs, hd, n, t_out=ht, deg_out=hdeg)  # warm
+        barrier(pg, dev)
+        times = []
+        for _ in range(args.e2e_steps):
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            Te, _, _ = tc.tc_count_per_vertex_host(hs, hd, n, t_out=ht, deg_out=hdeg)
+            times.append(time.perf_counter() - a)
+            assert Te == T
+        e2e_s = max_over_ranks(pg, statistics.mean(times), dev)
+        e2e = {"value": world * m_in / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * m_in,
+               "d2h_bytes_per_step": 12 * n + 128, "ms_per_step": e2e_s * 1e3,
+               "api": "tc_count_per_vertex_host (pinned host buffers)"}
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        dt, pairs = time_oracle(src, dst, n, CPU_SAMPLE_PAIRS)
+        cpu = {"value": pairs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "first %d pairs of the %s edge array (a uniform edge sample: the "
+                         "pairs are in random draw order), single-threaded C oracle, "
+                         "%.1f s" % (pairs, args.workload, dt)}
+    steps_ms = {k: round(v[0] / args.steps, 4) for k, v in prof.items()}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": graphgen.WORKLOADS[args.workload][0], "n": n, "m_in": m_in,
+                   "m_distinct": m, "triangles": T,
+                   "outputs": "T (uint64), t[n] (int64), deg[n] (int32)",
+                   "l2": "no flush: inputs %.2f GB and key buffers %.2f GB exceed L2"
+                         % (8 * m_in / 1e9, 16 * m_in / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roofline(prof, args.steps, m_in, m, n, args.workload),
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        "phase_ms_per_step": steps_ms,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local, pg = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank, pg)
+        else:
+            run_ours(args, world, rank, local, pg)
+    finally:
+        if pg is not None:
+            pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

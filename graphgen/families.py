@@ -22,7 +22,8 @@ def _out(pairs, n):
 
 def complete(n: int):
     """K_n."""
-    return _out(list(itertools.combinations(range(n), 2)), n)
+    iu = np.triu_indices(n, 1)
+    return iu[0].astype(np.int32), iu[1].astype(np.int32), n
 
 
 def complete_bipartite(a: int, b: int):

@@ -1,0 +1,168 @@
+/*
+ * tc.h -- exact triangle counting on GB300 (sm_103a): the C ABI.
+ *
+ * Method: the forward algorithm of A. Polak, "Counting Triangles in Large
+ * Graphs on GPU" (arXiv 1503.00576), Sec. II-B/II-C: order the vertices by
+ * (degree, id), keep each undirected edge only in the forward list N+(u) of
+ * its lower endpoint, sort every forward list, and add |N+(u) & N+(v)| for
+ * every forward edge (u, v).  Preprocessing follows Sec. III-B (sort the
+ * edges as 64-bit keys, build the node array, drop backward edges, unzip);
+ * counting follows Sec. III-C.  All arithmetic is exact integer.
+ *
+ * Input format (Sec. III-A, relaxed): an edge array given as two int32 arrays
+ * src[0..m) and dst[0..m), pair i being the edge {src[i], dst[i]}.  The paper
+ * assumes no self-loops, no repeated edges and every edge listed in both
+ * directions; this library accepts any pairs: each pair is undirected,
+ * self-loops are dropped and repeats (in either direction) collapse to one
+ * edge.  So the paper's format (each edge twice) and a list with each edge
+ * once give the same counts.  Vertex ids must satisfy 0 <= id < n.
+ *
+ * Memory: unless a function says "host", every pointer is a device pointer
+ * on the current CUDA device.  Inputs are read-only and caller-owned; outputs
+ * are caller-allocated.  Scratch space comes from the stream-ordered
+ * allocator (cudaMallocAsync on the given stream) and is released before the
+ * call returns, except in tc_count_ws, which uses the caller's workspace.
+ *
+ * Streams: `stream` is a cudaStream_t (0 = the legacy default stream).  All
+ * work is enqueued on it.  Every function that returns a host value
+ * synchronises that stream before returning.
+ *
+ * Errors: every call sets a thread-local status readable with
+ * tc_last_error(); tc_status_string() names it.  Limits: n <= 2^31 - 1,
+ * m <= 2^31 - 1 pairs (larger m gives TC_ERR_OVERFLOW).
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t, without pulling in the CUDA headers. */
+typedef struct CUstream_st *tc_stream_t;
+
+typedef enum tc_status {
+  TC_OK = 0,
+  TC_ERR_INVALID_ARG = 1, /* m < 0, n < 0, a required pointer is NULL, ws too small */
+  TC_ERR_ID_RANGE = 2,    /* some src[i] or dst[i] is outside [0, n) */
+  TC_ERR_OOM = 3,         /* the stream-ordered allocator failed */
+  TC_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed */
+  TC_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (never expected) */
+  TC_ERR_OVERFLOW = 6     /* m or n beyond the documented limits */
+} tc_status;
+
+/* Value tc_count returns on error (no graph within the limits has this many
+ * triangles: T < m^1.5 / 3 < 2^47). */
+#define TC_COUNT_ERROR UINT64_MAX
+
+/*
+ * Number of triangles T of the graph, by the forward algorithm (Sec. II-C:
+ * preprocessing of Sec. III-B, counting of Sec. III-C, reduction of the
+ * per-thread counts).
+ *   src, dst  device int32[m], read-only
+ *   m         number of pairs (>= 0; 0 gives T = 0)
+ *   n         number of vertices; every id must be < n
+ * Returns T, or TC_COUNT_ERROR with tc_last_error() set.  Synchronises.
+ */
+uint64_t tc_count(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
+                  tc_stream_t stream);
+
+/*
+ * Per-vertex triangle counts t(v) (the number of triangles containing v; the
+ * numerator of the local clustering coefficient, Sec. I) plus T and the
+ * degrees of the cleaned simple graph.
+ *   t_out      device int64[n], written (required when n > 0)
+ *   deg_out    device int32[n], written if not NULL
+ *   total_out  HOST uint64, written if not NULL (sum of t_out is 3T)
+ * Synchronises (the device-side error word is read back before return).
+ */
+tc_status tc_count_per_vertex(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
+                              tc_stream_t stream, int64_t *t_out, int32_t *deg_out,
+                              uint64_t *total_out);
+
+/*
+ * Local clustering coefficients and the transitivity ratio from per-vertex
+ * counts and degrees (Sec. I names both as the reason to count triangles):
+ *   cc(v) = 2 t(v) / (deg(v) (deg(v) - 1)) in float64, 0 where deg(v) < 2
+ *   transitivity = 3T / sum_v deg(v)(deg(v)-1)/2, T = sum_v t(v) / 3, with
+ *                  both integers exact and one float64 division; 0 if the
+ *                  denominator is 0.
+ *   t, deg            device int64[n], int32[n] (as written by
+ *                     tc_count_per_vertex)
+ *   cc_out            device float64[n], written if not NULL
+ *   transitivity_out  HOST double, written if not NULL (synchronises)
+ */
+tc_status tc_clustering(const int64_t *t, const int32_t *deg, int32_t n, tc_stream_t stream,
+                        double *cc_out, double *transitivity_out);
+
+/*
+ * Host-buffer variants: the same computations as tc_count /
+ * tc_count_per_vertex with inputs and outputs in HOST memory.  The copies
+ * are part of the call: the edge array is copied to the device, counted on
+ * a stream private to the calling thread, and the results are copied back
+ * before return (the paper's end-to-end timing, Sec. IV, covers the same
+ * span).  Page-locked host buffers transfer fastest; pageable ones work.
+ * Both synchronise.
+ *   src_host, dst_host  host int32[m]
+ *   t_host              host int64[n] (required when n > 0)
+ *   deg_host            host int32[n] or NULL
+ */
+tc_status tc_count_host(const int32_t *src_host, const int32_t *dst_host, int64_t m, int32_t n,
+                        uint64_t *total_out);
+tc_status tc_count_per_vertex_host(const int32_t *src_host, const int32_t *dst_host, int64_t m,
+                                   int32_t n, int64_t *t_host, int32_t *deg_host,
+                                   uint64_t *total_out);
+
+/*
+ * Caller-provided workspace.  tc_workspace_bytes(m, n) is the size that
+ * tc_count_ws needs for an input of m pairs and n vertices (0 on bad
+ * arguments); ws must be a device allocation of at least that many bytes,
+ * 256-byte aligned.  tc_count_ws allocates nothing and otherwise behaves
+ * like tc_count, writing T to the HOST uint64 *total_out.  Calls sharing a
+ * workspace must be ordered (same stream, or synchronised).
+ */
+size_t tc_workspace_bytes(int64_t m, int32_t n);
+tc_status tc_count_ws(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
+                      tc_stream_t stream, void *ws, size_t ws_bytes, uint64_t *total_out);
+
+/* Status of the calling thread's most recent call, and its name. */
+tc_status tc_last_error(void);
+const char *tc_status_string(tc_status status);
+/* Human-readable detail of the last error of this thread ("" if none). */
+const char *tc_last_error_detail(void);
+
+/*
+ * Instrumentation.
+ *   tc_launch_count     number of kernels this library has launched in this
+ *                       process (monotonic).
+ *   tc_profile_enable   1: record CUDA events around every phase of every
+ *                       subsequent call (on the call's stream); 0: stop.
+ *   tc_profile_read     copies the accumulated per-phase device time in ms
+ *                       and launch counts since the last reset into
+ *                       ms_out[0..TC_NUM_PHASES) / launches_out (either may
+ *                       be NULL); reset != 0 clears them.
+ *   tc_phase_name       name of phase i.
+ */
+enum {
+  TC_PHASE_CANON = 0,   /* validate ids, drop loops, 64-bit keys, digit histograms */
+  TC_PHASE_SORT1 = 1,   /* LSD radix sort of the undirected keys */
+  TC_PHASE_DEGREE = 2,  /* drop repeats, degree histogram */
+  TC_PHASE_ORIENT = 3,  /* compact + orient by (degree, id) + out-degree */
+  TC_PHASE_SORT2 = 4,   /* LSD radix sort by owner, unzip to the column array */
+  TC_PHASE_OFFSETS = 5, /* node array by exclusive scan, row lists */
+  TC_PHASE_COUNT = 6,   /* intersections and reductions */
+  TC_NUM_PHASES = 7
+};
+uint64_t tc_launch_count(void);
+void tc_profile_enable(int on);
+void tc_profile_read(double *ms_out, uint64_t *launches_out, int reset);
+const char *tc_phase_name(int phase);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TC_H */

@@ -1,0 +1,286 @@
+"""Exact triangle counting on GB300 (sm_103a): Python binding of libtc.
+
+The forward algorithm of A. Polak, "Counting Triangles in Large Graphs on
+GPU" (arXiv 1503.00576): every step runs in the CUDA kernels of libtc.so
+behind the C ABI of ``include/tc.h``; this module only marshals arguments
+(torch tensors for device memory and streams, numpy arrays for host
+buffers).  There is no CPU fallback: if the library is missing or no GPU is
+present, calls raise.
+
+Functions mirror the C ABI names:
+
+    tc_count(src, dst, n)                  -> T
+    tc_count_per_vertex(src, dst, n)       -> (T, t int64[n], deg int32[n])
+    tc_clustering(t, deg)                  -> (cc float64[n], transitivity)
+    tc_count_host(src, dst, n)             -> T          (numpy in, host copies timed inside)
+    tc_count_per_vertex_host(src, dst, n)  -> (T, t, deg) (numpy in and out)
+    tc_workspace_bytes(m, n), tc_count_ws(src, dst, n, ws)
+    tc_launch_count(), tc_profile_enable(on), tc_profile_read(reset)
+
+``src`` / ``dst`` are int32 CUDA tensors of the same length (pair i is the
+undirected edge {src[i], dst[i]}); ``n`` is the vertex count.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtc.so")
+
+TC_OK = 0
+TC_ERR_INVALID_ARG = 1
+TC_ERR_ID_RANGE = 2
+TC_ERR_OOM = 3
+TC_ERR_CUDA = 4
+TC_ERR_TIMEOUT = 5
+TC_ERR_OVERFLOW = 6
+TC_COUNT_ERROR = (1 << 64) - 1
+PHASES = ("canon", "sort1", "degree", "orient", "sort2", "offsets", "count")
+
+# Every symbol include/tc.h declares.
+EXPORTS = ("tc_count", "tc_count_per_vertex", "tc_clustering", "tc_count_host",
+           "tc_count_per_vertex_host", "tc_workspace_bytes", "tc_count_ws", "tc_last_error",
+           "tc_status_string", "tc_last_error_detail", "tc_launch_count", "tc_profile_enable",
+           "tc_profile_read", "tc_phase_name")
+
+
+class TCError(RuntimeError):
+    """A libtc call returned an error status."""
+
+    def __init__(self, code: int, detail: str):
+        super().__init__("libtc: %s (%d)%s" % (_status_name(code), code,
+                                              ": " + detail if detail else ""))
+        self.code = code
+        self.detail = detail
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def _bind(lib):
+    c = ctypes
+    vp, i64, i32, u64, sz = c.c_void_p, c.c_int64, c.c_int32, c.c_uint64, c.c_size_t
+    sig = {
+        "tc_count": ([vp, vp, i64, i32, vp], u64),
+        "tc_count_per_vertex": ([vp, vp, i64, i32, vp, vp, vp, c.POINTER(u64)], c.c_int),
+        "tc_clustering": ([vp, vp, i32, vp, vp, c.POINTER(c.c_double)], c.c_int),
+        "tc_count_host": ([vp, vp, i64, i32, c.POINTER(u64)], c.c_int),
+        "tc_count_per_vertex_host": ([vp, vp, i64, i32, vp, vp, c.POINTER(u64)], c.c_int),
+        "tc_workspace_bytes": ([i64, i32], sz),
+        "tc_count_ws": ([vp, vp, i64, i32, vp, vp, sz, c.POINTER(u64)], c.c_int),
+        "tc_last_error": ([], c.c_int),
+        "tc_status_string": ([c.c_int], c.c_char_p),
+        "tc_last_error_detail": ([], c.c_char_p),
+        "tc_launch_count": ([], u64),
+        "tc_profile_enable": ([c.c_int], None),
+        "tc_profile_read": ([c.POINTER(c.c_double), c.POINTER(u64), c.c_int], None),
+        "tc_phase_name": ([c.c_int], c.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libtc.so (build it with ``python -m paper_1503_00576_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(
+                    "libtc.so not found at %s: build it with "
+                    "`python -m paper_1503_00576_gb300.build` (nvcc, sm_103a). "
+                    "There is no CPU fallback." % path)
+            _lib = _bind(ctypes.CDLL(path))
+    return _lib
+
+
+def _status_name(code: int) -> str:
+    names = {0: "ok", 1: "invalid argument", 2: "vertex id out of range", 3: "out of device memory",
+             4: "CUDA error", 5: "device wait timed out", 6: "size beyond limits"}
+    return names.get(code, "unknown status")
+
+
+def _check(code: int):
+    if code != TC_OK:
+        raise TCError(code, load_library().tc_last_error_detail().decode())
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream_of(stream, device):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _edges(src, dst):
+    torch = _torch()
+    for name, x in (("src", src), ("dst", dst)):
+        if not isinstance(x, torch.Tensor) or not x.is_cuda:
+            raise TypeError("%s must be a CUDA tensor" % name)
+        if x.dtype != torch.int32:
+            raise TypeError("%s must be int32, got %s" % (name, x.dtype))
+        if x.dim() != 1 or not x.is_contiguous():
+            raise TypeError("%s must be 1-D and contiguous" % name)
+    if src.numel() != dst.numel():
+        raise ValueError("src and dst differ in length")
+    if src.device != dst.device:
+        raise ValueError("src and dst are on different devices")
+    return src.device
+
+
+def tc_count(src, dst, n: int, stream=None) -> int:
+    """Triangle count T (uint64) of the graph given by the pairs (src[i], dst[i])."""
+    torch = _torch()
+    dev = _edges(src, dst)
+    lib = load_library()
+    with torch.cuda.device(dev):
+        T = lib.tc_count(src.data_ptr(), dst.data_ptr(), src.numel(), n, _stream_of(stream, dev))
+    if T == TC_COUNT_ERROR:
+        _check(lib.tc_last_error())
+    return int(T)
+
+
+def tc_count_per_vertex(src, dst, n: int, stream=None, t_out=None, deg_out=None):
+    """(T, t, deg): t[v] = triangles containing v (int64), deg[v] = degree of
+    v in the simple graph (int32), both device tensors of length n."""
+    torch = _torch()
+    dev = _edges(src, dst)
+    t = t_out if t_out is not None else torch.empty(n, dtype=torch.int64, device=dev)
+    deg = deg_out if deg_out is not None else torch.empty(n, dtype=torch.int32, device=dev)
+    if t.dtype != torch.int64 or t.numel() != n or deg.dtype != torch.int32 or deg.numel() != n:
+        raise TypeError("t_out must be int64[n] and deg_out int32[n]")
+    total = ctypes.c_uint64(0)
+    lib = load_library()
+    with torch.cuda.device(dev):
+        rc = lib.tc_count_per_vertex(src.data_ptr(), dst.data_ptr(), src.numel(), n,
+                                     _stream_of(stream, dev), t.data_ptr(), deg.data_ptr(),
+                                     ctypes.byref(total))
+    _check(rc)
+    return int(total.value), t, deg
+
+
+def tc_clustering(t, deg, stream=None, want_cc: bool = True):
+    """(cc, transitivity): local clustering coefficients (float64 device
+    tensor, or None) and the transitivity ratio (float)."""
+    torch = _torch()
+    if t.dtype != torch.int64 or deg.dtype != torch.int32 or t.numel() != deg.numel():
+        raise TypeError("t must be int64[n] and deg int32[n]")
+    n = t.numel()
+    cc = torch.empty(n, dtype=torch.float64, device=t.device) if want_cc else None
+    tr = ctypes.c_double(0.0)
+    lib = load_library()
+    with torch.cuda.device(t.device):
+        rc = lib.tc_clustering(t.data_ptr(), deg.data_ptr(), n, _stream_of(stream, t.device),
+                               cc.data_ptr() if cc is not None else None, ctypes.byref(tr))
+    _check(rc)
+    return cc, float(tr.value)
+
+
+def _host_i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a
+
+
+def tc_count_host(src, dst, n: int) -> int:
+    """T from HOST arrays (numpy int32 or pinned CPU tensors); the copies to
+    and from the device are part of the call."""
+    s, d = _host_ptrs(src, dst)
+    total = ctypes.c_uint64(0)
+    _check(load_library().tc_count_host(s[1], d[1], s[2], n, ctypes.byref(total)))
+    return int(total.value)
+
+
+def tc_count_per_vertex_host(src, dst, n: int, t_out=None, deg_out=None):
+    """(T, t, deg) from and into HOST buffers (numpy arrays or CPU tensors)."""
+    s, d = _host_ptrs(src, dst)
+    t = t_out if t_out is not None else np.empty(n, np.int64)
+    deg = deg_out if deg_out is not None else np.empty(n, np.int32)
+    total = ctypes.c_uint64(0)
+    _check(load_library().tc_count_per_vertex_host(s[1], d[1], s[2], n, _host_ptr(t, 8),
+                                                   _host_ptr(deg, 4), ctypes.byref(total)))
+    return int(total.value), t, deg
+
+
+def _host_ptr(x, itemsize):
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous or x.itemsize != itemsize:
+            raise TypeError("host buffer must be contiguous with %d-byte items" % itemsize)
+        return x.ctypes.data
+    torch = _torch()
+    if isinstance(x, torch.Tensor) and not x.is_cuda and x.is_contiguous() \
+            and x.element_size() == itemsize:
+        return x.data_ptr()
+    raise TypeError("expected a numpy array or a contiguous CPU tensor")
+
+
+def _host_ptrs(src, dst):
+    out = []
+    for x in (src, dst):
+        if isinstance(x, np.ndarray):
+            if x.dtype != np.int32 or not x.flags.c_contiguous:
+                raise TypeError("host edge arrays must be contiguous int32")
+            out.append((x, x.ctypes.data, len(x)))
+        else:
+            torch = _torch()
+            if not isinstance(x, torch.Tensor) or x.is_cuda or x.dtype != torch.int32 \
+                    or not x.is_contiguous():
+                raise TypeError("host edge arrays must be contiguous int32 CPU tensors")
+            out.append((x, x.data_ptr(), x.numel()))
+    if out[0][2] != out[1][2]:
+        raise ValueError("src and dst differ in length")
+    return out
+
+
+def tc_workspace_bytes(m: int, n: int) -> int:
+    return int(load_library().tc_workspace_bytes(m, n))
+
+
+def tc_count_ws(src, dst, n: int, ws, stream=None) -> int:
+    """T using the caller's workspace ``ws`` (a CUDA uint8 tensor of at least
+    tc_workspace_bytes(m, n) bytes); libtc allocates nothing."""
+    torch = _torch()
+    dev = _edges(src, dst)
+    total = ctypes.c_uint64(0)
+    lib = load_library()
+    with torch.cuda.device(dev):
+        rc = lib.tc_count_ws(src.data_ptr(), dst.data_ptr(), src.numel(), n,
+                             _stream_of(stream, dev), ws.data_ptr(),
+                             ws.numel() * ws.element_size(), ctypes.byref(total))
+    _check(rc)
+    return int(total.value)
+
+
+def tc_launch_count() -> int:
+    return int(load_library().tc_launch_count())
+
+
+def tc_profile_enable(on: bool = True) -> None:
+    load_library().tc_profile_enable(1 if on else 0)
+
+
+def tc_profile_read(reset: bool = False) -> dict:
+    """{phase: (ms, launches)} accumulated since the last reset."""
+    ms = (ctypes.c_double * len(PHASES))()
+    nl = (ctypes.c_uint64 * len(PHASES))()
+    load_library().tc_profile_read(ms, nl, 1 if reset else 0)
+    return {p: (float(ms[i]), int(nl[i])) for i, p in enumerate(PHASES)}
+
+
+# short aliases
+count = tc_count
+count_per_vertex = tc_count_per_vertex
+clustering = tc_clustering

@@ -1,0 +1,496 @@
+// preprocess.cu -- preprocessing of the forward algorithm on sm_103a.
+//
+// Sec. III-B of the paper builds, from an edge array, the sorted forward
+// adjacency lists: sort the edges (as 64-bit integers, Sec. III-D), build the
+// node array, mark and remove backward edges, unzip, rebuild the node array.
+// Here the same result is reached in this order, each step one kernel:
+//
+//   canon          validate ids (Sec. III-B computes n = max id + 1; here n
+//                  is given and any id >= n is an error), drop self-loops,
+//                  write the undirected key min(u,v) << b | max(u,v) with
+//                  b = bits of n, and histogram every 8-bit digit of every
+//                  key for all radix passes at once.
+//   radix pass     one stable LSD pass (onesweep: local ranking by warp
+//                  multisplit, decoupled look-back across tiles for the
+//                  global digit offsets, shared-memory staging so that the
+//                  scatter writes runs of equal digits contiguously).
+//   unique+degree  after sort 1, equal keys are adjacent: the first of each
+//                  run is a distinct edge; degree histogram of those.
+//   orient         compact the distinct edges (tile scan + look-back) and
+//                  emit each as owner << b | neighbour, the owner being the
+//                  endpoint lower in (degree, id) order -- marking and
+//                  removing backward edges of Sec. III-B in one pass; also
+//                  the out-degree histogram and the digit histograms of the
+//                  owner field.
+//   radix passes   stable LSD passes over the owner bits only.  Sort 1 left
+//                  the keys ordered by (min, max); every entry of a forward
+//                  list that came from a flipped edge has a smaller id than
+//                  the owner and precedes, in that order, all entries of the
+//                  owner's own run, so a stable sort by owner alone leaves
+//                  each list sorted by neighbour id.  The last pass writes
+//                  only the neighbour (the column array: the "unzip").
+//   offsets        exclusive scan of the out-degrees = node array (CSR
+//                  offsets); rows with >= 2 entries are binned for counting
+//                  (a row with one entry cannot close a triangle).
+#include <cstdio>
+
+#include "tc_common.cuh"
+
+namespace tc {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p) {
+  return *(const volatile unsigned long long *)p;
+}
+__device__ __forceinline__ void st_volatile_u64(unsigned long long *p, unsigned long long v) {
+  *(volatile unsigned long long *)p = v;
+}
+
+// Exclusive scan of one uint32 per thread over the first 256 threads of the
+// block; returns the thread's exclusive prefix, *total gets the sum.  All
+// threads of the block must call it.  `scratch` holds >= 8 words.
+__device__ __forceinline__ uint32_t scan256_exclusive(uint32_t v, uint32_t *scratch,
+                                                      uint32_t *total) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t x = (tid < 256) ? v : 0u;
+  uint32_t incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  __syncthreads();
+  if (tid < 256 && lane == 31) scratch[warp] = incl;
+  __syncthreads();
+  uint32_t before = 0, all = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    uint32_t s = scratch[w];
+    if (w < warp) before += s;
+    all += s;
+  }
+  *total = all;
+  return before + incl - x;
+}
+
+// Generic block exclusive scan of one uint32 per thread (any block size that
+// is a multiple of 32, up to 1024).  scratch holds >= 32 words.
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_scan_exclusive(uint32_t x, uint32_t *scratch,
+                                                         uint32_t *total) {
+  constexpr int WARPS = THREADS / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  __syncthreads();
+  if (lane == 31) scratch[warp] = incl;
+  __syncthreads();
+  uint32_t before = 0, all = 0;
+#pragma unroll
+  for (int w = 0; w < WARPS; ++w) {
+    uint32_t s = scratch[w];
+    if (w < warp) before += s;
+    all += s;
+  }
+  *total = all;
+  return before + incl - x;
+}
+
+// Decoupled look-back for one running sum (one thread).  Publishes the
+// tile's aggregate, walks back to the nearest inclusive prefix, publishes
+// its own inclusive prefix and returns the exclusive prefix.
+__device__ uint64_t lookback_single(unsigned long long *status, uint32_t tile, uint64_t agg,
+                                    Ctrl *ctrl) {
+  if (tile == 0) {
+    st_volatile_u64(&status[0], kFlagInclusive | agg);
+    return 0;
+  }
+  st_volatile_u64(&status[tile], kFlagAggregate | agg);
+  uint64_t excl = 0;
+  int64_t j = (int64_t)tile - 1;
+  uint32_t spins = 0;
+  while (j >= 0) {
+    unsigned long long s = ld_volatile_u64(&status[j]);
+    unsigned long long flag = s & ~kValueMask;
+    if (flag == 0) {
+      if (++spins > kSpinLimit) {
+        atomicOr(&ctrl->err, kErrTimeout);
+        break;
+      }
+      if (spins > 64) __nanosleep(64);
+      continue;
+    }
+    excl += s & kValueMask;
+    if (flag == kFlagInclusive) break;
+    --j;
+  }
+  st_volatile_u64(&status[tile], kFlagInclusive | (excl + agg));
+  return excl;
+}
+
+// ---------------------------------------------------------------------------
+// canon: validate, drop loops, undirected 64-bit keys, digit histograms
+// ---------------------------------------------------------------------------
+constexpr int kCanonThreads = 256;
+
+__global__ void __launch_bounds__(kCanonThreads)
+k_canon(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, uint32_t m_in,
+        int32_t n, int b, int passes, uint64_t *__restrict__ keys, uint32_t *__restrict__ hist,
+        Ctrl *ctrl) {
+  __shared__ uint32_t sh[kMaxSort1Passes * 256];
+  for (int i = threadIdx.x; i < passes * 256; i += kCanonThreads) sh[i] = 0;
+  __syncthreads();
+  const uint64_t sentinel = (1ull << (2 * b)) - 1;  // > every valid key; 2b <= 62
+  bool bad = false;
+  const uint32_t stride = gridDim.x * kCanonThreads;
+  for (uint32_t i = blockIdx.x * kCanonThreads + threadIdx.x; i < m_in; i += stride) {
+    const int32_t u = __ldg(src + i), v = __ldg(dst + i);
+    uint64_t key;
+    if ((uint32_t)u >= (uint32_t)n || (uint32_t)v >= (uint32_t)n) {
+      bad = true;
+      key = sentinel;
+    } else if (u == v) {
+      key = sentinel;  // self-loop: sorts last, dropped with the sentinels
+    } else {
+      const uint32_t lo = (uint32_t)min(u, v), hi = (uint32_t)max(u, v);
+      key = ((uint64_t)lo << b) | hi;
+    }
+    keys[i] = key;
+    for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * 256 + ((key >> (8 * p)) & 255)], 1u);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctrl->err, kErrIdRange);
+  for (int i = threadIdx.x; i < passes * 256; i += kCanonThreads)
+    if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// ---------------------------------------------------------------------------
+// one LSD radix pass (8-bit digit at `shift`), onesweep style
+// ---------------------------------------------------------------------------
+template <bool OUT_COL>
+__global__ void __launch_bounds__(kSortThreads)
+k_radix_pass(const uint64_t *__restrict__ in, void *__restrict__ out, uint32_t n_keys_bound,
+             const uint32_t *__restrict__ n_keys_dev, int shift, uint32_t col_mask,
+             const uint32_t *__restrict__ hist, unsigned long long *__restrict__ status,
+             uint32_t *ticket, Ctrl *ctrl) {
+  constexpr int WARPS = kSortThreads / 32, KPT = kSortKeysPerThread, TILE = kSortTile;
+  __shared__ uint64_t s_keys[TILE];
+  __shared__ uint32_t s_whist[WARPS][256];
+  __shared__ uint32_t s_tile_start[256];
+  __shared__ uint32_t s_gbase[256];
+  __shared__ uint32_t s_scratch[32];
+  __shared__ uint32_t s_tile;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t n_keys = n_keys_dev ? *n_keys_dev : n_keys_bound;
+  if (tid == 0) s_tile = atomicAdd(ticket, 1u);
+  for (int i = tid; i < WARPS * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0;
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint32_t tile_base = tile * (uint32_t)TILE;
+  if (tile_base >= n_keys) return;  // uniform for the block
+
+  // global start of every digit: exclusive scan of the pass histogram
+  uint32_t dummy;
+  const uint32_t gofs = scan256_exclusive(hist[tid], s_scratch, &dummy);
+
+  // ---- rank keys within the tile (stable: warp-major, round-major, lane) ----
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  uint64_t k[KPT];
+  uint32_t rk[KPT];
+#pragma unroll
+  for (int i = 0; i < KPT; ++i) {
+    const uint32_t idx = tile_base + (uint32_t)(warp * 32 * KPT + i * 32 + lane);
+    const bool valid = idx < n_keys;
+    k[i] = valid ? __ldg(in + idx) : 0ull;
+    const uint32_t d = (uint32_t)(k[i] >> shift) & 255u;
+    uint32_t peers = __ballot_sync(kFull, valid);
+#pragma unroll
+    for (int bit = 0; bit < 8; ++bit) {
+      const uint32_t bb = __ballot_sync(kFull, (d >> bit) & 1u);
+      peers &= ((d >> bit) & 1u) ? bb : ~bb;
+    }
+    const uint32_t before = s_whist[warp][d];
+    rk[i] = before + __popc(peers & lt_mask);
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) s_whist[warp][d] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+
+  // ---- per digit: warp offsets, tile offsets, global offsets ----
+  uint32_t tile_cnt = 0;
+  {
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) {
+      const uint32_t c = s_whist[w][tid];
+      s_whist[w][tid] = run;
+      run += c;
+    }
+    tile_cnt = run;
+  }
+  uint32_t tile_total;
+  const uint32_t tstart = scan256_exclusive(tile_cnt, s_scratch, &tile_total);
+  s_tile_start[tid] = tstart;
+  {
+    // decoupled look-back for this digit
+    unsigned long long *st = status + (size_t)tile * 256 + tid;
+    uint64_t excl = 0;
+    if (tile == 0) {
+      st_volatile_u64(st, kFlagInclusive | tile_cnt);
+    } else {
+      st_volatile_u64(st, kFlagAggregate | tile_cnt);
+      int64_t j = (int64_t)tile - 1;
+      uint32_t spins = 0;
+      while (j >= 0) {
+        const unsigned long long s = ld_volatile_u64(status + (size_t)j * 256 + tid);
+        const unsigned long long flag = s & ~kValueMask;
+        if (flag == 0) {
+          if (++spins > kSpinLimit) {
+            atomicOr(&ctrl->err, kErrTimeout);
+            break;
+          }
+          if (spins > 64) __nanosleep(64);
+          continue;
+        }
+        excl += s & kValueMask;
+        if (flag == kFlagInclusive) break;
+        --j;
+      }
+      st_volatile_u64(st, kFlagInclusive | (excl + tile_cnt));
+    }
+    // output position of the tile-local sorted index i with digit d is
+    // s_gbase[d] + i (mod 2^32 arithmetic; the result is < 2^31)
+    s_gbase[tid] = gofs + (uint32_t)excl - tstart;
+  }
+  __syncthreads();
+
+  // ---- stage in shared memory, sorted by digit ----
+#pragma unroll
+  for (int i = 0; i < KPT; ++i) {
+    const uint32_t idx = tile_base + (uint32_t)(warp * 32 * KPT + i * 32 + lane);
+    if (idx < n_keys) {
+      const uint32_t d = (uint32_t)(k[i] >> shift) & 255u;
+      s_keys[s_tile_start[d] + s_whist[warp][d] + rk[i]] = k[i];
+    }
+  }
+  __syncthreads();
+
+  // ---- scatter: consecutive threads write consecutive positions of a run ----
+  const uint32_t tile_n = min((uint32_t)TILE, n_keys - tile_base);
+  for (uint32_t i = tid; i < tile_n; i += kSortThreads) {
+    const uint64_t key = s_keys[i];
+    const uint32_t pos = s_gbase[(uint32_t)(key >> shift) & 255u] + i;
+    if (OUT_COL)
+      ((uint32_t *)out)[pos] = (uint32_t)key & col_mask;
+    else
+      ((uint64_t *)out)[pos] = key;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// distinct edges after sort 1 and their degree histogram
+// ---------------------------------------------------------------------------
+constexpr int kDegThreads = 256;
+
+__global__ void __launch_bounds__(kDegThreads)
+k_unique_degree(const uint64_t *__restrict__ keys, uint32_t m_in, int b, int32_t *deg) {
+  const uint64_t sentinel = (1ull << (2 * b)) - 1;
+  const uint64_t mask = (1ull << b) - 1;
+  const uint32_t stride = gridDim.x * kDegThreads;
+  for (uint32_t i = blockIdx.x * kDegThreads + threadIdx.x; i < m_in; i += stride) {
+    const uint64_t key = __ldg(keys + i);
+    if (key == sentinel) continue;
+    if (i > 0 && __ldg(keys + i - 1) == key) continue;
+    atomicAdd(&deg[(uint32_t)(key >> b)], 1);
+    atomicAdd(&deg[(uint32_t)(key & mask)], 1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// orient: compact distinct edges, orient by (degree, id), out-degrees
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kOrientThreads)
+k_orient(const uint64_t *__restrict__ keys, uint32_t m_in, int b,
+         const int32_t *__restrict__ deg, uint64_t *__restrict__ okeys, int32_t *outdeg,
+         uint32_t *__restrict__ hist2, int passes2, unsigned long long *status, Ctrl *ctrl) {
+  constexpr int KPT = kOrientKeysPerThread, TILE = kOrientTile;
+  __shared__ uint32_t s_scratch[32];
+  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_excl;
+  __shared__ uint32_t s_hist[kMaxSort2Passes * 256];
+  const int tid = threadIdx.x;
+  if (tid == 0) s_tile = atomicAdd(&ctrl->tile_ticket[kTicketOrient], 1u);
+  for (int i = tid; i < passes2 * 256; i += kOrientThreads) s_hist[i] = 0;
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint32_t tile_base = tile * (uint32_t)TILE;
+  if (tile_base >= m_in) return;
+  const uint64_t sentinel = (1ull << (2 * b)) - 1;
+  const uint64_t mask = (1ull << b) - 1;
+
+  const uint32_t first = tile_base + (uint32_t)tid * KPT;
+  uint64_t k[KPT];
+  uint32_t flags = 0, cnt = 0;
+  uint64_t prev = (first > 0 && first <= m_in) ? __ldg(keys + first - 1) : sentinel;
+  if (first == 0) prev = ~0ull;  // differs from every key
+#pragma unroll
+  for (int i = 0; i < KPT; ++i) {
+    const uint32_t idx = first + i;
+    k[i] = idx < m_in ? __ldg(keys + idx) : sentinel;
+    const bool keep = k[i] != sentinel && k[i] != prev;
+    prev = k[i];
+    flags |= (uint32_t)keep << i;
+    cnt += keep;
+  }
+  uint32_t tile_cnt;
+  const uint32_t toff = block_scan_exclusive<kOrientThreads>(cnt, s_scratch, &tile_cnt);
+  if (tid == 0) {
+    const uint64_t excl = lookback_single(status, tile, tile_cnt, ctrl);
+    s_excl = (uint32_t)excl;
+    if (tile_base + TILE >= m_in) ctrl->m = (uint32_t)(excl + tile_cnt);  // last tile
+  }
+  __syncthreads();
+  uint32_t pos = s_excl + toff;
+#pragma unroll
+  for (int i = 0; i < KPT; ++i) {
+    if (!((flags >> i) & 1u)) continue;
+    const uint32_t a = (uint32_t)(k[i] >> b), c = (uint32_t)(k[i] & mask);
+    const int32_t da = __ldg(deg + a), dc = __ldg(deg + c);
+    // a < c always (canonical key); so on equal degree the lower id owns
+    const bool a_first = (da < dc) || (da == dc);
+    const uint32_t owner = a_first ? a : c, nbr = a_first ? c : a;
+    okeys[pos++] = ((uint64_t)owner << b) | nbr;
+    atomicAdd(&outdeg[owner], 1);
+    for (int p = 0; p < passes2; ++p) atomicAdd(&s_hist[p * 256 + ((owner >> (8 * p)) & 255u)], 1u);
+  }
+  __syncthreads();
+  for (int i = tid; i < passes2 * 256; i += kOrientThreads)
+    if (s_hist[i]) atomicAdd(&hist2[i], s_hist[i]);
+}
+
+// ---------------------------------------------------------------------------
+// offsets: exclusive scan of out-degrees (node array) + row binning
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kScanThreads)
+k_offsets(const int32_t *__restrict__ outdeg, int32_t n, int32_t *__restrict__ off,
+          int32_t *__restrict__ warp_rows, int32_t *__restrict__ cta_rows,
+          unsigned long long *status, Ctrl *ctrl) {
+  constexpr int IPT = kScanItemsPerThread, TILE = kScanTile;
+  __shared__ uint32_t s_scratch[32];
+  __shared__ uint32_t s_tile, s_excl;
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid == 0) s_tile = atomicAdd(&ctrl->tile_ticket[kTicketScan], 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint32_t items = (uint32_t)n + 1;  // off[0..n]
+  const uint32_t tile_base = tile * (uint32_t)TILE;
+  if (tile_base >= items) return;
+  const uint32_t first = tile_base + (uint32_t)tid * IPT;
+  int32_t d[IPT];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int i = 0; i < IPT; ++i) {
+    const uint32_t v = first + i;
+    d[i] = v < (uint32_t)n ? __ldg(outdeg + v) : 0;
+    sum += (uint32_t)d[i];
+  }
+  uint32_t tile_sum;
+  const uint32_t toff = block_scan_exclusive<kScanThreads>(sum, s_scratch, &tile_sum);
+  if (tid == 0) s_excl = (uint32_t)lookback_single(status, tile, tile_sum, ctrl);
+  __syncthreads();
+  uint32_t run = s_excl + toff;
+#pragma unroll
+  for (int i = 0; i < IPT; ++i) {
+    const uint32_t v = first + i;
+    if (v < items) off[v] = (int32_t)run;
+    run += (uint32_t)d[i];
+  }
+  // bin rows: one appending atomic per warp and list
+#pragma unroll
+  for (int i = 0; i < IPT; ++i) {
+    const uint32_t v = first + i;
+    const bool is_warp = v < (uint32_t)n && d[i] >= 2 && d[i] <= kWarpMaxRow;
+    const bool is_cta = v < (uint32_t)n && d[i] > kWarpMaxRow;
+    const uint32_t bw = __ballot_sync(kFull, is_warp), bc = __ballot_sync(kFull, is_cta);
+    uint32_t basew = 0, basec = 0;
+    if (lane == 0) {
+      if (bw) basew = atomicAdd(&ctrl->n_warp_rows, (uint32_t)__popc(bw));
+      if (bc) basec = atomicAdd(&ctrl->n_cta_rows, (uint32_t)__popc(bc));
+    }
+    basew = __shfl_sync(kFull, basew, 0);
+    basec = __shfl_sync(kFull, basec, 0);
+    const uint32_t lt = (1u << lane) - 1u;
+    if (is_warp) warp_rows[basew + __popc(bw & lt)] = (int32_t)v;
+    if (is_cta) cta_rows[basec + __popc(bc & lt)] = (int32_t)v;
+  }
+}
+
+int g_num_sms = 0;
+int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  return g_num_sms;
+}
+
+}  // namespace
+
+void launch_canon(const int32_t *src, const int32_t *dst, uint32_t m_in, int32_t n, int b,
+                  int passes, uint64_t *keys, uint32_t *hist, Ctrl *ctrl, cudaStream_t st) {
+  const uint32_t want = (m_in + kCanonThreads * 8 - 1) / (kCanonThreads * 8);
+  const uint32_t cap = (uint32_t)num_sms() * 8;
+  const uint32_t grid = max(1u, min(want, cap));
+  k_canon<<<grid, kCanonThreads, 0, st>>>(src, dst, m_in, n, b, passes, keys, hist, ctrl);
+  note_launch();
+}
+
+void launch_radix_pass(const uint64_t *in, void *out, bool out_col, uint32_t n_keys_bound,
+                       const uint32_t *n_keys_dev, int shift, uint32_t col_mask,
+                       const uint32_t *hist, unsigned long long *status, uint32_t *ticket,
+                       Ctrl *ctrl, cudaStream_t st) {
+  const uint32_t grid = max(1u, (n_keys_bound + kSortTile - 1) / kSortTile);
+  if (out_col)
+    k_radix_pass<true><<<grid, kSortThreads, 0, st>>>(in, out, n_keys_bound, n_keys_dev, shift,
+                                                      col_mask, hist, status, ticket, ctrl);
+  else
+    k_radix_pass<false><<<grid, kSortThreads, 0, st>>>(in, out, n_keys_bound, n_keys_dev, shift,
+                                                       col_mask, hist, status, ticket, ctrl);
+  note_launch();
+}
+
+void launch_unique_degree(const uint64_t *keys, uint32_t m_in, int b, int32_t *deg,
+                          cudaStream_t st) {
+  const uint32_t want = (m_in + kDegThreads * 8 - 1) / (kDegThreads * 8);
+  const uint32_t grid = max(1u, min(want, (uint32_t)num_sms() * 8));
+  k_unique_degree<<<grid, kDegThreads, 0, st>>>(keys, m_in, b, deg);
+  note_launch();
+}
+
+void launch_orient(const uint64_t *keys, uint32_t m_in, int b, const int32_t *deg,
+                   uint64_t *okeys, int32_t *outdeg, uint32_t *hist2, int passes2,
+                   unsigned long long *status, Ctrl *ctrl, cudaStream_t st) {
+  const uint32_t grid = max(1u, (m_in + kOrientTile - 1) / kOrientTile);
+  k_orient<<<grid, kOrientThreads, 0, st>>>(keys, m_in, b, deg, okeys, outdeg, hist2, passes2,
+                                            status, ctrl);
+  note_launch();
+}
+
+void launch_offsets(const int32_t *outdeg, int32_t n, int32_t *off, int32_t *warp_rows,
+                    int32_t *cta_rows, unsigned long long *status, Ctrl *ctrl, cudaStream_t st) {
+  const uint32_t items = (uint32_t)n + 1;
+  const uint32_t grid = max(1u, (items + kScanTile - 1) / kScanTile);
+  k_offsets<<<grid, kScanThreads, 0, st>>>(outdeg, n, off, warp_rows, cta_rows, status, ctrl);
+  note_launch();
+}
+
+}  // namespace tc

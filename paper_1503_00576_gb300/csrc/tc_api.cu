@@ -1,0 +1,434 @@
+// tc_api.cu -- the C ABI of include/tc.h: argument checks, workspace,
+// phase sequence, host-buffer variants, errors and instrumentation.
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "tc.h"
+#include "tc_common.cuh"
+
+namespace tc {
+
+static std::atomic<uint64_t> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+}  // namespace tc
+
+using namespace tc;
+
+namespace {
+
+thread_local tc_status t_last = TC_OK;
+thread_local char t_detail[256] = "";
+
+tc_status set_status(tc_status s, const char *fmt = nullptr, ...) {
+  t_last = s;
+  if (fmt) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(t_detail, sizeof(t_detail), fmt, ap);
+    va_end(ap);
+  } else {
+    t_detail[0] = 0;
+  }
+  return s;
+}
+
+tc_status cuda_fail(cudaError_t e, const char *what) {
+  if (e == cudaErrorMemoryAllocation)
+    return set_status(TC_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return set_status(TC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define TC_CUDA(call, what)                     \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+// ---- instrumentation ----
+std::atomic<int> g_prof_on{0};
+std::mutex g_prof_mu;
+double g_prof_ms[TC_NUM_PHASES];
+uint64_t g_prof_launches[TC_NUM_PHASES];
+
+const char *const kPhaseNames[TC_NUM_PHASES] = {"canon", "sort1", "degree", "orient",
+                                                "sort2", "offsets", "count"};
+
+// Events around each phase of one call, folded into the global totals after
+// the call has synchronised its stream.
+struct PhaseTimer {
+  bool on = false;
+  cudaStream_t st = nullptr;
+  cudaEvent_t beg[TC_NUM_PHASES] = {}, end[TC_NUM_PHASES] = {};
+  uint64_t launches[TC_NUM_PHASES] = {};
+  uint64_t at = 0;
+  bool used[TC_NUM_PHASES] = {};
+
+  explicit PhaseTimer(cudaStream_t s) : st(s) {
+    on = g_prof_on.load() != 0;
+    if (!on) return;
+    for (int i = 0; i < TC_NUM_PHASES; ++i) {
+      cudaEventCreate(&beg[i]);
+      cudaEventCreate(&end[i]);
+    }
+  }
+  void start(int p) {
+    at = g_launches.load();
+    if (!on) return;
+    cudaEventRecord(beg[p], st);
+  }
+  void stop(int p) {
+    if (!on) return;
+    cudaEventRecord(end[p], st);
+    launches[p] += g_launches.load() - at;
+    used[p] = true;
+  }
+  // call after the stream has been synchronised
+  void fold() {
+    if (!on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (int i = 0; i < TC_NUM_PHASES; ++i) {
+      if (!used[i]) continue;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, beg[i], end[i]) == cudaSuccess) g_prof_ms[i] += ms;
+      g_prof_launches[i] += launches[i];
+    }
+  }
+  ~PhaseTimer() {
+    if (!on) return;
+    for (int i = 0; i < TC_NUM_PHASES; ++i) {
+      cudaEventDestroy(beg[i]);
+      cudaEventDestroy(end[i]);
+    }
+  }
+};
+
+// Keep freed stream-ordered allocations cached in the device's default pool
+// (release threshold = unlimited) so repeated calls do not return memory to
+// the driver and fetch it again.
+void keep_pool_memory() {
+  static std::atomic<uint64_t> done_mask{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  const uint64_t bit = 1ull << dev;
+  if (done_mask.load() & bit) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done_mask.fetch_or(bit);
+}
+
+Ctrl *host_ctrl() {
+  static thread_local Ctrl *h = nullptr;
+  if (!h && cudaMallocHost((void **)&h, sizeof(Ctrl)) != cudaSuccess) h = nullptr;
+  return h;
+}
+
+tc_status check_args(const int32_t *src, const int32_t *dst, int64_t m, int32_t n) {
+  if (m < 0 || n < 0) return set_status(TC_ERR_INVALID_ARG, "m=%lld n=%d", (long long)m, n);
+  if (m > (int64_t)INT32_MAX)
+    return set_status(TC_ERR_OVERFLOW, "m=%lld exceeds 2^31-1 pairs", (long long)m);
+  if (m > 0 && (!src || !dst)) return set_status(TC_ERR_INVALID_ARG, "src/dst is NULL");
+  return TC_OK;
+}
+
+// All phases on `st` using workspace `ws` laid out by L.  t_out == nullptr
+// counts the total only.  Synchronises `st` and writes T to *total.
+tc_status run_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t n,
+                   cudaStream_t st, unsigned char *ws, const Layout &L, int64_t *t_out,
+                   int32_t *deg_out, uint64_t *total) {
+  PhaseTimer pt(st);
+  const uint32_t m = (uint32_t)m_in;
+  const int b = id_bits(n);
+  const int passes1 = (2 * b + 7) / 8, passes2 = (b + 7) / 8;
+  Ctrl *ctrl = reinterpret_cast<Ctrl *>(ws + L.ctrl);
+  uint32_t *hist = reinterpret_cast<uint32_t *>(ws + L.hist);
+  auto *st_sort = reinterpret_cast<unsigned long long *>(ws + L.st_sort);
+  auto *st_orient = reinterpret_cast<unsigned long long *>(ws + L.st_orient);
+  auto *st_scan = reinterpret_cast<unsigned long long *>(ws + L.st_scan);
+  uint64_t *keys_a = reinterpret_cast<uint64_t *>(ws + L.keys_a);
+  uint64_t *keys_b = reinterpret_cast<uint64_t *>(ws + L.keys_b);
+  int32_t *deg = deg_out ? deg_out : reinterpret_cast<int32_t *>(ws + L.deg);
+  int32_t *outdeg = reinterpret_cast<int32_t *>(ws + L.outdeg);
+  int32_t *off = reinterpret_cast<int32_t *>(ws + L.off);
+  int32_t *warp_rows = reinterpret_cast<int32_t *>(ws + L.warp_rows);
+  int32_t *cta_rows = reinterpret_cast<int32_t *>(ws + L.cta_rows);
+  const size_t words = L.st_sort_words_per_pass;
+
+  // zero the control block, histograms and the look-back status words in use
+  TC_CUDA(cudaMemsetAsync(ws, 0, L.st_sort + sizeof(unsigned long long) * words *
+                                                  (size_t)(passes1 + passes2), st),
+          "memset control");
+  TC_CUDA(cudaMemsetAsync(ws + L.st_orient, 0, L.keys_a - L.st_orient, st), "memset status");
+  TC_CUDA(cudaMemsetAsync(deg, 0, sizeof(int32_t) * (size_t)n, st), "memset deg");
+  TC_CUDA(cudaMemsetAsync(outdeg, 0, sizeof(int32_t) * (size_t)n, st), "memset outdeg");
+  if (t_out) TC_CUDA(cudaMemsetAsync(t_out, 0, sizeof(int64_t) * (size_t)n, st), "memset t");
+
+  pt.start(TC_PHASE_CANON);
+  launch_canon(src, dst, m, n, b, passes1, keys_a, hist, ctrl, st);
+  pt.stop(TC_PHASE_CANON);
+
+  pt.start(TC_PHASE_SORT1);
+  uint64_t *in = keys_a, *out = keys_b;
+  for (int p = 0; p < passes1; ++p) {
+    launch_radix_pass(in, out, false, m, nullptr, 8 * p, 0u, hist + 256 * p,
+                      st_sort + words * p, &ctrl->tile_ticket[kTicketSort + p], ctrl, st);
+    uint64_t *x = in;
+    in = out;
+    out = x;
+  }
+  pt.stop(TC_PHASE_SORT1);
+
+  pt.start(TC_PHASE_DEGREE);
+  launch_unique_degree(in, m, b, deg, st);
+  pt.stop(TC_PHASE_DEGREE);
+
+  pt.start(TC_PHASE_ORIENT);
+  launch_orient(in, m, b, deg, out, outdeg, hist + 256 * kMaxSort1Passes, passes2, st_orient,
+                ctrl, st);
+  pt.stop(TC_PHASE_ORIENT);
+
+  pt.start(TC_PHASE_SORT2);
+  {
+    uint64_t *x = in;
+    in = out;
+    out = x;
+  }
+  const uint32_t col_mask = (uint32_t)((1ull << b) - 1);
+  for (int p = 0; p < passes2; ++p) {
+    const bool last = p == passes2 - 1;
+    launch_radix_pass(in, out, last, m, &ctrl->m, b + 8 * p, col_mask,
+                      hist + 256 * (kMaxSort1Passes + p), st_sort + words * (passes1 + p),
+                      &ctrl->tile_ticket[kTicketSort + passes1 + p], ctrl, st);
+    if (!last) {
+      uint64_t *x = in;
+      in = out;
+      out = x;
+    }
+  }
+  const int32_t *col = reinterpret_cast<const int32_t *>(out);
+  pt.stop(TC_PHASE_SORT2);
+
+  pt.start(TC_PHASE_OFFSETS);
+  launch_offsets(outdeg, n, off, warp_rows, cta_rows, st_scan, ctrl, st);
+  pt.stop(TC_PHASE_OFFSETS);
+
+  pt.start(TC_PHASE_COUNT);
+  cudaError_t e = launch_count(off, col, warp_rows, cta_rows, ctrl, t_out, st);
+  pt.stop(TC_PHASE_COUNT);
+  if (e != cudaSuccess) return cuda_fail(e, "count kernel");
+  TC_CUDA(cudaGetLastError(), "kernel launch");
+
+  Ctrl *h = host_ctrl();
+  if (!h) return set_status(TC_ERR_OOM, "pinned staging buffer");
+  TC_CUDA(cudaMemcpyAsync(h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st), "read result");
+  TC_CUDA(cudaStreamSynchronize(st), "synchronize");
+  pt.fold();
+  if (h->err & kErrIdRange)
+    return set_status(TC_ERR_ID_RANGE, "a vertex id is outside [0, %d)", n);
+  if (h->err & kErrTimeout)
+    return set_status(TC_ERR_TIMEOUT, "a device-side wait reached its iteration limit");
+  *total = (uint64_t)h->total;
+  return set_status(TC_OK);
+}
+
+tc_status count_impl(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
+                     cudaStream_t st, void *ws_user, size_t ws_bytes, int64_t *t_out,
+                     int32_t *deg_out, uint64_t *total) {
+  tc_status s = check_args(src, dst, m, n);
+  if (s != TC_OK) return s;
+  if (m > 0 && n == 0) return set_status(TC_ERR_ID_RANGE, "n = 0 but m > 0");
+  if (m == 0) {
+    if (n > 0 && t_out)
+      TC_CUDA(cudaMemsetAsync(t_out, 0, sizeof(int64_t) * (size_t)n, st), "memset t");
+    if (n > 0 && deg_out)
+      TC_CUDA(cudaMemsetAsync(deg_out, 0, sizeof(int32_t) * (size_t)n, st), "memset deg");
+    TC_CUDA(cudaStreamSynchronize(st), "synchronize");
+    *total = 0;
+    return set_status(TC_OK);
+  }
+  const Layout L = make_layout(m, n);
+  if (ws_user) {
+    if (ws_bytes < L.total)
+      return set_status(TC_ERR_INVALID_ARG, "workspace has %zu bytes, needs %zu", ws_bytes,
+                        L.total);
+    if ((uintptr_t)ws_user & 255)
+      return set_status(TC_ERR_INVALID_ARG, "workspace is not 256-byte aligned");
+    return run_core(src, dst, m, n, st, (unsigned char *)ws_user, L, t_out, deg_out, total);
+  }
+  keep_pool_memory();
+  void *ws = nullptr;
+  TC_CUDA(cudaMallocAsync(&ws, L.total, st), "workspace allocation");
+  s = run_core(src, dst, m, n, st, (unsigned char *)ws, L, t_out, deg_out, total);
+  const tc_status keep = s;
+  char detail[256];
+  memcpy(detail, t_detail, sizeof(detail));
+  cudaError_t e = cudaFreeAsync(ws, st);
+  if (keep != TC_OK) {
+    t_last = keep;
+    memcpy(t_detail, detail, sizeof(detail));
+    return keep;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "workspace release");
+  return keep;
+}
+
+// Host-buffer driver: copy in, count, copy out, on a private stream.
+tc_status host_impl(const int32_t *src_h, const int32_t *dst_h, int64_t m, int32_t n,
+                    int64_t *t_h, int32_t *deg_h, uint64_t *total, bool per_vertex) {
+  tc_status s = check_args(src_h, dst_h, m, n);
+  if (s != TC_OK) return s;
+  if (per_vertex && n > 0 && !t_h) return set_status(TC_ERR_INVALID_ARG, "t_host is NULL");
+  static thread_local cudaStream_t st = nullptr;
+  if (!st) TC_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream");
+  keep_pool_memory();
+  const size_t in_bytes = sizeof(int32_t) * (size_t)m;
+  int32_t *d_src = nullptr, *d_dst = nullptr, *d_deg = nullptr;
+  int64_t *d_t = nullptr;
+  if (m > 0) {
+    TC_CUDA(cudaMallocAsync((void **)&d_src, in_bytes, st), "input allocation");
+    TC_CUDA(cudaMallocAsync((void **)&d_dst, in_bytes, st), "input allocation");
+    TC_CUDA(cudaMemcpyAsync(d_src, src_h, in_bytes, cudaMemcpyHostToDevice, st), "copy in");
+    TC_CUDA(cudaMemcpyAsync(d_dst, dst_h, in_bytes, cudaMemcpyHostToDevice, st), "copy in");
+  }
+  if (per_vertex && n > 0) {
+    TC_CUDA(cudaMallocAsync((void **)&d_t, sizeof(int64_t) * (size_t)n, st), "t allocation");
+    if (deg_h)
+      TC_CUDA(cudaMallocAsync((void **)&d_deg, sizeof(int32_t) * (size_t)n, st), "deg allocation");
+  }
+  uint64_t T = 0;
+  s = count_impl(d_src, d_dst, m, n, st, nullptr, 0, per_vertex ? d_t : nullptr, d_deg, &T);
+  if (s == TC_OK && per_vertex && n > 0) {
+    cudaError_t e = cudaMemcpyAsync(t_h, d_t, sizeof(int64_t) * (size_t)n,
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && deg_h)
+      e = cudaMemcpyAsync(deg_h, d_deg, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) s = cuda_fail(e, "copy out");
+  }
+  if (d_src) cudaFreeAsync(d_src, st);
+  if (d_dst) cudaFreeAsync(d_dst, st);
+  if (d_t) cudaFreeAsync(d_t, st);
+  if (d_deg) cudaFreeAsync(d_deg, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (s != TC_OK) return s;
+  if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+  if (total) *total = T;
+  return set_status(TC_OK);
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t tc_count(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
+                  tc_stream_t stream) {
+  uint64_t T = 0;
+  tc_status s = count_impl(src, dst, m, n, (cudaStream_t)stream, nullptr, 0, nullptr, nullptr, &T);
+  return s == TC_OK ? T : TC_COUNT_ERROR;
+}
+
+tc_status tc_count_per_vertex(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
+                              tc_stream_t stream, int64_t *t_out, int32_t *deg_out,
+                              uint64_t *total_out) {
+  if (n > 0 && !t_out) return set_status(TC_ERR_INVALID_ARG, "t_out is NULL");
+  uint64_t T = 0;
+  tc_status s =
+      count_impl(src, dst, m, n, (cudaStream_t)stream, nullptr, 0, t_out, deg_out, &T);
+  if (s == TC_OK && total_out) *total_out = T;
+  return s;
+}
+
+tc_status tc_clustering(const int64_t *t, const int32_t *deg, int32_t n, tc_stream_t stream,
+                        double *cc_out, double *transitivity_out) {
+  if (n < 0) return set_status(TC_ERR_INVALID_ARG, "n < 0");
+  if (n > 0 && (!t || !deg)) return set_status(TC_ERR_INVALID_ARG, "t/deg is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n == 0) {
+    if (transitivity_out) *transitivity_out = 0.0;
+    return set_status(TC_OK);
+  }
+  keep_pool_memory();
+  unsigned char *buf = nullptr;
+  TC_CUDA(cudaMallocAsync((void **)&buf, 32, st), "scratch allocation");
+  auto *sums = reinterpret_cast<unsigned long long *>(buf);
+  double *dev_out = reinterpret_cast<double *>(buf + 16);
+  TC_CUDA(cudaMemsetAsync(buf, 0, 32, st), "memset");
+  launch_clustering(t, deg, n, cc_out, sums, st);
+  launch_transitivity(sums, dev_out, st);
+  double h = 0.0;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && transitivity_out)
+    e = cudaMemcpyAsync(&h, dev_out, sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(buf, st);
+  if (e == cudaSuccess && transitivity_out) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "clustering");
+  if (transitivity_out) *transitivity_out = h;
+  return set_status(TC_OK);
+}
+
+tc_status tc_count_host(const int32_t *src_host, const int32_t *dst_host, int64_t m, int32_t n,
+                        uint64_t *total_out) {
+  return host_impl(src_host, dst_host, m, n, nullptr, nullptr, total_out, false);
+}
+
+tc_status tc_count_per_vertex_host(const int32_t *src_host, const int32_t *dst_host, int64_t m,
+                                   int32_t n, int64_t *t_host, int32_t *deg_host,
+                                   uint64_t *total_out) {
+  return host_impl(src_host, dst_host, m, n, t_host, deg_host, total_out, true);
+}
+
+size_t tc_workspace_bytes(int64_t m, int32_t n) {
+  if (m < 0 || n < 0 || m > (int64_t)INT32_MAX) return 0;
+  return make_layout(m, n).total;
+}
+
+tc_status tc_count_ws(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
+                      tc_stream_t stream, void *ws, size_t ws_bytes, uint64_t *total_out) {
+  if (!ws || !total_out) return set_status(TC_ERR_INVALID_ARG, "ws/total_out is NULL");
+  return count_impl(src, dst, m, n, (cudaStream_t)stream, ws, ws_bytes, nullptr, nullptr,
+                    total_out);
+}
+
+tc_status tc_last_error(void) { return t_last; }
+
+const char *tc_last_error_detail(void) { return t_detail; }
+
+const char *tc_status_string(tc_status s) {
+  switch (s) {
+    case TC_OK: return "ok";
+    case TC_ERR_INVALID_ARG: return "invalid argument";
+    case TC_ERR_ID_RANGE: return "vertex id out of range";
+    case TC_ERR_OOM: return "out of device memory";
+    case TC_ERR_CUDA: return "CUDA error";
+    case TC_ERR_TIMEOUT: return "device wait timed out";
+    case TC_ERR_OVERFLOW: return "size beyond limits";
+  }
+  return "unknown status";
+}
+
+uint64_t tc_launch_count(void) { return g_launches.load(); }
+
+void tc_profile_enable(int on) { g_prof_on.store(on ? 1 : 0); }
+
+void tc_profile_read(double *ms_out, uint64_t *launches_out, int reset) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (int i = 0; i < TC_NUM_PHASES; ++i) {
+    if (ms_out) ms_out[i] = g_prof_ms[i];
+    if (launches_out) launches_out[i] = g_prof_launches[i];
+    if (reset) {
+      g_prof_ms[i] = 0.0;
+      g_prof_launches[i] = 0;
+    }
+  }
+}
+
+const char *tc_phase_name(int phase) {
+  return (phase >= 0 && phase < TC_NUM_PHASES) ? kPhaseNames[phase] : "?";
+}
+
+}  // extern "C"

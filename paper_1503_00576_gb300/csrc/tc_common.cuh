@@ -1,0 +1,136 @@
+// tc_common.cuh -- definitions shared by the library's CUDA translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tc {
+
+// Device-side error bits (Ctrl::err).
+enum : uint32_t { kErrIdRange = 1u, kErrTimeout = 2u };
+
+// Upper bound on iterations of any spin-wait in a kernel.  Every wait in this
+// library is on a predecessor tile that is already resident (tiles are handed
+// out in launch order through an atomic ticket), so the bound is a safety
+// net: if it is ever reached the kernel records kErrTimeout, stops waiting
+// and the host reports TC_ERR_TIMEOUT.
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+constexpr int kMaxSort1Passes = 8;  // 2 * 31 id bits / 8-bit digits
+constexpr int kMaxSort2Passes = 4;  // 31 owner bits / 8-bit digits
+constexpr int kMaxPasses = kMaxSort1Passes + kMaxSort2Passes;
+
+// Control block: zeroed at the start of every call.
+struct Ctrl {
+  uint32_t err;                    // kErr* bits
+  uint32_t m;                      // distinct undirected edges (set by orient)
+  uint32_t tile_ticket[16];        // per look-back kernel: next tile to hand out
+  uint32_t n_warp_rows;            // rows counted by one warp each
+  uint32_t n_cta_rows;             // rows counted by a whole CTA each
+  uint32_t next_warp_row;          // work cursors of the counting kernel
+  uint32_t next_cta_row;
+  unsigned long long total;        // triangle count T
+  uint32_t pad[8];
+};
+static_assert(sizeof(Ctrl) % 16 == 0, "Ctrl must keep 16-byte alignment");
+
+// Ticket slots in Ctrl::tile_ticket.
+enum { kTicketSort = 0 /* .. kMaxPasses-1 */, kTicketOrient = 12, kTicketScan = 13 };
+
+// Look-back status words: value in the low 62 bits, flag in the top 2.
+constexpr unsigned long long kFlagAggregate = 1ull << 62;
+constexpr unsigned long long kFlagInclusive = 2ull << 62;
+constexpr unsigned long long kValueMask = (1ull << 62) - 1;
+
+// Rows (forward lists) longer than this are counted by a whole CTA.
+constexpr int kWarpMaxRow = 256;
+
+// Workspace layout for an input of m_in pairs and n vertices.  All offsets
+// are 256-byte aligned.
+struct Layout {
+  size_t ctrl, hist, st_sort, st_orient, st_scan;
+  size_t keys_a, keys_b, deg, outdeg, off, warp_rows, cta_rows;
+  size_t total;
+  uint32_t sort_tiles, orient_tiles, scan_tiles;
+  size_t st_sort_words_per_pass;
+};
+
+// Radix sort tiles: 256 threads x 16 keys.
+constexpr int kSortThreads = 256;
+constexpr int kSortKeysPerThread = 16;
+constexpr int kSortTile = kSortThreads * kSortKeysPerThread;
+// Orientation/compaction tiles.
+constexpr int kOrientThreads = 256;
+constexpr int kOrientKeysPerThread = 16;
+constexpr int kOrientTile = kOrientThreads * kOrientKeysPerThread;
+// Offset-scan tiles.
+constexpr int kScanThreads = 256;
+constexpr int kScanItemsPerThread = 16;
+constexpr int kScanTile = kScanThreads * kScanItemsPerThread;
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+inline Layout make_layout(int64_t m_in, int32_t n) {
+  Layout L{};
+  size_t p = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = p;
+    p = align256(p + bytes);
+    return at;
+  };
+  const uint64_t m = (uint64_t)(m_in > 0 ? m_in : 1);
+  const uint64_t nv = (uint64_t)(n > 0 ? n : 1);
+  L.sort_tiles = (uint32_t)((m + kSortTile - 1) / kSortTile);
+  L.orient_tiles = (uint32_t)((m + kOrientTile - 1) / kOrientTile);
+  L.scan_tiles = (uint32_t)((nv + 1 + kScanTile - 1) / kScanTile);
+  L.st_sort_words_per_pass = (size_t)L.sort_tiles * 256;
+  L.ctrl = take(sizeof(Ctrl));
+  L.hist = take(sizeof(uint32_t) * 256 * kMaxPasses);
+  L.st_sort = take(sizeof(unsigned long long) * L.st_sort_words_per_pass * kMaxPasses);
+  L.st_orient = take(sizeof(unsigned long long) * L.orient_tiles);
+  L.st_scan = take(sizeof(unsigned long long) * L.scan_tiles);
+  L.keys_a = take(sizeof(uint64_t) * m);
+  L.keys_b = take(sizeof(uint64_t) * m);
+  L.deg = take(sizeof(int32_t) * nv);
+  L.outdeg = take(sizeof(int32_t) * nv);
+  L.off = take(sizeof(int32_t) * (nv + 1));
+  L.warp_rows = take(sizeof(int32_t) * nv);
+  L.cta_rows = take(sizeof(int32_t) * nv);
+  L.total = p;
+  return L;
+}
+
+// Number of bits that hold any id in [0, n): at least 1.
+inline int id_bits(int32_t n) {
+  int b = 1;
+  while (b < 31 && ((int64_t)1 << b) < (int64_t)n) ++b;
+  return b;
+}
+
+// Kernel-launch bookkeeping (defined in tc_api.cu).
+void note_launch();
+
+// ---- launchers (preprocess.cu) ----
+void launch_canon(const int32_t *src, const int32_t *dst, uint32_t m_in, int32_t n, int b,
+                  int passes, uint64_t *keys, uint32_t *hist, Ctrl *ctrl, cudaStream_t st);
+void launch_radix_pass(const uint64_t *in, void *out, bool out_col, uint32_t n_keys_bound,
+                       const uint32_t *n_keys_dev, int shift, uint32_t col_mask,
+                       const uint32_t *hist, unsigned long long *status, uint32_t *ticket,
+                       Ctrl *ctrl, cudaStream_t st);
+void launch_unique_degree(const uint64_t *keys, uint32_t m_in, int b, int32_t *deg,
+                          cudaStream_t st);
+void launch_orient(const uint64_t *keys, uint32_t m_in, int b, const int32_t *deg,
+                   uint64_t *okeys, int32_t *outdeg, uint32_t *hist2, int passes2,
+                   unsigned long long *status, Ctrl *ctrl, cudaStream_t st);
+void launch_offsets(const int32_t *outdeg, int32_t n, int32_t *off, int32_t *warp_rows,
+                    int32_t *cta_rows, unsigned long long *status, Ctrl *ctrl, cudaStream_t st);
+// ---- launchers (count.cu) ----
+cudaError_t launch_count(const int32_t *off, const int32_t *col, const int32_t *warp_rows,
+                         const int32_t *cta_rows, Ctrl *ctrl, int64_t *t, cudaStream_t st);
+// ---- clustering (count.cu) ----
+void launch_clustering(const int64_t *t, const int32_t *deg, int32_t n, double *cc,
+                       unsigned long long *sums /* [2]: sum t, sum C(deg,2) */, cudaStream_t st);
+void launch_transitivity(const unsigned long long *sums, double *out, cudaStream_t st);
+
+}  // namespace tc
