@@ -128,6 +128,37 @@ size_t tc_workspace_bytes(int64_t m, int32_t n);
 tc_status tc_count_ws(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
                       tc_stream_t stream, void *ws, size_t ws_bytes, uint64_t *total_out);
 
+/*
+ * Allocation-free count, for callers that cannot allocate device memory
+ * while they run: for example a process whose own pool allocator reserves
+ * all device memory at start-up and forbids driver allocations afterwards,
+ * or a service whose memory budget is fixed when it starts.  The paper has
+ * no counterpart; this is a deployment variant of tc_count.
+ *
+ * It computes exactly what tc_count computes, on the caller's device
+ * pointers and stream, but its scratch space is a static device array of
+ * TC_NOALLOC_SCRATCH_BYTES bytes that is part of the library image: every
+ * GPU that loads the library holds it until the process exits.  The call
+ * allocates nothing (no cudaMalloc*, cudaFree*, pinned host buffers or
+ * events).
+ *   src, dst   device int32[m], read-only
+ *   total_out  HOST uint64, receives T
+ * Returns TC_ERR_OVERFLOW, with a message stating the bytes needed, when
+ * tc_workspace_bytes(m, n) exceeds TC_NOALLOC_SCRATCH_BYTES (about
+ * 22 m + 20 n bytes: up to about 1.4 million pairs with n = 2^16).
+ * Synchronises.
+ *
+ * The first call on a device looks up the array's device address on that
+ * device (cudaGetSymbolAddress); make that first call before capturing any
+ * stream.  All calls share the one array and it keeps the previous call's
+ * contents (each call clears what must start at zero), so calls that
+ * overlap on the GPU -- from two threads or on two streams -- race: order
+ * them.
+ */
+#define TC_NOALLOC_SCRATCH_BYTES (32u << 20)
+tc_status tc_count_noalloc(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
+                           tc_stream_t stream, uint64_t *total_out);
+
 /* Status of the calling thread's most recent call, and its name. */
 tc_status tc_last_error(void);
 const char *tc_status_string(tc_status status);

@@ -43,7 +43,8 @@ PHASES = ("canon", "sort1", "degree", "orient", "sort2", "offsets", "count")
 
 # Every symbol include/tc.h declares.
 EXPORTS = ("tc_count", "tc_count_per_vertex", "tc_clustering", "tc_count_host",
-           "tc_count_per_vertex_host", "tc_workspace_bytes", "tc_count_ws", "tc_last_error",
+           "tc_count_per_vertex_host", "tc_workspace_bytes", "tc_count_ws", "tc_count_noalloc",
+           "tc_last_error",
            "tc_status_string", "tc_last_error_detail", "tc_launch_count", "tc_profile_enable",
            "tc_profile_read", "tc_phase_name")
 
@@ -73,6 +74,7 @@ def _bind(lib):
         "tc_count_per_vertex_host": ([vp, vp, i64, i32, vp, vp, c.POINTER(u64)], c.c_int),
         "tc_workspace_bytes": ([i64, i32], sz),
         "tc_count_ws": ([vp, vp, i64, i32, vp, vp, sz, c.POINTER(u64)], c.c_int),
+        "tc_count_noalloc": ([vp, vp, i64, i32, vp, c.POINTER(u64)], c.c_int),
         "tc_last_error": ([], c.c_int),
         "tc_status_string": ([c.c_int], c.c_char_p),
         "tc_last_error_detail": ([], c.c_char_p),
@@ -260,6 +262,26 @@ def tc_count_ws(src, dst, n: int, ws, stream=None) -> int:
         rc = lib.tc_count_ws(src.data_ptr(), dst.data_ptr(), src.numel(), n,
                              _stream_of(stream, dev), ws.data_ptr(),
                              ws.numel() * ws.element_size(), ctypes.byref(total))
+    _check(rc)
+    return int(total.value)
+
+
+TC_NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def tc_count_noalloc(src, dst, n: int, stream=None) -> int:
+    """T without any allocation inside the library: for callers that cannot
+    allocate device memory while they run.  Scratch is a static device array
+    of TC_NOALLOC_SCRATCH_BYTES shared by all calls, so calls must not
+    overlap on the GPU; graphs needing more scratch raise TCError
+    (TC_ERR_OVERFLOW)."""
+    torch = _torch()
+    dev = _edges(src, dst)
+    total = ctypes.c_uint64(0)
+    lib = load_library()
+    with torch.cuda.device(dev):
+        rc = lib.tc_count_noalloc(src.data_ptr(), dst.data_ptr(), src.numel(), n,
+                                  _stream_of(stream, dev), ctypes.byref(total))
     _check(rc)
     return int(total.value)
 

@@ -67,8 +67,8 @@ struct PhaseTimer {
   uint64_t at = 0;
   bool used[TC_NUM_PHASES] = {};
 
-  explicit PhaseTimer(cudaStream_t s) : st(s) {
-    on = g_prof_on.load() != 0;
+  PhaseTimer(cudaStream_t s, bool allowed) : st(s) {
+    on = allowed && g_prof_on.load() != 0;
     if (!on) return;
     for (int i = 0; i < TC_NUM_PHASES; ++i) {
       cudaEventCreate(&beg[i]);
@@ -138,11 +138,15 @@ tc_status check_args(const int32_t *src, const int32_t *dst, int64_t m, int32_t 
 }
 
 // All phases on `st` using workspace `ws` laid out by L.  t_out == nullptr
-// counts the total only.  Synchronises `st` and writes T to *total.
+// counts the total only.  Synchronises `st` and writes T to *total.  The
+// control block is read back into `staging` when given (any host memory),
+// else into this thread's pinned buffer; `profile` = false never records
+// phase events.
 tc_status run_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t n,
                    cudaStream_t st, unsigned char *ws, const Layout &L, int64_t *t_out,
-                   int32_t *deg_out, uint64_t *total) {
-  PhaseTimer pt(st);
+                   int32_t *deg_out, uint64_t *total, Ctrl *staging = nullptr,
+                   bool profile = true) {
+  PhaseTimer pt(st, profile);
   const uint32_t m = (uint32_t)m_in;
   const int b = id_bits(n);
   const int passes1 = (2 * b + 7) / 8, passes2 = (b + 7) / 8;
@@ -224,7 +228,7 @@ tc_status run_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t
   if (e != cudaSuccess) return cuda_fail(e, "count kernel");
   TC_CUDA(cudaGetLastError(), "kernel launch");
 
-  Ctrl *h = host_ctrl();
+  Ctrl *h = staging ? staging : host_ctrl();
   if (!h) return set_status(TC_ERR_OOM, "pinned staging buffer");
   TC_CUDA(cudaMemcpyAsync(h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st), "read result");
   TC_CUDA(cudaStreamSynchronize(st), "synchronize");
@@ -321,6 +325,42 @@ tc_status host_impl(const int32_t *src_h, const int32_t *dst_h, int64_t m, int32
   return set_status(TC_OK);
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free counting (tc_count_noalloc).
+//
+// Some callers cannot allocate device memory when they count: a host process
+// that hands all device memory to its own pool allocator at start-up and
+// forbids driver allocations afterwards, or a service whose memory budget is
+// fixed when it starts.  For them the whole workspace lives in this
+// file-scope array, reserved when the library is loaded and held by every GPU
+// that loads it until the process exits.  Host code cannot pass the array's
+// name to a kernel (on the host it is only a stand-in symbol), so its device
+// address is looked up once per device with cudaGetSymbolAddress, with that
+// device current, on the first call made there.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[TC_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device.
+tc_status noalloc_scratch(unsigned char **out) {
+  int dev = -1;
+  TC_CUDA(cudaGetDevice(&dev), "current device");
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return set_status(TC_ERR_INVALID_ARG, "device %d is beyond the %d supported", dev,
+                      kNoAllocMaxDevices);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    TC_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch), "scratch symbol address");
+    g_noalloc_addr[dev] = static_cast<unsigned char *>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return TC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -392,6 +432,29 @@ tc_status tc_count_ws(const int32_t *src, const int32_t *dst, int64_t m, int32_t
   if (!ws || !total_out) return set_status(TC_ERR_INVALID_ARG, "ws/total_out is NULL");
   return count_impl(src, dst, m, n, (cudaStream_t)stream, ws, ws_bytes, nullptr, nullptr,
                     total_out);
+}
+
+tc_status tc_count_noalloc(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
+                           tc_stream_t stream, uint64_t *total_out) {
+  if (!total_out) return set_status(TC_ERR_INVALID_ARG, "total_out is NULL");
+  tc_status s = check_args(src, dst, m, n);
+  if (s != TC_OK) return s;
+  if (m > 0 && n == 0) return set_status(TC_ERR_ID_RANGE, "n = 0 but m > 0");
+  if (m == 0) {
+    *total_out = 0;
+    return set_status(TC_OK);
+  }
+  const Layout L = make_layout(m, n);
+  if (L.total > (size_t)TC_NOALLOC_SCRATCH_BYTES)
+    return set_status(TC_ERR_OVERFLOW,
+                      "m=%lld, n=%d needs %zu bytes of scratch; the static scratch holds %zu",
+                      (long long)m, n, L.total, (size_t)TC_NOALLOC_SCRATCH_BYTES);
+  unsigned char *ws = nullptr;
+  s = noalloc_scratch(&ws);
+  if (s != TC_OK) return s;
+  Ctrl staging;  // pageable host memory: no pinned allocation either
+  return run_core(src, dst, m, n, (cudaStream_t)stream, ws, L, nullptr, nullptr, total_out,
+                  &staging, false);
 }
 
 tc_status tc_last_error(void) { return t_last; }
