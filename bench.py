@@ -40,8 +40,9 @@ UNIT = "edges/s"
 CPU_SAMPLE_PAIRS = 24_000_000      # cpu_baseline: first pairs of the workload
 REF_SAMPLE_PAIRS = 6_000_000       # reference arm: per step
 KERNEL_OF_PHASE = {"canon": "k_canon", "sort1": "k_radix_pass", "degree": "k_unique_degree",
+                   "rank": "k_rank_keys+k_radix_pass",
                    "orient": "k_orient", "sort2": "k_radix_pass", "offsets": "k_offsets",
-                   "count": "k_count"}
+                   "groups": "k_group_count+k_offsets+k_group_fill", "count": "k_count"}
 
 
 def parse_args():
@@ -167,7 +168,7 @@ def measured_peaks() -> dict:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("preprocess.cu", "count.cu", "tc_common.cuh"):
+    for name in ("preprocess.cu", "group.cu", "count.cu", "tc_common.cuh"):
         with open(os.path.join(ROOT, "paper_1503_00576_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

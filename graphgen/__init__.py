@@ -17,6 +17,7 @@ are not available, so seeded synthetic graphs of the same families stand in):
             permuted ids, self-loops and duplicates kept in the input
   rgg4m     random geometric graph, n=4,194,304, r=sqrt(32/(pi n))
   rmat24    R-MAT scale 24, draws until 180,000,000 distinct edges
+  rmat22    R-MAT scale 22, draws until 45,000,000 distinct edges (profiling)
 """
 from __future__ import annotations
 
@@ -163,11 +164,17 @@ def _w_rmat24():
     return rmat_distinct(24, 180_000_000, 1004) + (1 << 24,)
 
 
+def _w_rmat22():
+    return rmat_distinct(22, 45_000_000, 1005) + (1 << 22,)
+
+
 WORKLOADS = {
     "er16k": ("Erdos-Renyi G(n=16384, m=131072), seed 1001", _w_er16k),
     "rmat20": ("R-MAT scale 20, 16,777,216 raw draws, permuted ids, seed 1002", _w_rmat20),
     "rgg4m": ("random geometric graph n=4,194,304, r=sqrt(32/(pi n)), seed 1003", _w_rgg4m),
     "rmat24": ("R-MAT scale 24, draws until 180,000,000 distinct edges, seed 1004", _w_rmat24),
+    # same density as rmat24 at a quarter of the size: profiling captures
+    "rmat22": ("R-MAT scale 22, draws until 45,000,000 distinct edges, seed 1005", _w_rmat22),
 }
 
 

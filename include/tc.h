@@ -181,11 +181,13 @@ enum {
   TC_PHASE_CANON = 0,   /* validate ids, drop loops, 64-bit keys, digit histograms */
   TC_PHASE_SORT1 = 1,   /* LSD radix sort of the undirected keys */
   TC_PHASE_DEGREE = 2,  /* drop repeats, degree histogram */
-  TC_PHASE_ORIENT = 3,  /* compact + orient by (degree, id) + out-degree */
-  TC_PHASE_SORT2 = 4,   /* LSD radix sort by owner, unzip to the column array */
-  TC_PHASE_OFFSETS = 5, /* node array by exclusive scan, row lists */
-  TC_PHASE_COUNT = 6,   /* intersections and reductions */
-  TC_NUM_PHASES = 7
+  TC_PHASE_RANK = 3,    /* vertex ranks in (degree, id) order */
+  TC_PHASE_ORIENT = 4,  /* compact + orient from the lower rank + out-degree */
+  TC_PHASE_SORT2 = 5,   /* LSD radix sort by owner, unzip to the column array */
+  TC_PHASE_OFFSETS = 6, /* node array by exclusive scan */
+  TC_PHASE_GROUPS = 7,  /* each forward edge to the endpoint with the longer list */
+  TC_PHASE_COUNT = 8,   /* intersections, reductions, counts back to caller ids */
+  TC_NUM_PHASES = 9
 };
 uint64_t tc_launch_count(void);
 void tc_profile_enable(int on);

@@ -39,7 +39,7 @@ TC_ERR_CUDA = 4
 TC_ERR_TIMEOUT = 5
 TC_ERR_OVERFLOW = 6
 TC_COUNT_ERROR = (1 << 64) - 1
-PHASES = ("canon", "sort1", "degree", "orient", "sort2", "offsets", "count")
+PHASES = ("canon", "sort1", "degree", "rank", "orient", "sort2", "offsets", "groups", "count")
 
 # Every symbol include/tc.h declares.
 EXPORTS = ("tc_count", "tc_count_per_vertex", "tc_clustering", "tc_count_host",

@@ -2,45 +2,66 @@
 //
 // Sec. III-C of the paper counts with one thread per forward edge (u, v),
 // each running a two-pointer merge of N+(u) and N+(v) from global memory,
-// and then sums the per-thread counts (thrust::reduce).  The result is
-// sum over forward edges of |N+(u) & N+(v)|.  The same sum is computed here
-// row by row, which suits a GB300 SM better than a per-thread merge:
+// and then sums the per-thread counts (thrust::reduce).  The result is the
+// sum over forward edges of |N+(u) & N+(v)|.  Here the same sum is computed
+// over the partner groups built in group.cu (group h: the edges whose
+// longer forward list is N+(h); partners l: their other endpoints):
 //
-//  * a row u (its forward list N+(u), sorted, length du) is staged once in
-//    shared memory as an open-addressing hash set (multiplicative hashing,
-//    linear probing, load <= 1/2), by one warp for du <= 256 or by a whole
-//    CTA for longer rows;
-//  * for the <= 32 forward neighbours v of one chunk of N+(u), the lists
-//    N+(v) are read back to back as one flat sequence: in each 32-wide window
-//    lane p takes flat element p, finds its list by a ballot over the list
-//    starts plus an OR-reduction of the starts inside the window, and tests
-//    membership in the hash set.  Loads of N+(v) are coalesced and every lane
-//    does useful work however short the lists are;
+//  * N+(h) is staged once in shared memory as an open-addressing hash set
+//    (multiplicative hashing, linear probing, load <= 1/4; <= 1/2 past 4096
+//    entries), by one warp when |N+(h)| <= 128, else by a whole CTA whose
+//    warps claim chunks of 32 partners from a shared counter;
+//  * for the <= 32 partners l of a chunk, the lists N+(l) are read back to
+//    back as one flat sequence: in each 32-wide window lane p takes flat
+//    element p and finds its list by a ballot over the list starts plus an
+//    OR-reduction of the starts inside the window.  Loads are coalesced,
+//    every lane works however short the lists are, and four windows of loads
+//    are in flight per warp before any is probed;
 //  * counts stay in registers and are reduced per warp (shuffles) into one
 //    uint64 atomic per warp at the end (the paper's reduction, fused).
 //
 // Per-vertex counts t(v) (Sec. I: the numerator of the clustering
-// coefficient): a triangle found at row u, neighbour v, element w adds one
-// to t(u), t(v) and t(w).  t(u) is summed over the row, t(v) over the chunk
-// (shared-memory counters per neighbour) and t(w) in a 16-bit counter beside
-// w's hash slot, so global atomics scale with the number of forward edges,
+// coefficient): a triangle found in group h, partner l, element w adds one
+// to t(h), t(l) and t(w).  t(h) is summed over the group, t(l) over the
+// chunk (shared counters per partner) and t(w) in a 16-bit counter beside
+// w's hash slot (groups with fewer than 65536 partners; larger groups add to
+// t(w) directly), so global atomics scale with the number of forward edges,
 // not with the number of triangles.
 //
-// Rows longer than the CTA table (du > 8192, never seen in the workloads but
-// allowed by the bound du <= sqrt(2m)) fall back to a binary search of
-// N+(u) in global memory for membership.
+// A hashed list longer than 8192 entries (never seen in the workloads, but
+// allowed by |N+(v)| <= sqrt(2m)) is hashed in segments.  No step needs the
+// lists in sorted order: membership is by hashing, not by merging.
 #include "tc_common.cuh"
 
 namespace tc {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kCountThreads = 512;
-constexpr int kCountWarps = kCountThreads / 32;
-constexpr int kCtaSlots = 16384;                      // hash slots per CTA
-constexpr int kWarpSlots = kCtaSlots / kCountWarps;   // per warp in warp mode
-constexpr int kRowChunk = 4;                          // rows grabbed per atomic
-static_assert(kWarpSlots >= 4 * kWarpMaxRow, "warp tables must keep load <= 1/4");
+constexpr int kWarpSlots = 4 * kWarpMaxRow;  // per-warp table
+constexpr int kGroupChunk = 8;               // warp groups per atomic
+constexpr int kWindows = 4;                  // 32-wide windows of loads in flight
+
+// Main kernel: 256-thread CTAs; CTA tables of 4096 slots serve hashed lists
+// of up to kCtaMaxRow entries (load <= 1/8 up to 512, <= 1/4 up to 1024).
+constexpr int kMainThreads = 256;
+constexpr int kMainWarps = kMainThreads / 32;
+constexpr int kMainSlots = 4096;
+// Long-list kernel: 512-thread CTAs, 16384 slots (lists up to 8192 entries
+// at once; longer lists in segments).
+constexpr int kBigThreads = 512;
+constexpr int kBigWarps = kBigThreads / 32;
+constexpr int kBigSlots = 16384;
+static_assert(kWarpSlots * kMainWarps <= kMainSlots, "warp tables must fit the CTA table");
+static_assert(4 * kCtaMaxRow <= kMainSlots, "CTA lists must fit at load <= 1/4");
+
+// Hash-set slots.  Ids are < 2^31 - 1, so 0x7fffffff marks an empty slot and
+// bit 31 of an occupied slot records that some key whose home is this slot
+// was displaced further along (linear probing).  A lookup whose home slot is
+// neither the key nor flagged is a miss after one read: with the table at
+// most 1/4 full, almost every unsuccessful lookup stops there, which keeps
+// the lanes of a warp in step.
+constexpr int32_t kEmpty = 0x7fffffff;
+constexpr uint32_t kDisplaced = 0x80000000u;
 
 __device__ __forceinline__ uint32_t hash_slot(uint32_t x, int log_slots) {
   return (x * 0x9E3779B1u) >> (32 - log_slots);
@@ -50,6 +71,14 @@ __device__ __forceinline__ int ceil_log2(uint32_t x) {
   return x <= 1 ? 0 : 32 - __clz(x - 1);
 }
 
+// Table size for a list of len entries: load <= 1/8 when it fits, else as
+// large as the capacity allows; -1 if even load 1/2 does not fit.
+__device__ __forceinline__ int table_log_slots(int32_t len, int capacity) {
+  int lg = ceil_log2(8u * (uint32_t)len);
+  while ((1 << lg) > capacity && (1 << lg) >= 4 * len) --lg;
+  return (1 << lg) <= capacity ? lg : -1;
+}
+
 __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
@@ -57,223 +86,336 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t x) {
 }
 
 struct WarpScratch {
-  int32_t start[32];  // flat start of each non-empty list of the chunk
+  int32_t start[32];  // flat start of each non-empty partner list of the chunk
   int32_t base[32];   // col index of flat position 0 of that list
-  int32_t v[32];      // the neighbour owning the list (per-vertex mode)
-  uint32_t vc[32];    // triangles found through that neighbour
+  int32_t l[32];      // the partner owning the list (per-vertex mode)
+  uint32_t lc[32];    // triangles found through that partner
 };
 
-// Empties the hash set tab[0..2^log_slots) (and its 16-bit counters in
-// per-vertex mode).  The calling group (a warp or the whole CTA) must
-// synchronise before filling it.
+// Empties tab[0..slots) and its 16-bit counters (one word per slot pair).
 template <bool PV>
-__device__ __forceinline__ void clear_table(int32_t *tab, uint32_t *cnt, int log_slots, int rank,
+__device__ __forceinline__ void clear_table(int32_t *tab, uint32_t *cnt, int slots, int rank,
                                             int group) {
-  const uint32_t slots = 1u << log_slots;
-  for (uint32_t i = rank; i < slots; i += group) tab[i] = -1;
+  for (int i = rank; i < slots; i += group) tab[i] = kEmpty;
   if (PV)
-    for (uint32_t i = rank; i < (slots + 1) / 2; i += group) cnt[i] = 0u;
+    for (int i = rank; i < slots / 2; i += group) cnt[i] = 0u;
 }
 
-// Inserts col[beg..beg+du) (distinct ids) into the emptied hash set.
+// Inserts col[beg..beg+len) (distinct ids) into the empty hash set.
 __device__ __forceinline__ void fill_table(const int32_t *__restrict__ col, int32_t beg,
-                                           int32_t du, int32_t *tab, int log_slots, int rank,
+                                           int32_t len, int32_t *tab, int log_slots, int rank,
                                            int group) {
   const uint32_t msk = (1u << log_slots) - 1u;
-  for (int32_t i = rank; i < du; i += group) {
+  for (int32_t i = rank; i < len; i += group) {
     const int32_t x = __ldg(col + beg + i);
-    uint32_t h = hash_slot((uint32_t)x, log_slots);
-    while (atomicCAS(&tab[h], -1, x) != -1) h = (h + 1u) & msk;
+    const uint32_t home = hash_slot((uint32_t)x, log_slots);
+    uint32_t h = home;
+    for (;;) {
+      const int32_t old = atomicCAS(&tab[h], kEmpty, x);
+      if (old == kEmpty) break;
+      if (h == home && !((uint32_t)old & kDisplaced)) atomicOr((unsigned *)&tab[h], kDisplaced);
+      h = (h + 1u) & msk;
+    }
   }
 }
 
-// Adds each slot's triangle count to t(w) for the w stored in that slot.
-__device__ __forceinline__ void flush_table(const int32_t *tab, const uint32_t *cnt,
-                                            int log_slots, int rank, int group, int64_t *t) {
-  const uint32_t slots = 1u << log_slots;
-  for (uint32_t i = rank; i < slots; i += group) {
-    const uint32_t c = (cnt[i >> 1] >> (16 * (i & 1))) & 0xffffu;
-    if (c) atomicAdd((unsigned long long *)&t[tab[i]], (unsigned long long)c);
+// Empties the first 2^log_slots slots again; in per-vertex mode with slot
+// counters, first adds each slot's count to t(w) of the w stored there.
+// Each thread owns whole counter words (two slots), so no barrier is needed
+// between reading and clearing.
+template <bool PV>
+__device__ __forceinline__ void drain_table(int32_t *tab, uint32_t *cnt, int log_slots,
+                                            bool flush, int rank, int group, int64_t *t) {
+  const int words = (1 << log_slots) / 2;
+  for (int i = rank; i < words; i += group) {
+    if (PV) {
+      const uint32_t c = cnt[i];
+      if (flush && c) {
+        if (c & 0xffffu)
+          atomicAdd((unsigned long long *)&t[tab[2 * i] & 0x7fffffff],
+                    (unsigned long long)(c & 0xffffu));
+        if (c >> 16)
+          atomicAdd((unsigned long long *)&t[tab[2 * i + 1] & 0x7fffffff],
+                    (unsigned long long)(c >> 16));
+      }
+      cnt[i] = 0u;
+    }
+    tab[2 * i] = kEmpty;
+    tab[2 * i + 1] = kEmpty;
   }
 }
 
-// Intersections of N+(u) (in the table, or in global memory when TABLE is
-// false) with N+(v) for the forward neighbours v = col[beg+c0 .. beg+c0+32).
-template <bool PV, bool TABLE>
+// Membership of x in the hash set; the slot holding x goes to *slot.
+__device__ __forceinline__ bool member(int32_t x, const int32_t *tab, int log_slots,
+                                       uint32_t *slot) {
+  uint32_t h = hash_slot((uint32_t)x, log_slots);
+  int32_t y = tab[h];
+  if ((y & 0x7fffffff) == x) {
+    *slot = h;
+    return true;
+  }
+  if (!((uint32_t)y & kDisplaced)) return false;
+  const uint32_t msk = (1u << log_slots) - 1u;
+  for (;;) {
+    h = (h + 1u) & msk;
+    y = tab[h];
+    if ((y & 0x7fffffff) == x) {
+      *slot = h;
+      return true;
+    }
+    if (y == kEmpty) return false;
+  }
+}
+
+// Streams N+(l) for the partners l = part[c0 .. c0+cs) (of np, cs <= 32)
+// through the hash set of the group's list.  The chunk's non-empty lists are concatenated into one flat
+// sequence; lane p takes flat positions p, p+32, ... and keeps a cursor on
+// the list that holds its position (lists average ~200 entries, so the
+// cursor rarely moves).  Matches are counted in registers; per partner they
+// reach shared memory only when a lane's cursor leaves that partner.
+// slot_cnt: per-vertex counts of w go to the 16-bit slot counters (valid
+// while a group has < 65536 partners); otherwise straight to t(w).
+template <bool PV>
 __device__ __forceinline__ void probe_chunk(const int32_t *__restrict__ off,
-                                            const int32_t *__restrict__ col, int32_t beg,
-                                            int32_t du, int32_t c0, const int32_t *tab,
-                                            uint32_t *cnt, int log_slots, WarpScratch &ws,
-                                            int64_t *t, uint64_t &found_total,
-                                            uint64_t &found_row) {
+                                            const int32_t *__restrict__ col,
+                                            const int32_t *__restrict__ part, int32_t np,
+                                            int32_t c0, int32_t cs, const int32_t *tab,
+                                            uint32_t *cnt, int log_slots, bool slot_cnt,
+                                            WarpScratch &ws, int64_t *t, uint64_t &found_total,
+                                            uint64_t &found_group) {
   const int lane = threadIdx.x & 31;
   const int32_t j = c0 + lane;
-  int32_t v = 0, vb = 0, dv = 0;
-  if (j < du) {
-    v = __ldg(col + beg + j);
-    vb = __ldg(off + v);
-    dv = __ldg(off + v + 1) - vb;
+  int32_t l = 0, lb = 0, dl = 0;
+  if (lane < cs && j < np) {
+    l = __ldg(part + j);
+    lb = __ldg(off + l);
+    dl = __ldg(off + l + 1) - lb;
   }
-  const uint32_t nonempty = __ballot_sync(kFull, dv > 0);
+  const uint32_t nonempty = __ballot_sync(kFull, dl > 0);
   if (nonempty == 0) return;
   const int k = __popc(nonempty);
   const int rank = __popc(nonempty & ((1u << lane) - 1u));
-  int32_t incl = dv;
+  int32_t incl = dl;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int32_t y = __shfl_up_sync(kFull, incl, o);
     if (lane >= o) incl += y;
   }
   const int32_t total = __shfl_sync(kFull, incl, 31);
-  if (dv > 0) {
-    ws.start[rank] = incl - dv;
-    ws.base[rank] = vb - (incl - dv);
+  if (dl > 0) {
+    ws.start[rank] = incl - dl;
+    ws.base[rank] = lb - (incl - dl);
     if (PV) {
-      ws.v[rank] = v;
-      ws.vc[rank] = 0u;
+      ws.l[rank] = l;
+      ws.lc[rank] = 0u;
     }
   }
   __syncwarp();
-  const int32_t my_start = lane < k ? ws.start[lane] : INT32_MAX;
-  const int32_t my_base = lane < k ? ws.base[lane] : 0;
-  const uint32_t msk = (1u << log_slots) - 1u;
-  for (int32_t w0 = 0; w0 < total; w0 += 32) {
-    const int r0 = __popc(__ballot_sync(kFull, my_start <= w0)) - 1;
-    const uint32_t bit =
-        (my_start > w0 && my_start < w0 + 32) ? (1u << (my_start - w0)) : 0u;
-    const uint32_t starts = __reduce_or_sync(kFull, bit);
-    const int r = r0 + __popc(starts & ((2u << lane) - 1u));
-    const int32_t base = __shfl_sync(kFull, my_base, r);
-    const int32_t p = w0 + lane;
-    if (p < total) {
-      const int32_t x = __ldg(col + base + p);
-      bool found = false;
-      uint32_t h = 0;
-      if (TABLE) {
-        h = hash_slot((uint32_t)x, log_slots);
-        for (;;) {
-          const int32_t y = tab[h];
-          if (y == x) { found = true; break; }
-          if (y < 0) break;
-          h = (h + 1u) & msk;
+  int r = 0;
+  int32_t base = ws.base[0];
+  int32_t next = k > 1 ? ws.start[1] : INT32_MAX;
+  uint32_t found = 0;     // matches of this lane in this chunk
+  uint32_t run = 0;       // matches of this lane for partner run_r
+  int run_r = 0;
+  for (int32_t p0 = lane; p0 < total; p0 += 32 * kWindows) {
+    int32_t x[kWindows];
+    int rq[kWindows];
+#pragma unroll
+    for (int q = 0; q < kWindows; ++q) {
+      const int32_t p = p0 + 32 * q;
+      x[q] = -1;
+      rq[q] = r;
+      if (p < total) {
+        while (p >= next) {
+          ++r;
+          base = ws.base[r];
+          next = r + 1 < k ? ws.start[r + 1] : INT32_MAX;
         }
-      } else {
-        int32_t lo = beg, hi = beg + du;
-        while (lo < hi) {
-          const int32_t mid = (lo + hi) >> 1;
-          if (__ldg(col + mid) < x) lo = mid + 1; else hi = mid;
-        }
-        found = lo < beg + du && __ldg(col + lo) == x;
+        x[q] = __ldg(col + base + p);
+        rq[q] = r;
       }
-      if (found) {
-        ++found_total;
-        if (PV) {
-          ++found_row;
-          atomicAdd(&ws.vc[r], 1u);
-          if (TABLE)
-            atomicAdd(&cnt[h >> 1], 1u << (16 * (h & 1u)));
-          else
-            atomicAdd((unsigned long long *)&t[x], 1ull);
+    }
+#pragma unroll
+    for (int q = 0; q < kWindows; ++q) {
+      if (x[q] < 0) continue;
+      uint32_t slot = 0;
+      const bool hit = member(x[q], tab, log_slots, &slot);
+      found += hit;
+      if (PV && hit) {
+        if (rq[q] != run_r) {
+          if (run) atomicAdd(&ws.lc[run_r], run);
+          run = 0;
+          run_r = rq[q];
         }
+        ++run;
+        if (slot_cnt)
+          atomicAdd(&cnt[slot >> 1], 1u << (16 * (slot & 1u)));
+        else
+          atomicAdd((unsigned long long *)&t[x[q]], 1ull);
       }
     }
   }
+  found_total += found;
   if (PV) {
+    found_group += found;
+    if (run) atomicAdd(&ws.lc[run_r], run);
     __syncwarp();
-    if (lane < k && ws.vc[lane])
-      atomicAdd((unsigned long long *)&t[ws.v[lane]], (unsigned long long)ws.vc[lane]);
+    if (lane < k && ws.lc[lane])
+      atomicAdd((unsigned long long *)&t[ws.l[lane]], (unsigned long long)ws.lc[lane]);
   }
   __syncwarp();
 }
 
-template <bool PV>
-__global__ void __launch_bounds__(kCountThreads)
-k_count(const int32_t *__restrict__ off, const int32_t *__restrict__ col,
-        const int32_t *__restrict__ warp_rows, const int32_t *__restrict__ cta_rows, Ctrl *ctrl,
-        int64_t *t) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  int32_t *tab = reinterpret_cast<int32_t *>(smem);                    // kCtaSlots
-  uint32_t *cnt = reinterpret_cast<uint32_t *>(smem + 4 * kCtaSlots);   // kCtaSlots/2 (PV)
-  __shared__ WarpScratch s_ws[kCountWarps];
-  __shared__ int32_t s_row;
-  __shared__ unsigned long long s_rowsum;
+struct CtaShared {
+  int32_t group;
+  uint32_t chunk;
+  unsigned long long groupsum;
+};
 
+// Groups of `list` counted by the whole CTA: N+(h) hashed once, warps claim
+// chunks of partners (32, or fewer when a group has few partners, so that
+// every warp gets about two).  A list too long for the table at load 1/2 is
+// hashed in equal segments, one after another, each probed by all partners:
+// N+(h) & N+(l) is the disjoint union of the segments' intersections.  The
+// table (SLOTS slots) is empty on entry and on exit.
+template <bool PV, int THREADS, int SLOTS>
+__device__ __forceinline__ void cta_groups(const int32_t *__restrict__ off,
+                                           const int32_t *__restrict__ col,
+                                           const int32_t *__restrict__ goff,
+                                           const int32_t *__restrict__ part,
+                                           const int32_t *__restrict__ list, uint32_t n_list,
+                                           uint32_t *cursor, int32_t *tab, uint32_t *cnt,
+                                           WarpScratch *s_ws, CtaShared &sh, int64_t *t,
+                                           uint64_t &found_total) {
+  constexpr int WARPS = THREADS / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t n_cta = ctrl->n_cta_rows, n_warp = ctrl->n_warp_rows;
-  uint64_t found_total = 0;
-
-  // ---- long rows: a whole CTA per row ----
   for (;;) {
     if (tid == 0) {
-      s_row = (int32_t)atomicAdd(&ctrl->next_cta_row, 1u);
-      s_rowsum = 0ull;
+      sh.group = (int32_t)atomicAdd(cursor, 1u);
+      sh.groupsum = 0ull;
     }
-    __syncthreads();
-    const uint32_t r = (uint32_t)s_row;
-    if (r >= n_cta) break;
-    const int32_t u = __ldg(cta_rows + r);
-    const int32_t beg = __ldg(off + u), du = __ldg(off + u + 1) - beg;
-    int log_slots = ceil_log2(4u * (uint32_t)du);
-    if ((1 << log_slots) > kCtaSlots) log_slots = ceil_log2(2u * (uint32_t)du);
-    const bool use_table = (1 << log_slots) <= kCtaSlots;
-    if (use_table) {
-      clear_table<PV>(tab, cnt, log_slots, tid, kCountThreads);
+    __syncthreads();  // also orders the previous group's drain before this fill
+    const uint32_t g = (uint32_t)sh.group;
+    if (g >= n_list) break;
+    // lists are filled in about ascending rank, and high ranks (high
+    // degrees) carry the most work: take them first to shorten the tail
+    const int32_t h = __ldg(list + (n_list - 1 - g));
+    const int32_t hb = __ldg(off + h), hd = __ldg(off + h + 1) - hb;
+    const int32_t pb = __ldg(goff + h), np = __ldg(goff + h + 1) - pb;
+    const int32_t nseg = (hd + SLOTS / 2 - 1) / (SLOTS / 2);
+    const int32_t seg_len = (hd + nseg - 1) / nseg;
+    const int log_slots = table_log_slots(seg_len, SLOTS);
+    const bool slot_cnt = np < 65536;
+    const int32_t cs = max(8, min(32, (np + 2 * WARPS - 1) / (2 * WARPS)));
+    uint64_t found_group = 0;
+    for (int32_t s0 = 0; s0 < hd; s0 += seg_len) {
+      const int32_t len = min(seg_len, hd - s0);
+      if (tid == 0) sh.chunk = 0u;
+      fill_table(col, hb + s0, len, tab, log_slots, tid, THREADS);
       __syncthreads();
-      fill_table(col, beg, du, tab, log_slots, tid, kCountThreads);
-    }
-    __syncthreads();
-    uint64_t found_row = 0;
-    for (int32_t c0 = warp * 32; c0 < du; c0 += kCountThreads) {
-      if (use_table)
-        probe_chunk<PV, true>(off, col, beg, du, c0, tab, cnt, log_slots, s_ws[warp], t,
-                              found_total, found_row);
-      else
-        probe_chunk<PV, false>(off, col, beg, du, c0, tab, cnt, 1, s_ws[warp], t, found_total,
-                               found_row);
+      for (;;) {
+        uint32_t c = 0;
+        if (lane == 0) c = atomicAdd(&sh.chunk, 1u);
+        c = __shfl_sync(kFull, c, 0);
+        const int32_t c0 = (int32_t)c * cs;
+        if (c0 >= np) break;
+        probe_chunk<PV>(off, col, part + pb, np, c0, cs, tab, cnt, log_slots, slot_cnt,
+                        s_ws[warp], t, found_total, found_group);
+      }
+      __syncthreads();
+      drain_table<PV>(tab, cnt, log_slots, slot_cnt, tid, THREADS, t);
+      if (s0 + seg_len < hd) __syncthreads();  // next segment refills the table
     }
     if (PV) {
-      found_row = warp_sum_u64(found_row);
-      if (lane == 0 && found_row) atomicAdd(&s_rowsum, (unsigned long long)found_row);
+      found_group = warp_sum_u64(found_group);
+      if (lane == 0 && found_group) atomicAdd(&sh.groupsum, (unsigned long long)found_group);
     }
     __syncthreads();
-    if (PV) {
-      if (tid == 0 && s_rowsum) atomicAdd((unsigned long long *)&t[u], s_rowsum);
-      if (use_table) flush_table(tab, cnt, log_slots, tid, kCountThreads, t);
-    }
-    __syncthreads();
+    if (PV && tid == 0 && sh.groupsum) atomicAdd((unsigned long long *)&t[h], sh.groupsum);
   }
+}
 
-  // ---- short rows: one warp per row, private table ----
-  int32_t *wtab = tab + warp * kWarpSlots;
-  uint32_t *wcnt = cnt + warp * (kWarpSlots / 2);
+// Groups of `list` counted by one warp each with a private table of
+// kWarpSlots slots (empty on entry and on exit).
+template <bool PV>
+__device__ __forceinline__ void warp_groups(const int32_t *__restrict__ off,
+                                            const int32_t *__restrict__ col,
+                                            const int32_t *__restrict__ goff,
+                                            const int32_t *__restrict__ part,
+                                            const int32_t *__restrict__ list, uint32_t n_list,
+                                            uint32_t *cursor, int32_t *wtab, uint32_t *wcnt,
+                                            WarpScratch &ws, int64_t *t, uint64_t &found_total) {
+  const int lane = threadIdx.x & 31;
   for (;;) {
-    uint32_t r0 = 0;
-    if (lane == 0) r0 = atomicAdd(&ctrl->next_warp_row, (uint32_t)kRowChunk);
-    r0 = __shfl_sync(kFull, r0, 0);
-    if (r0 >= n_warp) break;
-    const uint32_t r1 = min(r0 + (uint32_t)kRowChunk, n_warp);
-    for (uint32_t r = r0; r < r1; ++r) {
-      const int32_t u = __ldg(warp_rows + r);
-      const int32_t beg = __ldg(off + u), du = __ldg(off + u + 1) - beg;
-      const int log_slots = ceil_log2(4u * (uint32_t)du);
-      clear_table<PV>(wtab, wcnt, log_slots, lane, 32);
+    uint32_t g0 = 0;
+    if (lane == 0) g0 = atomicAdd(cursor, (uint32_t)kGroupChunk);
+    g0 = __shfl_sync(kFull, g0, 0);
+    if (g0 >= n_list) break;
+    const uint32_t g1 = min(g0 + (uint32_t)kGroupChunk, n_list);
+    for (uint32_t g = g0; g < g1; ++g) {
+      const int32_t h = __ldg(list + (n_list - 1 - g));  // heavy (high-rank) groups first
+      const int32_t hb = __ldg(off + h), hd = __ldg(off + h + 1) - hb;
+      const int32_t pb = __ldg(goff + h), np = __ldg(goff + h + 1) - pb;
+      const int log_slots = table_log_slots(hd, kWarpSlots);
+      const bool slot_cnt = np < 65536;
+      fill_table(col, hb, hd, wtab, log_slots, lane, 32);
       __syncwarp();
-      fill_table(col, beg, du, wtab, log_slots, lane, 32);
-      __syncwarp();
-      uint64_t found_row = 0;
-      for (int32_t c0 = 0; c0 < du; c0 += 32)
-        probe_chunk<PV, true>(off, col, beg, du, c0, wtab, wcnt, log_slots, s_ws[warp], t,
-                              found_total, found_row);
+      uint64_t found_group = 0;
+      for (int32_t c0 = 0; c0 < np; c0 += 32)
+        probe_chunk<PV>(off, col, part + pb, np, c0, 32, wtab, wcnt, log_slots, slot_cnt, ws, t,
+                        found_total, found_group);
       if (PV) {
-        found_row = warp_sum_u64(found_row);
-        if (lane == 0 && found_row) atomicAdd((unsigned long long *)&t[u], found_row);
-        __syncwarp();
-        flush_table(wtab, wcnt, log_slots, lane, 32, t);
+        found_group = warp_sum_u64(found_group);
+        if (lane == 0 && found_group) atomicAdd((unsigned long long *)&t[h], found_group);
       }
       __syncwarp();
+      drain_table<PV>(wtab, wcnt, log_slots, slot_cnt, lane, 32, t);
+      __syncwarp();
     }
   }
+}
 
+// Main counting kernel: CTA groups first (the heavy ones), then warp groups.
+template <bool PV>
+__global__ void __launch_bounds__(kMainThreads)
+k_count(const int32_t *__restrict__ off, const int32_t *__restrict__ col,
+        const int32_t *__restrict__ goff, const int32_t *__restrict__ part,
+        const int32_t *__restrict__ warp_list, const int32_t *__restrict__ cta_list, Ctrl *ctrl,
+        int64_t *t) {
+  __shared__ int32_t s_tab[kMainSlots];
+  __shared__ uint32_t s_cnt[PV ? kMainSlots / 2 : 1];
+  __shared__ WarpScratch s_ws[kMainWarps];
+  __shared__ CtaShared s_sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  clear_table<PV>(s_tab, s_cnt, kMainSlots, tid, kMainThreads);
+  uint64_t found_total = 0;
+  cta_groups<PV, kMainThreads, kMainSlots>(off, col, goff, part, cta_list, ctrl->n_cta_groups,
+                                           &ctrl->next_cta_group, s_tab, s_cnt, s_ws, s_sh, t,
+                                           found_total);
+  warp_groups<PV>(off, col, goff, part, warp_list, ctrl->n_warp_groups, &ctrl->next_warp_group,
+                  s_tab + warp * kWarpSlots, s_cnt + warp * (kWarpSlots / 2), s_ws[warp], t,
+                  found_total);
+  found_total = warp_sum_u64(found_total);
+  if (lane == 0 && found_total) atomicAdd(&ctrl->total, (unsigned long long)found_total);
+}
+
+// Groups whose hashed list is longer than kCtaMaxRow (rare).
+template <bool PV>
+__global__ void __launch_bounds__(kBigThreads)
+k_count_big(const int32_t *__restrict__ off, const int32_t *__restrict__ col,
+            const int32_t *__restrict__ goff, const int32_t *__restrict__ part,
+            const int32_t *__restrict__ big_list, Ctrl *ctrl, int64_t *t) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  int32_t *tab = reinterpret_cast<int32_t *>(smem);
+  uint32_t *cnt = reinterpret_cast<uint32_t *>(smem + 4 * kBigSlots);
+  __shared__ WarpScratch s_ws[kBigWarps];
+  __shared__ CtaShared s_sh;
+  const int tid = threadIdx.x, lane = tid & 31;
+  clear_table<PV>(tab, cnt, kBigSlots, tid, kBigThreads);
+  uint64_t found_total = 0;
+  cta_groups<PV, kBigThreads, kBigSlots>(off, col, goff, part, big_list, ctrl->n_big_groups,
+                                         &ctrl->next_big_group, tab, cnt, s_ws, s_sh, t,
+                                         found_total);
   found_total = warp_sum_u64(found_total);
   if (lane == 0 && found_total) atomicAdd(&ctrl->total, (unsigned long long)found_total);
 }
@@ -307,6 +449,15 @@ k_clustering(const int64_t *__restrict__ t, const int32_t *__restrict__ deg, int
   }
 }
 
+// Per-vertex counts from rank space back to the caller's vertex ids.
+__global__ void __launch_bounds__(kClusterThreads)
+k_gather_counts(const int64_t *__restrict__ t_rank, const int32_t *__restrict__ rank, int32_t n,
+                int64_t *__restrict__ t_out) {
+  const uint32_t stride = gridDim.x * kClusterThreads;
+  for (uint32_t v = blockIdx.x * kClusterThreads + threadIdx.x; v < (uint32_t)n; v += stride)
+    t_out[v] = __ldg(t_rank + __ldg(rank + v));
+}
+
 // transitivity = 3T / wedges with T = (sum t) / 3: one float64 division.
 __global__ void k_transitivity(const unsigned long long *sums, double *out) {
   const unsigned long long three_t = sums[0];  // sum of t(v) is exactly 3T
@@ -316,38 +467,70 @@ __global__ void k_transitivity(const unsigned long long *sums, double *out) {
 
 constexpr int kMaxDevices = 64;
 
-}  // namespace
+struct CountGrid {
+  int main_blocks, big_blocks;
+};
 
-cudaError_t launch_count(const int32_t *off, const int32_t *col, const int32_t *warp_rows,
-                         const int32_t *cta_rows, Ctrl *ctrl, int64_t *t, cudaStream_t st) {
-  const bool pv = t != nullptr;
-  const size_t smem = (size_t)4 * kCtaSlots + (pv ? (size_t)2 * kCtaSlots : 0);
-  static int grid_cache[kMaxDevices][2];
+cudaError_t count_grid(bool pv, CountGrid *out) {
+  static CountGrid cache[kMaxDevices][2];
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  int grid = (dev >= 0 && dev < kMaxDevices) ? grid_cache[dev][pv] : 0;
-  if (grid == 0) {
-    e = pv ? cudaFuncSetAttribute(k_count<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)
-           : cudaFuncSetAttribute(k_count<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem);
-    if (e != cudaSuccess) return e;
-    int sms = 0, per_sm = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (pv)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count<true>, kCountThreads, smem);
-    else
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count<false>, kCountThreads,
-                                                        smem);
-    if (e != cudaSuccess) return e;
-    grid = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-    if (dev >= 0 && dev < kMaxDevices) grid_cache[dev][pv] = grid;
+  if (dev >= 0 && dev < kMaxDevices && cache[dev][pv].main_blocks) {
+    *out = cache[dev][pv];
+    return cudaSuccess;
   }
-  if (pv)
-    k_count<true><<<grid, kCountThreads, smem, st>>>(off, col, warp_rows, cta_rows, ctrl, t);
-  else
-    k_count<false><<<grid, kCountThreads, smem, st>>>(off, col, warp_rows, cta_rows, ctrl, t);
+  const size_t big_smem = (size_t)4 * kBigSlots + (pv ? (size_t)2 * kBigSlots : 0);
+  e = pv ? cudaFuncSetAttribute(k_count_big<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)big_smem)
+         : cudaFuncSetAttribute(k_count_big<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)big_smem);
+  if (e != cudaSuccess) return e;
+  int sms = 0, per_main = 0, per_big = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (pv) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_main, k_count<true>, kMainThreads, 0);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_big, k_count_big<true>, kBigThreads,
+                                                        big_smem);
+  } else {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_main, k_count<false>, kMainThreads, 0);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_big, k_count_big<false>,
+                                                        kBigThreads, big_smem);
+  }
+  if (e != cudaSuccess) return e;
+  sms = sms > 0 ? sms : 1;
+  CountGrid g{sms * (per_main > 0 ? per_main : 1), sms * (per_big > 0 ? per_big : 1)};
+  if (dev >= 0 && dev < kMaxDevices) cache[dev][pv] = g;
+  *out = g;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_count(const int32_t *off, const int32_t *col, const int32_t *goff,
+                         const int32_t *part, const int32_t *warp_groups,
+                         const int32_t *cta_groups, const int32_t *big_groups, Ctrl *ctrl,
+                         int64_t *t, cudaStream_t st) {
+  const bool pv = t != nullptr;
+  CountGrid g;
+  cudaError_t e = count_grid(pv, &g);
+  if (e != cudaSuccess) return e;
+  const size_t big_smem = (size_t)4 * kBigSlots + (pv ? (size_t)2 * kBigSlots : 0);
+  // the rare long lists first, on their own wide CTAs; usually an empty list
+  if (pv) {
+    k_count_big<true><<<g.big_blocks, kBigThreads, big_smem, st>>>(off, col, goff, part,
+                                                                   big_groups, ctrl, t);
+    k_count<true><<<g.main_blocks, kMainThreads, 0, st>>>(off, col, goff, part, warp_groups,
+                                                          cta_groups, ctrl, t);
+  } else {
+    k_count_big<false><<<g.big_blocks, kBigThreads, big_smem, st>>>(off, col, goff, part,
+                                                                    big_groups, ctrl, t);
+    k_count<false><<<g.main_blocks, kMainThreads, 0, st>>>(off, col, goff, part, warp_groups,
+                                                           cta_groups, ctrl, t);
+  }
+  note_launch();
   note_launch();
   return cudaGetLastError();
 }
@@ -360,6 +543,17 @@ void launch_clustering(const int64_t *t, const int32_t *deg, int32_t n, double *
   const uint32_t want = ((uint32_t)n + kClusterThreads * 4 - 1) / (kClusterThreads * 4);
   const uint32_t grid = max(1u, min(want, (uint32_t)(sms > 0 ? sms : 1) * 8));
   k_clustering<<<grid, kClusterThreads, 0, st>>>(t, deg, n, cc, sums);
+  note_launch();
+}
+
+void launch_gather_counts(const int64_t *t_rank, const int32_t *rank, int32_t n, int64_t *t_out,
+                          cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint32_t want = ((uint32_t)n + kClusterThreads * 4 - 1) / (kClusterThreads * 4);
+  const uint32_t grid = max(1u, min(want, (uint32_t)(sms > 0 ? sms : 1) * 8));
+  k_gather_counts<<<grid, kClusterThreads, 0, st>>>(t_rank, rank, n, t_out);
   note_launch();
 }
 

@@ -16,9 +16,12 @@
 //                  scatter writes runs of equal digits contiguously).
 //   unique+degree  after sort 1, equal keys are adjacent: the first of each
 //                  run is a distinct edge; degree histogram of those.
+//   rank keys      the (degree, id) order of Sec. II-B as a permutation:
+//                  a stable radix sort of deg(v) << b | v whose last pass
+//                  scatters rank[v]; the rest of the pipeline runs on ranks.
 //   orient         compact the distinct edges (tile scan + look-back) and
-//                  emit each as owner << b | neighbour, the owner being the
-//                  endpoint lower in (degree, id) order -- marking and
+//                  emit each as owner << b | neighbour in rank space, the
+//                  owner being the endpoint of lower rank -- marking and
 //                  removing backward edges of Sec. III-B in one pass; also
 //                  the out-degree histogram and the digit histograms of the
 //                  owner field.
@@ -30,8 +33,9 @@
 //                  each list sorted by neighbour id.  The last pass writes
 //                  only the neighbour (the column array: the "unzip").
 //   offsets        exclusive scan of the out-degrees = node array (CSR
-//                  offsets); rows with >= 2 entries are binned for counting
-//                  (a row with one entry cannot close a triangle).
+//                  offsets).  The last sort pass also wrote the row of
+//                  every entry, so (row[], col[]) is the paper's unzipped
+//                  structure-of-arrays edge array.
 #include <cstdio>
 
 #include "tc_common.cuh"
@@ -172,12 +176,12 @@ k_canon(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, uint32
 // ---------------------------------------------------------------------------
 // one LSD radix pass (8-bit digit at `shift`), onesweep style
 // ---------------------------------------------------------------------------
-template <bool OUT_COL>
+template <int MODE>
 __global__ void __launch_bounds__(kSortThreads)
 k_radix_pass(const uint64_t *__restrict__ in, void *__restrict__ out, uint32_t n_keys_bound,
              const uint32_t *__restrict__ n_keys_dev, int shift, uint32_t col_mask,
-             const uint32_t *__restrict__ hist, unsigned long long *__restrict__ status,
-             uint32_t *ticket, Ctrl *ctrl) {
+             uint32_t *__restrict__ row_out, int owner_shift, const uint32_t *__restrict__ hist,
+             unsigned long long *__restrict__ status, uint32_t *ticket, Ctrl *ctrl) {
   constexpr int WARPS = kSortThreads / 32, KPT = kSortKeysPerThread, TILE = kSortTile;
   __shared__ uint64_t s_keys[TILE];
   __shared__ uint32_t s_whist[WARPS][256];
@@ -287,10 +291,14 @@ k_radix_pass(const uint64_t *__restrict__ in, void *__restrict__ out, uint32_t n
   for (uint32_t i = tid; i < tile_n; i += kSortThreads) {
     const uint64_t key = s_keys[i];
     const uint32_t pos = s_gbase[(uint32_t)(key >> shift) & 255u] + i;
-    if (OUT_COL)
+    if (MODE == kOutColRow) {
       ((uint32_t *)out)[pos] = (uint32_t)key & col_mask;
-    else
+      row_out[pos] = (uint32_t)(key >> owner_shift);
+    } else if (MODE == kOutRank) {
+      ((uint32_t *)out)[(uint32_t)key & col_mask] = pos;
+    } else {
       ((uint64_t *)out)[pos] = key;
+    }
   }
 }
 
@@ -314,11 +322,36 @@ k_unique_degree(const uint64_t *__restrict__ keys, uint32_t m_in, int b, int32_t
 }
 
 // ---------------------------------------------------------------------------
-// orient: compact distinct edges, orient by (degree, id), out-degrees
+// rank keys: the order of Sec. II-B as a permutation.  Vertex v gets the key
+// deg(v) << b | v; a stable LSD sort over the degree bits leaves the keys in
+// (degree, id) order, and its last pass scatters rank[v] = position.  From
+// here on the pipeline works on ranks: an edge is oriented from its lower
+// rank, and the high-degree vertices, which fill most forward lists, get
+// the highest, adjacent ids.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kCanonThreads)
+k_rank_keys(const int32_t *__restrict__ deg, int32_t n, int b, int passes,
+            uint64_t *__restrict__ vkeys, uint32_t *__restrict__ hist) {
+  __shared__ uint32_t sh[kMaxRankPasses * 256];
+  for (int i = threadIdx.x; i < passes * 256; i += kCanonThreads) sh[i] = 0;
+  __syncthreads();
+  const uint32_t stride = gridDim.x * kCanonThreads;
+  for (uint32_t v = blockIdx.x * kCanonThreads + threadIdx.x; v < (uint32_t)n; v += stride) {
+    const uint32_t d = (uint32_t)__ldg(deg + v);
+    vkeys[v] = ((uint64_t)d << b) | v;
+    for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * 256 + ((d >> (8 * p)) & 255u)], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * 256; i += kCanonThreads)
+    if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// ---------------------------------------------------------------------------
+// orient: compact distinct edges, orient by rank (= (degree, id) order)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kOrientThreads)
 k_orient(const uint64_t *__restrict__ keys, uint32_t m_in, int b,
-         const int32_t *__restrict__ deg, uint64_t *__restrict__ okeys, int32_t *outdeg,
+         const int32_t *__restrict__ rank, uint64_t *__restrict__ okeys, int32_t *outdeg,
          uint32_t *__restrict__ hist2, int passes2, unsigned long long *status, Ctrl *ctrl) {
   constexpr int KPT = kOrientKeysPerThread, TILE = kOrientTile;
   __shared__ uint32_t s_scratch[32];
@@ -362,10 +395,8 @@ k_orient(const uint64_t *__restrict__ keys, uint32_t m_in, int b,
   for (int i = 0; i < KPT; ++i) {
     if (!((flags >> i) & 1u)) continue;
     const uint32_t a = (uint32_t)(k[i] >> b), c = (uint32_t)(k[i] & mask);
-    const int32_t da = __ldg(deg + a), dc = __ldg(deg + c);
-    // a < c always (canonical key); so on equal degree the lower id owns
-    const bool a_first = (da < dc) || (da == dc);
-    const uint32_t owner = a_first ? a : c, nbr = a_first ? c : a;
+    const uint32_t ra = (uint32_t)__ldg(rank + a), rc = (uint32_t)__ldg(rank + c);
+    const uint32_t owner = min(ra, rc), nbr = max(ra, rc);
     okeys[pos++] = ((uint64_t)owner << b) | nbr;
     atomicAdd(&outdeg[owner], 1);
     for (int p = 0; p < passes2; ++p) atomicAdd(&s_hist[p * 256 + ((owner >> (8 * p)) & 255u)], 1u);
@@ -376,17 +407,23 @@ k_orient(const uint64_t *__restrict__ keys, uint32_t m_in, int b,
 }
 
 // ---------------------------------------------------------------------------
-// offsets: exclusive scan of out-degrees (node array) + row binning
+// offsets: exclusive scan of per-vertex counts.  Used for the node array
+// (counts = out-degrees) and for the partner groups of the counting phase
+// (counts = partners per group), where it also bins the groups that can
+// hold a triangle (>= 1 partner, >= 2 entries in the hashed list) by the
+// length of the hashed list: one warp, or a whole CTA.
 // ---------------------------------------------------------------------------
+template <bool GROUPS>
 __global__ void __launch_bounds__(kScanThreads)
-k_offsets(const int32_t *__restrict__ outdeg, int32_t n, int32_t *__restrict__ off,
-          int32_t *__restrict__ warp_rows, int32_t *__restrict__ cta_rows,
-          unsigned long long *status, Ctrl *ctrl) {
+k_offsets(const int32_t *__restrict__ counts, int32_t n, int32_t *__restrict__ off,
+          const int32_t *__restrict__ row_off, int32_t *__restrict__ warp_list,
+          int32_t *__restrict__ cta_list, int32_t *__restrict__ big_list,
+          unsigned long long *status, uint32_t *ticket, Ctrl *ctrl) {
   constexpr int IPT = kScanItemsPerThread, TILE = kScanTile;
   __shared__ uint32_t s_scratch[32];
   __shared__ uint32_t s_tile, s_excl;
   const int tid = threadIdx.x, lane = tid & 31;
-  if (tid == 0) s_tile = atomicAdd(&ctrl->tile_ticket[kTicketScan], 1u);
+  if (tid == 0) s_tile = atomicAdd(ticket, 1u);
   __syncthreads();
   const uint32_t tile = s_tile;
   const uint32_t items = (uint32_t)n + 1;  // off[0..n]
@@ -398,7 +435,7 @@ k_offsets(const int32_t *__restrict__ outdeg, int32_t n, int32_t *__restrict__ o
 #pragma unroll
   for (int i = 0; i < IPT; ++i) {
     const uint32_t v = first + i;
-    d[i] = v < (uint32_t)n ? __ldg(outdeg + v) : 0;
+    d[i] = v < (uint32_t)n ? __ldg(counts + v) : 0;
     sum += (uint32_t)d[i];
   }
   uint32_t tile_sum;
@@ -412,23 +449,34 @@ k_offsets(const int32_t *__restrict__ outdeg, int32_t n, int32_t *__restrict__ o
     if (v < items) off[v] = (int32_t)run;
     run += (uint32_t)d[i];
   }
-  // bin rows: one appending atomic per warp and list
+  if constexpr (GROUPS) {
+  // bin groups: one appending atomic per warp and list
 #pragma unroll
   for (int i = 0; i < IPT; ++i) {
     const uint32_t v = first + i;
-    const bool is_warp = v < (uint32_t)n && d[i] >= 2 && d[i] <= kWarpMaxRow;
-    const bool is_cta = v < (uint32_t)n && d[i] > kWarpMaxRow;
+    int32_t dh = 0;
+    if (v < (uint32_t)n && d[i] > 0) dh = __ldg(row_off + v + 1) - __ldg(row_off + v);
+    // a warp takes a group only if both its list and its partner count are
+    // short: one warp streaming thousands of partners would finish last
+    const bool is_warp = dh >= 2 && dh <= kWarpMaxRow && d[i] <= kWarpMaxPartners;
+    const bool is_cta = dh >= 2 && dh <= kCtaMaxRow && !is_warp;
+    const bool is_big = dh > kCtaMaxRow;
     const uint32_t bw = __ballot_sync(kFull, is_warp), bc = __ballot_sync(kFull, is_cta);
-    uint32_t basew = 0, basec = 0;
+    const uint32_t bb = __ballot_sync(kFull, is_big);
+    uint32_t basew = 0, basec = 0, baseb = 0;
     if (lane == 0) {
-      if (bw) basew = atomicAdd(&ctrl->n_warp_rows, (uint32_t)__popc(bw));
-      if (bc) basec = atomicAdd(&ctrl->n_cta_rows, (uint32_t)__popc(bc));
+      if (bw) basew = atomicAdd(&ctrl->n_warp_groups, (uint32_t)__popc(bw));
+      if (bc) basec = atomicAdd(&ctrl->n_cta_groups, (uint32_t)__popc(bc));
+      if (bb) baseb = atomicAdd(&ctrl->n_big_groups, (uint32_t)__popc(bb));
     }
     basew = __shfl_sync(kFull, basew, 0);
     basec = __shfl_sync(kFull, basec, 0);
+    baseb = __shfl_sync(kFull, baseb, 0);
     const uint32_t lt = (1u << lane) - 1u;
-    if (is_warp) warp_rows[basew + __popc(bw & lt)] = (int32_t)v;
-    if (is_cta) cta_rows[basec + __popc(bc & lt)] = (int32_t)v;
+    if (is_warp) warp_list[basew + __popc(bw & lt)] = (int32_t)v;
+    if (is_cta) cta_list[basec + __popc(bc & lt)] = (int32_t)v;
+    if (is_big) big_list[baseb + __popc(bb & lt)] = (int32_t)v;
+  }
   }
 }
 
@@ -454,17 +502,32 @@ void launch_canon(const int32_t *src, const int32_t *dst, uint32_t m_in, int32_t
   note_launch();
 }
 
-void launch_radix_pass(const uint64_t *in, void *out, bool out_col, uint32_t n_keys_bound,
-                       const uint32_t *n_keys_dev, int shift, uint32_t col_mask,
-                       const uint32_t *hist, unsigned long long *status, uint32_t *ticket,
-                       Ctrl *ctrl, cudaStream_t st) {
+void launch_radix_pass(const uint64_t *in, void *out, RadixOut mode, uint32_t *row_out,
+                       uint32_t n_keys_bound, const uint32_t *n_keys_dev, int shift,
+                       uint32_t col_mask, int owner_shift, const uint32_t *hist,
+                       unsigned long long *status, uint32_t *ticket, Ctrl *ctrl,
+                       cudaStream_t st) {
   const uint32_t grid = max(1u, (n_keys_bound + kSortTile - 1) / kSortTile);
-  if (out_col)
-    k_radix_pass<true><<<grid, kSortThreads, 0, st>>>(in, out, n_keys_bound, n_keys_dev, shift,
-                                                      col_mask, hist, status, ticket, ctrl);
+  if (mode == kOutColRow)
+    k_radix_pass<kOutColRow><<<grid, kSortThreads, 0, st>>>(
+        in, out, n_keys_bound, n_keys_dev, shift, col_mask, row_out, owner_shift, hist, status,
+        ticket, ctrl);
+  else if (mode == kOutRank)
+    k_radix_pass<kOutRank><<<grid, kSortThreads, 0, st>>>(in, out, n_keys_bound, n_keys_dev,
+                                                          shift, col_mask, nullptr, 0, hist,
+                                                          status, ticket, ctrl);
   else
-    k_radix_pass<false><<<grid, kSortThreads, 0, st>>>(in, out, n_keys_bound, n_keys_dev, shift,
-                                                       col_mask, hist, status, ticket, ctrl);
+    k_radix_pass<kOutKeys><<<grid, kSortThreads, 0, st>>>(in, out, n_keys_bound, n_keys_dev,
+                                                          shift, col_mask, nullptr, 0, hist,
+                                                          status, ticket, ctrl);
+  note_launch();
+}
+
+void launch_rank_keys(const int32_t *deg, int32_t n, int b, int passes, uint64_t *vkeys,
+                      uint32_t *hist, cudaStream_t st) {
+  const uint32_t want = ((uint32_t)n + kCanonThreads * 8 - 1) / (kCanonThreads * 8);
+  const uint32_t grid = max(1u, min(want, (uint32_t)num_sms() * 8));
+  k_rank_keys<<<grid, kCanonThreads, 0, st>>>(deg, n, b, passes, vkeys, hist);
   note_launch();
 }
 
@@ -476,20 +539,26 @@ void launch_unique_degree(const uint64_t *keys, uint32_t m_in, int b, int32_t *d
   note_launch();
 }
 
-void launch_orient(const uint64_t *keys, uint32_t m_in, int b, const int32_t *deg,
+void launch_orient(const uint64_t *keys, uint32_t m_in, int b, const int32_t *rank,
                    uint64_t *okeys, int32_t *outdeg, uint32_t *hist2, int passes2,
                    unsigned long long *status, Ctrl *ctrl, cudaStream_t st) {
   const uint32_t grid = max(1u, (m_in + kOrientTile - 1) / kOrientTile);
-  k_orient<<<grid, kOrientThreads, 0, st>>>(keys, m_in, b, deg, okeys, outdeg, hist2, passes2,
+  k_orient<<<grid, kOrientThreads, 0, st>>>(keys, m_in, b, rank, okeys, outdeg, hist2, passes2,
                                             status, ctrl);
   note_launch();
 }
 
-void launch_offsets(const int32_t *outdeg, int32_t n, int32_t *off, int32_t *warp_rows,
-                    int32_t *cta_rows, unsigned long long *status, Ctrl *ctrl, cudaStream_t st) {
+void launch_offsets(const int32_t *counts, int32_t n, int32_t *off, const int32_t *row_off,
+                    int32_t *warp_list, int32_t *cta_list, int32_t *big_list,
+                    unsigned long long *status, uint32_t *ticket, Ctrl *ctrl, cudaStream_t st) {
   const uint32_t items = (uint32_t)n + 1;
   const uint32_t grid = max(1u, (items + kScanTile - 1) / kScanTile);
-  k_offsets<<<grid, kScanThreads, 0, st>>>(outdeg, n, off, warp_rows, cta_rows, status, ctrl);
+  if (row_off)
+    k_offsets<true><<<grid, kScanThreads, 0, st>>>(counts, n, off, row_off, warp_list, cta_list,
+                                                   big_list, status, ticket, ctrl);
+  else
+    k_offsets<false><<<grid, kScanThreads, 0, st>>>(counts, n, off, nullptr, nullptr, nullptr,
+                                                    nullptr, status, ticket, ctrl);
   note_launch();
 }
 

@@ -54,8 +54,8 @@ std::mutex g_prof_mu;
 double g_prof_ms[TC_NUM_PHASES];
 uint64_t g_prof_launches[TC_NUM_PHASES];
 
-const char *const kPhaseNames[TC_NUM_PHASES] = {"canon", "sort1", "degree", "orient",
-                                                "sort2", "offsets", "count"};
+const char *const kPhaseNames[TC_NUM_PHASES] = {"canon", "sort1",   "degree", "rank", "orient",
+                                                "sort2", "offsets", "groups", "count"};
 
 // Events around each phase of one call, folded into the global totals after
 // the call has synchronised its stream.
@@ -149,29 +149,46 @@ tc_status run_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t
   PhaseTimer pt(st, profile);
   const uint32_t m = (uint32_t)m_in;
   const int b = id_bits(n);
-  const int passes1 = (2 * b + 7) / 8, passes2 = (b + 7) / 8;
+  // radix passes: undirected keys (2b bits), rank keys (degree bits < 2^b),
+  // oriented keys (owner bits)
+  const int passes1 = (2 * b + 7) / 8, passes_r = (b + 7) / 8, passes2 = (b + 7) / 8;
   Ctrl *ctrl = reinterpret_cast<Ctrl *>(ws + L.ctrl);
   uint32_t *hist = reinterpret_cast<uint32_t *>(ws + L.hist);
   auto *st_sort = reinterpret_cast<unsigned long long *>(ws + L.st_sort);
   auto *st_orient = reinterpret_cast<unsigned long long *>(ws + L.st_orient);
   auto *st_scan = reinterpret_cast<unsigned long long *>(ws + L.st_scan);
+  auto *st_scan2 = reinterpret_cast<unsigned long long *>(ws + L.st_scan2);
   uint64_t *keys_a = reinterpret_cast<uint64_t *>(ws + L.keys_a);
   uint64_t *keys_b = reinterpret_cast<uint64_t *>(ws + L.keys_b);
+  uint64_t *vkeys_a = reinterpret_cast<uint64_t *>(ws + L.vkeys_a);
+  uint64_t *vkeys_b = reinterpret_cast<uint64_t *>(ws + L.vkeys_b);
   int32_t *deg = deg_out ? deg_out : reinterpret_cast<int32_t *>(ws + L.deg);
   int32_t *outdeg = reinterpret_cast<int32_t *>(ws + L.outdeg);
   int32_t *off = reinterpret_cast<int32_t *>(ws + L.off);
-  int32_t *warp_rows = reinterpret_cast<int32_t *>(ws + L.warp_rows);
-  int32_t *cta_rows = reinterpret_cast<int32_t *>(ws + L.cta_rows);
+  int32_t *goff = reinterpret_cast<int32_t *>(ws + L.goff);
+  int32_t *warp_groups = reinterpret_cast<int32_t *>(ws + L.warp_groups);
+  int32_t *cta_groups = reinterpret_cast<int32_t *>(ws + L.cta_groups);
+  int32_t *big_groups = reinterpret_cast<int32_t *>(ws + L.big_groups);
+  int32_t *rank = reinterpret_cast<int32_t *>(ws + L.rank);
+  int64_t *t_rank = t_out ? reinterpret_cast<int64_t *>(ws + L.t_rank) : nullptr;
   const size_t words = L.st_sort_words_per_pass;
+  // look-back status and tile tickets: one slot per radix pass, in the order
+  // the passes run (sort 1, rank sort, sort 2)
+  int slot = 0;
+  auto next_pass = [&](unsigned long long **status, uint32_t **ticket) {
+    *status = st_sort + words * (size_t)slot;
+    *ticket = &ctrl->tile_ticket[kTicketSort + slot];
+    ++slot;
+  };
 
   // zero the control block, histograms and the look-back status words in use
   TC_CUDA(cudaMemsetAsync(ws, 0, L.st_sort + sizeof(unsigned long long) * words *
-                                                  (size_t)(passes1 + passes2), st),
+                                                  (size_t)(passes1 + passes_r + passes2), st),
           "memset control");
   TC_CUDA(cudaMemsetAsync(ws + L.st_orient, 0, L.keys_a - L.st_orient, st), "memset status");
   TC_CUDA(cudaMemsetAsync(deg, 0, sizeof(int32_t) * (size_t)n, st), "memset deg");
   TC_CUDA(cudaMemsetAsync(outdeg, 0, sizeof(int32_t) * (size_t)n, st), "memset outdeg");
-  if (t_out) TC_CUDA(cudaMemsetAsync(t_out, 0, sizeof(int64_t) * (size_t)n, st), "memset t");
+  if (t_rank) TC_CUDA(cudaMemsetAsync(t_rank, 0, sizeof(int64_t) * (size_t)n, st), "memset t");
 
   pt.start(TC_PHASE_CANON);
   launch_canon(src, dst, m, n, b, passes1, keys_a, hist, ctrl, st);
@@ -180,8 +197,11 @@ tc_status run_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t
   pt.start(TC_PHASE_SORT1);
   uint64_t *in = keys_a, *out = keys_b;
   for (int p = 0; p < passes1; ++p) {
-    launch_radix_pass(in, out, false, m, nullptr, 8 * p, 0u, hist + 256 * p,
-                      st_sort + words * p, &ctrl->tile_ticket[kTicketSort + p], ctrl, st);
+    unsigned long long *status;
+    uint32_t *ticket;
+    next_pass(&status, &ticket);
+    launch_radix_pass(in, out, kOutKeys, nullptr, m, nullptr, 8 * p, 0u, 0, hist + 256 * p,
+                      status, ticket, ctrl, st);
     uint64_t *x = in;
     in = out;
     out = x;
@@ -192,9 +212,30 @@ tc_status run_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t
   launch_unique_degree(in, m, b, deg, st);
   pt.stop(TC_PHASE_DEGREE);
 
+  // rank of every vertex in the (degree, id) order
+  pt.start(TC_PHASE_RANK);
+  const uint32_t id_mask = (uint32_t)((1ull << b) - 1);
+  launch_rank_keys(deg, n, b, passes_r, vkeys_a, hist + 256 * kRankSlot, st);
+  {
+    uint64_t *vin = vkeys_a, *vout = vkeys_b;
+    for (int p = 0; p < passes_r; ++p) {
+      unsigned long long *status;
+      uint32_t *ticket;
+      next_pass(&status, &ticket);
+      const bool last = p == passes_r - 1;
+      launch_radix_pass(vin, last ? (void *)rank : (void *)vout, last ? kOutRank : kOutKeys,
+                        nullptr, (uint32_t)n, nullptr, b + 8 * p, id_mask, 0,
+                        hist + 256 * (kRankSlot + p), status, ticket, ctrl, st);
+      uint64_t *x = vin;
+      vin = vout;
+      vout = x;
+    }
+  }
+  pt.stop(TC_PHASE_RANK);
+
   pt.start(TC_PHASE_ORIENT);
-  launch_orient(in, m, b, deg, out, outdeg, hist + 256 * kMaxSort1Passes, passes2, st_orient,
-                ctrl, st);
+  launch_orient(in, m, b, rank, out, outdeg, hist + 256 * kSort2Slot, passes2, st_orient, ctrl,
+                st);
   pt.stop(TC_PHASE_ORIENT);
 
   pt.start(TC_PHASE_SORT2);
@@ -203,12 +244,16 @@ tc_status run_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t
     in = out;
     out = x;
   }
-  const uint32_t col_mask = (uint32_t)((1ull << b) - 1);
+  // the last pass writes the column array to `out` (first 4m bytes) and the
+  // row array to the second half of the same buffer
   for (int p = 0; p < passes2; ++p) {
+    unsigned long long *status;
+    uint32_t *ticket;
+    next_pass(&status, &ticket);
     const bool last = p == passes2 - 1;
-    launch_radix_pass(in, out, last, m, &ctrl->m, b + 8 * p, col_mask,
-                      hist + 256 * (kMaxSort1Passes + p), st_sort + words * (passes1 + p),
-                      &ctrl->tile_ticket[kTicketSort + passes1 + p], ctrl, st);
+    uint32_t *row_target = last ? reinterpret_cast<uint32_t *>(out) + m : nullptr;
+    launch_radix_pass(in, out, last ? kOutColRow : kOutKeys, row_target, m, &ctrl->m, b + 8 * p,
+                      id_mask, b, hist + 256 * (kSort2Slot + p), status, ticket, ctrl, st);
     if (!last) {
       uint64_t *x = in;
       in = out;
@@ -216,14 +261,30 @@ tc_status run_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t
     }
   }
   const int32_t *col = reinterpret_cast<const int32_t *>(out);
+  const int32_t *row = reinterpret_cast<const int32_t *>(out) + m;
+  int32_t *part = reinterpret_cast<int32_t *>(in);  // the last pass's input is free now
   pt.stop(TC_PHASE_SORT2);
 
   pt.start(TC_PHASE_OFFSETS);
-  launch_offsets(outdeg, n, off, warp_rows, cta_rows, st_scan, ctrl, st);
+  launch_offsets(outdeg, n, off, nullptr, nullptr, nullptr, nullptr, st_scan,
+                 &ctrl->tile_ticket[kTicketScan], ctrl, st);
   pt.stop(TC_PHASE_OFFSETS);
 
+  // partner groups: each forward edge goes to the endpoint with the longer
+  // forward list; gcnt reuses the out-degree array
+  pt.start(TC_PHASE_GROUPS);
+  int32_t *gcnt = outdeg;
+  TC_CUDA(cudaMemsetAsync(gcnt, 0, sizeof(int32_t) * (size_t)n, st), "memset groups");
+  launch_group_count(row, col, off, m, ctrl, gcnt, st);
+  launch_offsets(gcnt, n, goff, off, warp_groups, cta_groups, big_groups, st_scan2,
+                 &ctrl->tile_ticket[kTicketGroupScan], ctrl, st);
+  launch_group_fill(row, col, off, m, ctrl, goff, gcnt, part, st);
+  pt.stop(TC_PHASE_GROUPS);
+
   pt.start(TC_PHASE_COUNT);
-  cudaError_t e = launch_count(off, col, warp_rows, cta_rows, ctrl, t_out, st);
+  cudaError_t e =
+      launch_count(off, col, goff, part, warp_groups, cta_groups, big_groups, ctrl, t_rank, st);
+  if (e == cudaSuccess && t_out) launch_gather_counts(t_rank, rank, n, t_out, st);
   pt.stop(TC_PHASE_COUNT);
   if (e != cudaSuccess) return cuda_fail(e, "count kernel");
   TC_CUDA(cudaGetLastError(), "kernel launch");

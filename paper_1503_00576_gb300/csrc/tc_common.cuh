@@ -19,38 +19,55 @@ constexpr uint32_t kSpinLimit = 1u << 24;
 
 constexpr int kMaxSort1Passes = 8;  // 2 * 31 id bits / 8-bit digits
 constexpr int kMaxSort2Passes = 4;  // 31 owner bits / 8-bit digits
-constexpr int kMaxPasses = kMaxSort1Passes + kMaxSort2Passes;
+constexpr int kMaxRankPasses = 4;   // 31 degree bits / 8-bit digits
+constexpr int kMaxPasses = kMaxSort1Passes + kMaxSort2Passes + kMaxRankPasses;
+// First histogram / status slot of each sort.
+constexpr int kSort2Slot = kMaxSort1Passes;
+constexpr int kRankSlot = kMaxSort1Passes + kMaxSort2Passes;
 
 // Control block: zeroed at the start of every call.
 struct Ctrl {
   uint32_t err;                    // kErr* bits
   uint32_t m;                      // distinct undirected edges (set by orient)
-  uint32_t tile_ticket[16];        // per look-back kernel: next tile to hand out
-  uint32_t n_warp_rows;            // rows counted by one warp each
-  uint32_t n_cta_rows;             // rows counted by a whole CTA each
-  uint32_t next_warp_row;          // work cursors of the counting kernel
-  uint32_t next_cta_row;
+  uint32_t tile_ticket[24];        // per look-back kernel: next tile to hand out
+  uint32_t n_warp_groups;          // partner groups counted by one warp each
+  uint32_t n_cta_groups;           // ... by a 256-thread CTA each
+  uint32_t n_big_groups;           // ... by a 512-thread CTA with a large table
+  uint32_t next_warp_group;        // work cursors of the counting kernels
+  uint32_t next_cta_group;
+  uint32_t next_big_group;
   unsigned long long total;        // triangle count T
-  uint32_t pad[8];
+  uint32_t pad[2];
 };
 static_assert(sizeof(Ctrl) % 16 == 0, "Ctrl must keep 16-byte alignment");
 
 // Ticket slots in Ctrl::tile_ticket.
-enum { kTicketSort = 0 /* .. kMaxPasses-1 */, kTicketOrient = 12, kTicketScan = 13 };
+enum {
+  kTicketSort = 0 /* .. kMaxPasses-1, one per radix pass */,
+  kTicketOrient = kMaxPasses,
+  kTicketScan = kMaxPasses + 1,
+  kTicketGroupScan = kMaxPasses + 2
+};
+static_assert(kTicketGroupScan < 24, "ticket slots");
 
 // Look-back status words: value in the low 62 bits, flag in the top 2.
 constexpr unsigned long long kFlagAggregate = 1ull << 62;
 constexpr unsigned long long kFlagInclusive = 2ull << 62;
 constexpr unsigned long long kValueMask = (1ull << 62) - 1;
 
-// Rows (forward lists) longer than this are counted by a whole CTA.
-constexpr int kWarpMaxRow = 256;
+// Partner groups whose hashed forward list has at most kWarpMaxRow entries
+// are counted by one warp, up to kCtaMaxRow by a 256-thread CTA, and longer
+// ones by a 512-thread CTA with a larger table.
+constexpr int kWarpMaxRow = 128;
+constexpr int kWarpMaxPartners = 64;
+constexpr int kCtaMaxRow = 1024;
 
 // Workspace layout for an input of m_in pairs and n vertices.  All offsets
 // are 256-byte aligned.
 struct Layout {
-  size_t ctrl, hist, st_sort, st_orient, st_scan;
-  size_t keys_a, keys_b, deg, outdeg, off, warp_rows, cta_rows;
+  size_t ctrl, hist, st_sort, st_orient, st_scan, st_scan2;
+  size_t keys_a, keys_b, deg, outdeg, off, goff, warp_groups, cta_groups, big_groups;
+  size_t rank, vkeys_a, vkeys_b, t_rank;
   size_t total;
   uint32_t sort_tiles, orient_tiles, scan_tiles;
   size_t st_sort_words_per_pass;
@@ -81,7 +98,8 @@ inline Layout make_layout(int64_t m_in, int32_t n) {
   };
   const uint64_t m = (uint64_t)(m_in > 0 ? m_in : 1);
   const uint64_t nv = (uint64_t)(n > 0 ? n : 1);
-  L.sort_tiles = (uint32_t)((m + kSortTile - 1) / kSortTile);
+  const uint64_t keys_max = m > nv ? m : nv;  // the rank sort has n keys
+  L.sort_tiles = (uint32_t)((keys_max + kSortTile - 1) / kSortTile);
   L.orient_tiles = (uint32_t)((m + kOrientTile - 1) / kOrientTile);
   L.scan_tiles = (uint32_t)((nv + 1 + kScanTile - 1) / kScanTile);
   L.st_sort_words_per_pass = (size_t)L.sort_tiles * 256;
@@ -90,13 +108,20 @@ inline Layout make_layout(int64_t m_in, int32_t n) {
   L.st_sort = take(sizeof(unsigned long long) * L.st_sort_words_per_pass * kMaxPasses);
   L.st_orient = take(sizeof(unsigned long long) * L.orient_tiles);
   L.st_scan = take(sizeof(unsigned long long) * L.scan_tiles);
+  L.st_scan2 = take(sizeof(unsigned long long) * L.scan_tiles);
   L.keys_a = take(sizeof(uint64_t) * m);
   L.keys_b = take(sizeof(uint64_t) * m);
   L.deg = take(sizeof(int32_t) * nv);
   L.outdeg = take(sizeof(int32_t) * nv);
   L.off = take(sizeof(int32_t) * (nv + 1));
-  L.warp_rows = take(sizeof(int32_t) * nv);
-  L.cta_rows = take(sizeof(int32_t) * nv);
+  L.goff = take(sizeof(int32_t) * (nv + 1));
+  L.warp_groups = take(sizeof(int32_t) * nv);
+  L.cta_groups = take(sizeof(int32_t) * nv);
+  L.big_groups = take(sizeof(int32_t) * nv);
+  L.rank = take(sizeof(int32_t) * nv);
+  L.vkeys_a = take(sizeof(uint64_t) * nv);
+  L.vkeys_b = take(sizeof(uint64_t) * nv);
+  L.t_rank = take(sizeof(int64_t) * nv);
   L.total = p;
   return L;
 }
@@ -114,23 +139,47 @@ void note_launch();
 // ---- launchers (preprocess.cu) ----
 void launch_canon(const int32_t *src, const int32_t *dst, uint32_t m_in, int32_t n, int b,
                   int passes, uint64_t *keys, uint32_t *hist, Ctrl *ctrl, cudaStream_t st);
-void launch_radix_pass(const uint64_t *in, void *out, bool out_col, uint32_t n_keys_bound,
-                       const uint32_t *n_keys_dev, int shift, uint32_t col_mask,
-                       const uint32_t *hist, unsigned long long *status, uint32_t *ticket,
-                       Ctrl *ctrl, cudaStream_t st);
+// Output of a radix pass: the keys themselves; the column array (low bits,
+// to `out`) plus the row array (key >> owner_shift, to `row_out`); or the
+// rank scatter rank[low bits] = sorted position (to `out`).
+enum RadixOut { kOutKeys = 0, kOutColRow = 1, kOutRank = 2 };
+void launch_radix_pass(const uint64_t *in, void *out, RadixOut mode, uint32_t *row_out,
+                       uint32_t n_keys_bound, const uint32_t *n_keys_dev, int shift,
+                       uint32_t col_mask, int owner_shift, const uint32_t *hist,
+                       unsigned long long *status, uint32_t *ticket, Ctrl *ctrl,
+                       cudaStream_t st);
+// Keys deg(v) << b | v for every vertex, with the digit histograms of the
+// degree field (the rank sort).
+void launch_rank_keys(const int32_t *deg, int32_t n, int b, int passes, uint64_t *vkeys,
+                      uint32_t *hist, cudaStream_t st);
 void launch_unique_degree(const uint64_t *keys, uint32_t m_in, int b, int32_t *deg,
                           cudaStream_t st);
-void launch_orient(const uint64_t *keys, uint32_t m_in, int b, const int32_t *deg,
+void launch_orient(const uint64_t *keys, uint32_t m_in, int b, const int32_t *rank,
                    uint64_t *okeys, int32_t *outdeg, uint32_t *hist2, int passes2,
                    unsigned long long *status, Ctrl *ctrl, cudaStream_t st);
-void launch_offsets(const int32_t *outdeg, int32_t n, int32_t *off, int32_t *warp_rows,
-                    int32_t *cta_rows, unsigned long long *status, Ctrl *ctrl, cudaStream_t st);
+// Exclusive scan counts[0..n) -> off[0..n].  With row_off != nullptr the
+// entries are partner groups and are binned into warp_list / cta_list /
+// big_list by the length of their hashed list.
+void launch_offsets(const int32_t *counts, int32_t n, int32_t *off, const int32_t *row_off,
+                    int32_t *warp_list, int32_t *cta_list, int32_t *big_list,
+                    unsigned long long *status, uint32_t *ticket, Ctrl *ctrl, cudaStream_t st);
+// ---- launchers (group.cu) ----
+void launch_group_count(const int32_t *row, const int32_t *col, const int32_t *off,
+                        uint32_t m_bound, Ctrl *ctrl, int32_t *gcnt, cudaStream_t st);
+void launch_group_fill(const int32_t *row, const int32_t *col, const int32_t *off,
+                       uint32_t m_bound, Ctrl *ctrl, const int32_t *goff, int32_t *gcnt,
+                       int32_t *part, cudaStream_t st);
 // ---- launchers (count.cu) ----
-cudaError_t launch_count(const int32_t *off, const int32_t *col, const int32_t *warp_rows,
-                         const int32_t *cta_rows, Ctrl *ctrl, int64_t *t, cudaStream_t st);
+cudaError_t launch_count(const int32_t *off, const int32_t *col, const int32_t *goff,
+                         const int32_t *part, const int32_t *warp_groups,
+                         const int32_t *cta_groups, const int32_t *big_groups, Ctrl *ctrl,
+                         int64_t *t, cudaStream_t st);
 // ---- clustering (count.cu) ----
 void launch_clustering(const int64_t *t, const int32_t *deg, int32_t n, double *cc,
                        unsigned long long *sums /* [2]: sum t, sum C(deg,2) */, cudaStream_t st);
 void launch_transitivity(const unsigned long long *sums, double *out, cudaStream_t st);
+// t_out[v] = t_rank[rank[v]]: per-vertex counts back to the caller's ids.
+void launch_gather_counts(const int64_t *t_rank, const int32_t *rank, int32_t n, int64_t *t_out,
+                          cudaStream_t st);
 
 }  // namespace tc
