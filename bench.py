@@ -55,6 +55,8 @@ def parse_args():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--total-only", action="store_true",
+                   help="time tc_count (T only) instead of tc_count_per_vertex")
     return p.parse_args()
 
 
@@ -188,7 +190,8 @@ def committed_traffic(kernel: str, workload: str):
     return rec.get("dram_bytes_per_launch")
 
 
-def roofline(prof: dict, steps: int, m_in: int, m: int, n: int, workload: str) -> dict:
+def roofline(prof: dict, steps: int, m_in: int, m: int, n: int, workload: str,
+             total_only: bool = False) -> dict:
     """Dominant kernel by device time; achieved = algorithmic bytes per
     launch / average launch duration (CUDA events on the launch stream)."""
     b = max(1, (max(n, 2) - 1).bit_length())
@@ -203,7 +206,7 @@ def roofline(prof: dict, steps: int, m_in: int, m: int, n: int, workload: str) -
     ms_total, launches = per_kernel[kernel]
     if kernel == "k_count":
         # compulsory: the CSR read once (col 4m, offsets 4(n+1)) and t[] written once (8n)
-        bytes_per_launch = 4 * m + 4 * (n + 1) + 8 * n
+        bytes_per_launch = 4 * m + 4 * (n + 1) + (0 if total_only else 8 * n)
         how = "CSR read once (4m + 4(n+1)) + t written once (8n)"
     elif kernel == "k_radix_pass":
         total = passes1 * 16 * m_in + (passes2 - 1) * 16 * m + 12 * m
@@ -286,12 +289,19 @@ def run_ours(args, world, rank, local, pg):
     deg_out = torch.empty(n, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step():
-        return tc.tc_count_per_vertex(s, d, n, stream=stream, t_out=t_out, deg_out=deg_out)[0]
+    if args.total_only:
+        def step():
+            return tc.tc_count(s, d, n, stream=stream)
+    else:
+        def step():
+            return tc.tc_count_per_vertex(s, d, n, stream=stream, t_out=t_out,
+                                          deg_out=deg_out)[0]
 
     for _ in range(max(args.warmup, 3)):
         T = step()
     torch.cuda.synchronize()
+    if args.total_only:
+        tc.tc_count_per_vertex(s, d, n, stream=stream, t_out=t_out, deg_out=deg_out)
     m = int((deg_out.to(torch.int64).sum() // 2).item())
 
     clocks = ClockSampler(gpu_uuid(dev))
@@ -327,19 +337,27 @@ def run_ours(args, world, rank, local, pg):
         hd = torch.from_numpy(dst).pin_memory()
         ht = torch.empty(n, dtype=torch.int64).pin_memory()
         hdeg = torch.empty(n, dtype=torch.int32).pin_memory()
-        tc.tc_count_per_vertex_host(hs, hd, n, t_out=ht, deg_out=hdeg)  # warm
+
+        def host_step():
+            if args.total_only:
+                return tc.tc_count_host(hs, hd, n)
+            return tc.tc_count_per_vertex_host(hs, hd, n, t_out=ht, deg_out=hdeg)[0]
+
+        host_step()  # warm
         barrier(pg, dev)
         times = []
         for _ in range(args.e2e_steps):
             torch.cuda.synchronize()
             a = time.perf_counter()
-            Te, _, _ = tc.tc_count_per_vertex_host(hs, hd, n, t_out=ht, deg_out=hdeg)
+            Te = host_step()
             times.append(time.perf_counter() - a)
             assert Te == T
         e2e_s = max_over_ranks(pg, statistics.mean(times), dev)
         e2e = {"value": world * m_in / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * m_in,
-               "d2h_bytes_per_step": 12 * n + 128, "ms_per_step": e2e_s * 1e3,
-               "api": "tc_count_per_vertex_host (pinned host buffers)"}
+               "d2h_bytes_per_step": (0 if args.total_only else 12 * n) + 128,
+               "ms_per_step": e2e_s * 1e3,
+               "api": ("tc_count_host" if args.total_only else "tc_count_per_vertex_host")
+                      + " (pinned host buffers)"}
 
     if rank != 0:
         return
@@ -357,11 +375,12 @@ def run_ours(args, world, rank, local, pg):
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": graphgen.WORKLOADS[args.workload][0], "n": n, "m_in": m_in,
                    "m_distinct": m, "triangles": T,
-                   "outputs": "T (uint64), t[n] (int64), deg[n] (int32)",
+                   "outputs": "T (uint64)" if args.total_only
+                              else "T (uint64), t[n] (int64), deg[n] (int32)",
                    "l2": "no flush: inputs %.2f GB and key buffers %.2f GB exceed L2"
                          % (8 * m_in / 1e9, 16 * m_in / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": roofline(prof, args.steps, m_in, m, n, args.workload),
+        "roofline": roofline(prof, args.steps, m_in, m, n, args.workload, args.total_only),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "phase_ms_per_step": steps_ms,
     }

@@ -23,10 +23,9 @@
 // Per-vertex counts t(v) (Sec. I: the numerator of the clustering
 // coefficient): a triangle found in group h, partner l, element w adds one
 // to t(h), t(l) and t(w).  t(h) is summed over the group, t(l) over the
-// chunk (shared counters per partner) and t(w) in a 16-bit counter beside
-// w's hash slot (groups with fewer than 65536 partners; larger groups add to
-// t(w) directly), so global atomics scale with the number of forward edges,
-// not with the number of triangles.
+// chunk (shared counters per partner) and t(w) in a counter beside w's hash
+// slot, so global atomics scale with the number of forward edges, not with
+// the number of triangles.
 //
 // A hashed list longer than 8192 entries (never seen in the workloads, but
 // allowed by |N+(v)| <= sqrt(2m)) is hashed in segments.  No step needs the
@@ -92,13 +91,14 @@ struct WarpScratch {
   uint32_t lc[32];    // triangles found through that partner
 };
 
-// Empties tab[0..slots) and its 16-bit counters (one word per slot pair).
+// Empties tab[0..slots) and its per-slot counters.
 template <bool PV>
 __device__ __forceinline__ void clear_table(int32_t *tab, uint32_t *cnt, int slots, int rank,
                                             int group) {
-  for (int i = rank; i < slots; i += group) tab[i] = kEmpty;
-  if (PV)
-    for (int i = rank; i < slots / 2; i += group) cnt[i] = 0u;
+  for (int i = rank; i < slots; i += group) {
+    tab[i] = kEmpty;
+    if (PV) cnt[i] = 0u;
+  }
 }
 
 // Inserts col[beg..beg+len) (distinct ids) into the empty hash set.
@@ -119,29 +119,21 @@ __device__ __forceinline__ void fill_table(const int32_t *__restrict__ col, int3
   }
 }
 
-// Empties the first 2^log_slots slots again; in per-vertex mode with slot
-// counters, first adds each slot's count to t(w) of the w stored there.
-// Each thread owns whole counter words (two slots), so no barrier is needed
-// between reading and clearing.
+// Empties the first 2^log_slots slots again; in per-vertex mode, first adds
+// each slot's count to t(w) of the w stored there.
 template <bool PV>
-__device__ __forceinline__ void drain_table(int32_t *tab, uint32_t *cnt, int log_slots,
-                                            bool flush, int rank, int group, int64_t *t) {
-  const int words = (1 << log_slots) / 2;
-  for (int i = rank; i < words; i += group) {
+__device__ __forceinline__ void drain_table(int32_t *tab, uint32_t *cnt, int log_slots, int rank,
+                                            int group, int64_t *t) {
+  const int slots = 1 << log_slots;
+  for (int i = rank; i < slots; i += group) {
     if (PV) {
       const uint32_t c = cnt[i];
-      if (flush && c) {
-        if (c & 0xffffu)
-          atomicAdd((unsigned long long *)&t[tab[2 * i] & 0x7fffffff],
-                    (unsigned long long)(c & 0xffffu));
-        if (c >> 16)
-          atomicAdd((unsigned long long *)&t[tab[2 * i + 1] & 0x7fffffff],
-                    (unsigned long long)(c >> 16));
+      if (c) {
+        atomicAdd((unsigned long long *)&t[tab[i] & 0x7fffffff], (unsigned long long)c);
+        cnt[i] = 0u;
       }
-      cnt[i] = 0u;
     }
-    tab[2 * i] = kEmpty;
-    tab[2 * i + 1] = kEmpty;
+    tab[i] = kEmpty;
   }
 }
 
@@ -172,16 +164,15 @@ __device__ __forceinline__ bool member(int32_t x, const int32_t *tab, int log_sl
 // sequence; lane p takes flat positions p, p+32, ... and keeps a cursor on
 // the list that holds its position (lists average ~200 entries, so the
 // cursor rarely moves).  Matches are counted in registers; per partner they
-// reach shared memory only when a lane's cursor leaves that partner.
-// slot_cnt: per-vertex counts of w go to the 16-bit slot counters (valid
-// while a group has < 65536 partners); otherwise straight to t(w).
+// reach shared memory only when a lane's cursor leaves that partner; per w
+// they go to the counter beside w's slot.
 template <bool PV>
 __device__ __forceinline__ void probe_chunk(const int32_t *__restrict__ off,
                                             const int32_t *__restrict__ col,
                                             const int32_t *__restrict__ part, int32_t np,
                                             int32_t c0, int32_t cs, const int32_t *tab,
-                                            uint32_t *cnt, int log_slots, bool slot_cnt,
-                                            WarpScratch &ws, int64_t *t, uint64_t &found_total,
+                                            uint32_t *cnt, int log_slots, WarpScratch &ws,
+                                            int64_t *t, uint64_t &found_total,
                                             uint64_t &found_group) {
   const int lane = threadIdx.x & 31;
   const int32_t j = c0 + lane;
@@ -248,10 +239,7 @@ __device__ __forceinline__ void probe_chunk(const int32_t *__restrict__ off,
           run_r = rq[q];
         }
         ++run;
-        if (slot_cnt)
-          atomicAdd(&cnt[slot >> 1], 1u << (16 * (slot & 1u)));
-        else
-          atomicAdd((unsigned long long *)&t[x[q]], 1ull);
+        atomicAdd(&cnt[slot], 1u);
       }
     }
   }
@@ -305,7 +293,6 @@ __device__ __forceinline__ void cta_groups(const int32_t *__restrict__ off,
     const int32_t nseg = (hd + SLOTS / 2 - 1) / (SLOTS / 2);
     const int32_t seg_len = (hd + nseg - 1) / nseg;
     const int log_slots = table_log_slots(seg_len, SLOTS);
-    const bool slot_cnt = np < 65536;
     const int32_t cs = max(8, min(32, (np + 2 * WARPS - 1) / (2 * WARPS)));
     uint64_t found_group = 0;
     for (int32_t s0 = 0; s0 < hd; s0 += seg_len) {
@@ -319,11 +306,11 @@ __device__ __forceinline__ void cta_groups(const int32_t *__restrict__ off,
         c = __shfl_sync(kFull, c, 0);
         const int32_t c0 = (int32_t)c * cs;
         if (c0 >= np) break;
-        probe_chunk<PV>(off, col, part + pb, np, c0, cs, tab, cnt, log_slots, slot_cnt,
-                        s_ws[warp], t, found_total, found_group);
+        probe_chunk<PV>(off, col, part + pb, np, c0, cs, tab, cnt, log_slots, s_ws[warp], t,
+                        found_total, found_group);
       }
       __syncthreads();
-      drain_table<PV>(tab, cnt, log_slots, slot_cnt, tid, THREADS, t);
+      drain_table<PV>(tab, cnt, log_slots, tid, THREADS, t);
       if (s0 + seg_len < hd) __syncthreads();  // next segment refills the table
     }
     if (PV) {
@@ -357,19 +344,18 @@ __device__ __forceinline__ void warp_groups(const int32_t *__restrict__ off,
       const int32_t hb = __ldg(off + h), hd = __ldg(off + h + 1) - hb;
       const int32_t pb = __ldg(goff + h), np = __ldg(goff + h + 1) - pb;
       const int log_slots = table_log_slots(hd, kWarpSlots);
-      const bool slot_cnt = np < 65536;
       fill_table(col, hb, hd, wtab, log_slots, lane, 32);
       __syncwarp();
       uint64_t found_group = 0;
       for (int32_t c0 = 0; c0 < np; c0 += 32)
-        probe_chunk<PV>(off, col, part + pb, np, c0, 32, wtab, wcnt, log_slots, slot_cnt, ws, t,
+        probe_chunk<PV>(off, col, part + pb, np, c0, 32, wtab, wcnt, log_slots, ws, t,
                         found_total, found_group);
       if (PV) {
         found_group = warp_sum_u64(found_group);
         if (lane == 0 && found_group) atomicAdd((unsigned long long *)&t[h], found_group);
       }
       __syncwarp();
-      drain_table<PV>(wtab, wcnt, log_slots, slot_cnt, lane, 32, t);
+      drain_table<PV>(wtab, wcnt, log_slots, lane, 32, t);
       __syncwarp();
     }
   }
@@ -383,7 +369,7 @@ k_count(const int32_t *__restrict__ off, const int32_t *__restrict__ col,
         const int32_t *__restrict__ warp_list, const int32_t *__restrict__ cta_list, Ctrl *ctrl,
         int64_t *t) {
   __shared__ int32_t s_tab[kMainSlots];
-  __shared__ uint32_t s_cnt[PV ? kMainSlots / 2 : 1];
+  __shared__ uint32_t s_cnt[PV ? kMainSlots : 1];
   __shared__ WarpScratch s_ws[kMainWarps];
   __shared__ CtaShared s_sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -393,7 +379,7 @@ k_count(const int32_t *__restrict__ off, const int32_t *__restrict__ col,
                                            &ctrl->next_cta_group, s_tab, s_cnt, s_ws, s_sh, t,
                                            found_total);
   warp_groups<PV>(off, col, goff, part, warp_list, ctrl->n_warp_groups, &ctrl->next_warp_group,
-                  s_tab + warp * kWarpSlots, s_cnt + warp * (kWarpSlots / 2), s_ws[warp], t,
+                  s_tab + warp * kWarpSlots, s_cnt + warp * kWarpSlots, s_ws[warp], t,
                   found_total);
   found_total = warp_sum_u64(found_total);
   if (lane == 0 && found_total) atomicAdd(&ctrl->total, (unsigned long long)found_total);
@@ -480,7 +466,7 @@ cudaError_t count_grid(bool pv, CountGrid *out) {
     *out = cache[dev][pv];
     return cudaSuccess;
   }
-  const size_t big_smem = (size_t)4 * kBigSlots + (pv ? (size_t)2 * kBigSlots : 0);
+  const size_t big_smem = (size_t)4 * kBigSlots * (pv ? 2 : 1);
   e = pv ? cudaFuncSetAttribute(k_count_big<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)big_smem)
          : cudaFuncSetAttribute(k_count_big<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -517,7 +503,7 @@ cudaError_t launch_count(const int32_t *off, const int32_t *col, const int32_t *
   CountGrid g;
   cudaError_t e = count_grid(pv, &g);
   if (e != cudaSuccess) return e;
-  const size_t big_smem = (size_t)4 * kBigSlots + (pv ? (size_t)2 * kBigSlots : 0);
+  const size_t big_smem = (size_t)4 * kBigSlots * (pv ? 2 : 1);
   // the rare long lists first, on their own wide CTAs; usually an empty list
   if (pv) {
     k_count_big<true><<<g.big_blocks, kBigThreads, big_smem, st>>>(off, col, goff, part,

@@ -177,7 +177,7 @@ k_canon(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, uint32
 // one LSD radix pass (8-bit digit at `shift`), onesweep style
 // ---------------------------------------------------------------------------
 template <int MODE>
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 4)
 k_radix_pass(const uint64_t *__restrict__ in, void *__restrict__ out, uint32_t n_keys_bound,
              const uint32_t *__restrict__ n_keys_dev, int shift, uint32_t col_mask,
              uint32_t *__restrict__ row_out, int owner_shift, const uint32_t *__restrict__ hist,
@@ -204,14 +204,22 @@ k_radix_pass(const uint64_t *__restrict__ in, void *__restrict__ out, uint32_t n
   const uint32_t gofs = scan256_exclusive(hist[tid], s_scratch, &dummy);
 
   // ---- rank keys within the tile (stable: warp-major, round-major, lane) ----
+  // All 16 keys of a thread are loaded before ranking starts, and the
+  // kernel is held to 64 registers so that four tiles fit on an SM: the
+  // pass is latency-bound, and occupancy halves its time even though a few
+  // keys spill to L1.
   const uint32_t lt_mask = (1u << lane) - 1u;
   uint64_t k[KPT];
   uint32_t rk[KPT];
 #pragma unroll
   for (int i = 0; i < KPT; ++i) {
     const uint32_t idx = tile_base + (uint32_t)(warp * 32 * KPT + i * 32 + lane);
+    k[i] = idx < n_keys ? __ldg(in + idx) : 0ull;
+  }
+#pragma unroll
+  for (int i = 0; i < KPT; ++i) {
+    const uint32_t idx = tile_base + (uint32_t)(warp * 32 * KPT + i * 32 + lane);
     const bool valid = idx < n_keys;
-    k[i] = valid ? __ldg(in + idx) : 0ull;
     const uint32_t d = (uint32_t)(k[i] >> shift) & 255u;
     uint32_t peers = __ballot_sync(kFull, valid);
 #pragma unroll
