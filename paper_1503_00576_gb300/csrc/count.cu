@@ -45,11 +45,11 @@ constexpr int kWindows = 4;                  // 32-wide windows of loads in flig
 constexpr int kMainThreads = 256;
 constexpr int kMainWarps = kMainThreads / 32;
 constexpr int kMainSlots = 4096;
-// Long-list kernel: 512-thread CTAs, 16384 slots (lists up to 8192 entries
+// Long-list kernel: 512-thread CTAs, 8192 slots (lists up to 4096 entries
 // at once; longer lists in segments).
 constexpr int kBigThreads = 512;
 constexpr int kBigWarps = kBigThreads / 32;
-constexpr int kBigSlots = 16384;
+constexpr int kBigSlots = 8192;
 static_assert(kWarpSlots * kMainWarps <= kMainSlots, "warp tables must fit the CTA table");
 static_assert(4 * kCtaMaxRow <= kMainSlots, "CTA lists must fit at load <= 1/4");
 
@@ -78,6 +78,14 @@ __device__ __forceinline__ int table_log_slots(int32_t len, int capacity) {
   return (1 << lg) <= capacity ? lg : -1;
 }
 
+// Read-only view of the forward lists and partner groups.
+struct Lists {
+  const int32_t *__restrict__ off;   // node array (rank space)
+  const int32_t *__restrict__ col;   // forward lists
+  const int32_t *__restrict__ goff;  // partner-group offsets
+  const int32_t *__restrict__ part;  // partners
+};
+
 __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
@@ -101,13 +109,12 @@ __device__ __forceinline__ void clear_table(int32_t *tab, uint32_t *cnt, int slo
   }
 }
 
-// Inserts col[beg..beg+len) (distinct ids) into the empty hash set.
-__device__ __forceinline__ void fill_table(const int32_t *__restrict__ col, int32_t beg,
-                                           int32_t len, int32_t *tab, int log_slots, int rank,
-                                           int group) {
+// Inserts g.col[beg..beg+len) (distinct ids) into the empty hash set.
+__device__ __forceinline__ void fill_table(const Lists &g, int32_t beg, int32_t len, int32_t *tab,
+                                           int log_slots, int rank, int group) {
   const uint32_t msk = (1u << log_slots) - 1u;
   for (int32_t i = rank; i < len; i += group) {
-    const int32_t x = __ldg(col + beg + i);
+    const int32_t x = __ldg(g.col + beg + i);
     const uint32_t home = hash_slot((uint32_t)x, log_slots);
     uint32_t h = home;
     for (;;) {
@@ -167,20 +174,18 @@ __device__ __forceinline__ bool member(int32_t x, const int32_t *tab, int log_sl
 // reach shared memory only when a lane's cursor leaves that partner; per w
 // they go to the counter beside w's slot.
 template <bool PV>
-__device__ __forceinline__ void probe_chunk(const int32_t *__restrict__ off,
-                                            const int32_t *__restrict__ col,
-                                            const int32_t *__restrict__ part, int32_t np,
-                                            int32_t c0, int32_t cs, const int32_t *tab,
-                                            uint32_t *cnt, int log_slots, WarpScratch &ws,
-                                            int64_t *t, uint64_t &found_total,
+__device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__restrict__ part,
+                                            int32_t np, int32_t c0, int32_t cs,
+                                            const int32_t *tab, uint32_t *cnt, int log_slots,
+                                            WarpScratch &ws, int64_t *t, uint64_t &found_total,
                                             uint64_t &found_group) {
   const int lane = threadIdx.x & 31;
   const int32_t j = c0 + lane;
   int32_t l = 0, lb = 0, dl = 0;
   if (lane < cs && j < np) {
     l = __ldg(part + j);
-    lb = __ldg(off + l);
-    dl = __ldg(off + l + 1) - lb;
+    lb = __ldg(g.off + l);
+    dl = __ldg(g.off + l + 1) - lb;
   }
   const uint32_t nonempty = __ballot_sync(kFull, dl > 0);
   if (nonempty == 0) return;
@@ -222,7 +227,7 @@ __device__ __forceinline__ void probe_chunk(const int32_t *__restrict__ off,
           base = ws.base[r];
           next = r + 1 < k ? ws.start[r + 1] : INT32_MAX;
         }
-        x[q] = __ldg(col + base + p);
+        x[q] = __ldg(g.col + base + p);
         rq[q] = r;
       }
     }
@@ -267,14 +272,10 @@ struct CtaShared {
 // N+(h) & N+(l) is the disjoint union of the segments' intersections.  The
 // table (SLOTS slots) is empty on entry and on exit.
 template <bool PV, int THREADS, int SLOTS>
-__device__ __forceinline__ void cta_groups(const int32_t *__restrict__ off,
-                                           const int32_t *__restrict__ col,
-                                           const int32_t *__restrict__ goff,
-                                           const int32_t *__restrict__ part,
-                                           const int32_t *__restrict__ list, uint32_t n_list,
-                                           uint32_t *cursor, int32_t *tab, uint32_t *cnt,
-                                           WarpScratch *s_ws, CtaShared &sh, int64_t *t,
-                                           uint64_t &found_total) {
+__device__ __forceinline__ void cta_groups(const Lists &g, const int32_t *__restrict__ list,
+                                           uint32_t n_list, uint32_t *cursor, int32_t *tab,
+                                           uint32_t *cnt, WarpScratch *s_ws, CtaShared &sh,
+                                           int64_t *t, uint64_t &found_total) {
   constexpr int WARPS = THREADS / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (;;) {
@@ -283,13 +284,13 @@ __device__ __forceinline__ void cta_groups(const int32_t *__restrict__ off,
       sh.groupsum = 0ull;
     }
     __syncthreads();  // also orders the previous group's drain before this fill
-    const uint32_t g = (uint32_t)sh.group;
-    if (g >= n_list) break;
+    const uint32_t gi = (uint32_t)sh.group;
+    if (gi >= n_list) break;
     // lists are filled in about ascending rank, and high ranks (high
     // degrees) carry the most work: take them first to shorten the tail
-    const int32_t h = __ldg(list + (n_list - 1 - g));
-    const int32_t hb = __ldg(off + h), hd = __ldg(off + h + 1) - hb;
-    const int32_t pb = __ldg(goff + h), np = __ldg(goff + h + 1) - pb;
+    const int32_t h = __ldg(list + (n_list - 1 - gi));
+    const int32_t hb = __ldg(g.off + h), hd = __ldg(g.off + h + 1) - hb;
+    const int32_t pb = __ldg(g.goff + h), np = __ldg(g.goff + h + 1) - pb;
     const int32_t nseg = (hd + SLOTS / 2 - 1) / (SLOTS / 2);
     const int32_t seg_len = (hd + nseg - 1) / nseg;
     const int log_slots = table_log_slots(seg_len, SLOTS);
@@ -298,7 +299,7 @@ __device__ __forceinline__ void cta_groups(const int32_t *__restrict__ off,
     for (int32_t s0 = 0; s0 < hd; s0 += seg_len) {
       const int32_t len = min(seg_len, hd - s0);
       if (tid == 0) sh.chunk = 0u;
-      fill_table(col, hb + s0, len, tab, log_slots, tid, THREADS);
+      fill_table(g, hb + s0, len, tab, log_slots, tid, THREADS);
       __syncthreads();
       for (;;) {
         uint32_t c = 0;
@@ -306,7 +307,7 @@ __device__ __forceinline__ void cta_groups(const int32_t *__restrict__ off,
         c = __shfl_sync(kFull, c, 0);
         const int32_t c0 = (int32_t)c * cs;
         if (c0 >= np) break;
-        probe_chunk<PV>(off, col, part + pb, np, c0, cs, tab, cnt, log_slots, s_ws[warp], t,
+        probe_chunk<PV>(g, g.part + pb, np, c0, cs, tab, cnt, log_slots, s_ws[warp], t,
                         found_total, found_group);
       }
       __syncthreads();
@@ -325,13 +326,10 @@ __device__ __forceinline__ void cta_groups(const int32_t *__restrict__ off,
 // Groups of `list` counted by one warp each with a private table of
 // kWarpSlots slots (empty on entry and on exit).
 template <bool PV>
-__device__ __forceinline__ void warp_groups(const int32_t *__restrict__ off,
-                                            const int32_t *__restrict__ col,
-                                            const int32_t *__restrict__ goff,
-                                            const int32_t *__restrict__ part,
-                                            const int32_t *__restrict__ list, uint32_t n_list,
-                                            uint32_t *cursor, int32_t *wtab, uint32_t *wcnt,
-                                            WarpScratch &ws, int64_t *t, uint64_t &found_total) {
+__device__ __forceinline__ void warp_groups(const Lists &g, const int32_t *__restrict__ list,
+                                            uint32_t n_list, uint32_t *cursor, int32_t *wtab,
+                                            uint32_t *wcnt, WarpScratch &ws, int64_t *t,
+                                            uint64_t &found_total) {
   const int lane = threadIdx.x & 31;
   for (;;) {
     uint32_t g0 = 0;
@@ -339,17 +337,17 @@ __device__ __forceinline__ void warp_groups(const int32_t *__restrict__ off,
     g0 = __shfl_sync(kFull, g0, 0);
     if (g0 >= n_list) break;
     const uint32_t g1 = min(g0 + (uint32_t)kGroupChunk, n_list);
-    for (uint32_t g = g0; g < g1; ++g) {
-      const int32_t h = __ldg(list + (n_list - 1 - g));  // heavy (high-rank) groups first
-      const int32_t hb = __ldg(off + h), hd = __ldg(off + h + 1) - hb;
-      const int32_t pb = __ldg(goff + h), np = __ldg(goff + h + 1) - pb;
+    for (uint32_t gi = g0; gi < g1; ++gi) {
+      const int32_t h = __ldg(list + (n_list - 1 - gi));  // heavy (high-rank) groups first
+      const int32_t hb = __ldg(g.off + h), hd = __ldg(g.off + h + 1) - hb;
+      const int32_t pb = __ldg(g.goff + h), np = __ldg(g.goff + h + 1) - pb;
       const int log_slots = table_log_slots(hd, kWarpSlots);
-      fill_table(col, hb, hd, wtab, log_slots, lane, 32);
+      fill_table(g, hb, hd, wtab, log_slots, lane, 32);
       __syncwarp();
       uint64_t found_group = 0;
       for (int32_t c0 = 0; c0 < np; c0 += 32)
-        probe_chunk<PV>(off, col, part + pb, np, c0, 32, wtab, wcnt, log_slots, ws, t,
-                        found_total, found_group);
+        probe_chunk<PV>(g, g.part + pb, np, c0, 32, wtab, wcnt, log_slots, ws, t, found_total,
+                        found_group);
       if (PV) {
         found_group = warp_sum_u64(found_group);
         if (lane == 0 && found_group) atomicAdd((unsigned long long *)&t[h], found_group);
@@ -364,10 +362,8 @@ __device__ __forceinline__ void warp_groups(const int32_t *__restrict__ off,
 // Main counting kernel: CTA groups first (the heavy ones), then warp groups.
 template <bool PV>
 __global__ void __launch_bounds__(kMainThreads)
-k_count(const int32_t *__restrict__ off, const int32_t *__restrict__ col,
-        const int32_t *__restrict__ goff, const int32_t *__restrict__ part,
-        const int32_t *__restrict__ warp_list, const int32_t *__restrict__ cta_list, Ctrl *ctrl,
-        int64_t *t) {
+k_count(Lists g, const int32_t *__restrict__ warp_list, const int32_t *__restrict__ cta_list,
+        Ctrl *ctrl, int64_t *t) {
   __shared__ int32_t s_tab[kMainSlots];
   __shared__ uint32_t s_cnt[PV ? kMainSlots : 1];
   __shared__ WarpScratch s_ws[kMainWarps];
@@ -375,10 +371,10 @@ k_count(const int32_t *__restrict__ off, const int32_t *__restrict__ col,
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   clear_table<PV>(s_tab, s_cnt, kMainSlots, tid, kMainThreads);
   uint64_t found_total = 0;
-  cta_groups<PV, kMainThreads, kMainSlots>(off, col, goff, part, cta_list, ctrl->n_cta_groups,
+  cta_groups<PV, kMainThreads, kMainSlots>(g, cta_list, ctrl->n_cta_groups,
                                            &ctrl->next_cta_group, s_tab, s_cnt, s_ws, s_sh, t,
                                            found_total);
-  warp_groups<PV>(off, col, goff, part, warp_list, ctrl->n_warp_groups, &ctrl->next_warp_group,
+  warp_groups<PV>(g, warp_list, ctrl->n_warp_groups, &ctrl->next_warp_group,
                   s_tab + warp * kWarpSlots, s_cnt + warp * kWarpSlots, s_ws[warp], t,
                   found_total);
   found_total = warp_sum_u64(found_total);
@@ -388,9 +384,7 @@ k_count(const int32_t *__restrict__ off, const int32_t *__restrict__ col,
 // Groups whose hashed list is longer than kCtaMaxRow (rare).
 template <bool PV>
 __global__ void __launch_bounds__(kBigThreads)
-k_count_big(const int32_t *__restrict__ off, const int32_t *__restrict__ col,
-            const int32_t *__restrict__ goff, const int32_t *__restrict__ part,
-            const int32_t *__restrict__ big_list, Ctrl *ctrl, int64_t *t) {
+k_count_big(Lists g, const int32_t *__restrict__ big_list, Ctrl *ctrl, int64_t *t) {
   extern __shared__ __align__(16) unsigned char smem[];
   int32_t *tab = reinterpret_cast<int32_t *>(smem);
   uint32_t *cnt = reinterpret_cast<uint32_t *>(smem + 4 * kBigSlots);
@@ -399,9 +393,8 @@ k_count_big(const int32_t *__restrict__ off, const int32_t *__restrict__ col,
   const int tid = threadIdx.x, lane = tid & 31;
   clear_table<PV>(tab, cnt, kBigSlots, tid, kBigThreads);
   uint64_t found_total = 0;
-  cta_groups<PV, kBigThreads, kBigSlots>(off, col, goff, part, big_list, ctrl->n_big_groups,
-                                         &ctrl->next_big_group, tab, cnt, s_ws, s_sh, t,
-                                         found_total);
+  cta_groups<PV, kBigThreads, kBigSlots>(g, big_list, ctrl->n_big_groups, &ctrl->next_big_group,
+                                         tab, cnt, s_ws, s_sh, t, found_total);
   found_total = warp_sum_u64(found_total);
   if (lane == 0 && found_total) atomicAdd(&ctrl->total, (unsigned long long)found_total);
 }
@@ -500,21 +493,18 @@ cudaError_t launch_count(const int32_t *off, const int32_t *col, const int32_t *
                          const int32_t *cta_groups, const int32_t *big_groups, Ctrl *ctrl,
                          int64_t *t, cudaStream_t st) {
   const bool pv = t != nullptr;
-  CountGrid g;
-  cudaError_t e = count_grid(pv, &g);
+  CountGrid cg;
+  cudaError_t e = count_grid(pv, &cg);
   if (e != cudaSuccess) return e;
   const size_t big_smem = (size_t)4 * kBigSlots * (pv ? 2 : 1);
-  // the rare long lists first, on their own wide CTAs; usually an empty list
+  const Lists g{off, col, goff, part};
+  // the long lists first, on their own wide CTAs
   if (pv) {
-    k_count_big<true><<<g.big_blocks, kBigThreads, big_smem, st>>>(off, col, goff, part,
-                                                                   big_groups, ctrl, t);
-    k_count<true><<<g.main_blocks, kMainThreads, 0, st>>>(off, col, goff, part, warp_groups,
-                                                          cta_groups, ctrl, t);
+    k_count_big<true><<<cg.big_blocks, kBigThreads, big_smem, st>>>(g, big_groups, ctrl, t);
+    k_count<true><<<cg.main_blocks, kMainThreads, 0, st>>>(g, warp_groups, cta_groups, ctrl, t);
   } else {
-    k_count_big<false><<<g.big_blocks, kBigThreads, big_smem, st>>>(off, col, goff, part,
-                                                                    big_groups, ctrl, t);
-    k_count<false><<<g.main_blocks, kMainThreads, 0, st>>>(off, col, goff, part, warp_groups,
-                                                           cta_groups, ctrl, t);
+    k_count_big<false><<<cg.big_blocks, kBigThreads, big_smem, st>>>(g, big_groups, ctrl, t);
+    k_count<false><<<cg.main_blocks, kMainThreads, 0, st>>>(g, warp_groups, cta_groups, ctrl, t);
   }
   note_launch();
   note_launch();
