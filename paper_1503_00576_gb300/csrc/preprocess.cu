@@ -23,15 +23,15 @@
 //                  emit each as owner << b | neighbour in rank space, the
 //                  owner being the endpoint of lower rank -- marking and
 //                  removing backward edges of Sec. III-B in one pass; also
-//                  the out-degree histogram and the digit histograms of the
-//                  owner field.
+//                  the digit histograms of the owner field.
 //   radix passes   stable LSD passes over the owner bits only.  Sort 1 left
 //                  the keys ordered by (min, max); every entry of a forward
 //                  list that came from a flipped edge has a smaller id than
 //                  the owner and precedes, in that order, all entries of the
 //                  owner's own run, so a stable sort by owner alone leaves
 //                  each list sorted by neighbour id.  The last pass writes
-//                  only the neighbour (the column array: the "unzip").
+//                  the neighbour (the column array: the "unzip"), the owner
+//                  (the row array) and counts the out-degrees.
 //   offsets        exclusive scan of the out-degrees = node array (CSR
 //                  offsets).  The last sort pass also wrote the row of
 //                  every entry, so (row[], col[]) is the paper's unzipped
@@ -180,8 +180,9 @@ template <int MODE>
 __global__ void __launch_bounds__(kSortThreads, 4)
 k_radix_pass(const uint64_t *__restrict__ in, void *__restrict__ out, uint32_t n_keys_bound,
              const uint32_t *__restrict__ n_keys_dev, int shift, uint32_t col_mask,
-             uint32_t *__restrict__ row_out, int owner_shift, const uint32_t *__restrict__ hist,
-             unsigned long long *__restrict__ status, uint32_t *ticket, Ctrl *ctrl) {
+             uint32_t *__restrict__ row_out, int owner_shift, int32_t *outdeg,
+             const uint32_t *__restrict__ hist, unsigned long long *__restrict__ status,
+             uint32_t *ticket, Ctrl *ctrl) {
   constexpr int WARPS = kSortThreads / 32, KPT = kSortKeysPerThread, TILE = kSortTile;
   __shared__ uint64_t s_keys[TILE];
   __shared__ uint32_t s_whist[WARPS][256];
@@ -300,8 +301,13 @@ k_radix_pass(const uint64_t *__restrict__ in, void *__restrict__ out, uint32_t n
     const uint64_t key = s_keys[i];
     const uint32_t pos = s_gbase[(uint32_t)(key >> shift) & 255u] + i;
     if (MODE == kOutColRow) {
+      const uint32_t owner = (uint32_t)(key >> owner_shift);
       ((uint32_t *)out)[pos] = (uint32_t)key & col_mask;
-      row_out[pos] = (uint32_t)(key >> owner_shift);
+      row_out[pos] = owner;
+      // the staged tile is in owner order: consecutive lanes share owners,
+      // and one atomic per run gives the out-degrees (the node array's counts)
+      const uint32_t peers = __match_any_sync(__activemask(), owner);
+      if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&outdeg[owner], __popc(peers));
     } else if (MODE == kOutRank) {
       ((uint32_t *)out)[(uint32_t)key & col_mask] = pos;
     } else {
@@ -320,11 +326,17 @@ k_unique_degree(const uint64_t *__restrict__ keys, uint32_t m_in, int b, int32_t
   const uint64_t sentinel = (1ull << (2 * b)) - 1;
   const uint64_t mask = (1ull << b) - 1;
   const uint32_t stride = gridDim.x * kDegThreads;
+  const int lane = threadIdx.x & 31;
   for (uint32_t i = blockIdx.x * kDegThreads + threadIdx.x; i < m_in; i += stride) {
     const uint64_t key = __ldg(keys + i);
-    if (key == sentinel) continue;
-    if (i > 0 && __ldg(keys + i - 1) == key) continue;
-    atomicAdd(&deg[(uint32_t)(key >> b)], 1);
+    const bool first = key != sentinel && (i == 0 || __ldg(keys + i - 1) != key);
+    const uint32_t firsts = __ballot_sync(__activemask(), first);
+    if (!first) continue;
+    // sorted keys: neighbouring lanes usually share the lower endpoint, so
+    // that side takes one atomic per run
+    const uint32_t a = (uint32_t)(key >> b);
+    const uint32_t peers = __match_any_sync(firsts, a);
+    if (lane == __ffs(peers) - 1) atomicAdd(&deg[a], __popc(peers));
     atomicAdd(&deg[(uint32_t)(key & mask)], 1);
   }
 }
@@ -359,7 +371,7 @@ k_rank_keys(const int32_t *__restrict__ deg, int32_t n, int b, int passes,
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kOrientThreads)
 k_orient(const uint64_t *__restrict__ keys, uint32_t m_in, int b,
-         const int32_t *__restrict__ rank, uint64_t *__restrict__ okeys, int32_t *outdeg,
+         const int32_t *__restrict__ rank, uint64_t *__restrict__ okeys,
          uint32_t *__restrict__ hist2, int passes2, unsigned long long *status, Ctrl *ctrl) {
   constexpr int KPT = kOrientKeysPerThread, TILE = kOrientTile;
   __shared__ uint32_t s_scratch[32];
@@ -406,7 +418,6 @@ k_orient(const uint64_t *__restrict__ keys, uint32_t m_in, int b,
     const uint32_t ra = (uint32_t)__ldg(rank + a), rc = (uint32_t)__ldg(rank + c);
     const uint32_t owner = min(ra, rc), nbr = max(ra, rc);
     okeys[pos++] = ((uint64_t)owner << b) | nbr;
-    atomicAdd(&outdeg[owner], 1);
     for (int p = 0; p < passes2; ++p) atomicAdd(&s_hist[p * 256 + ((owner >> (8 * p)) & 255u)], 1u);
   }
   __syncthreads();
@@ -511,23 +522,23 @@ void launch_canon(const int32_t *src, const int32_t *dst, uint32_t m_in, int32_t
 }
 
 void launch_radix_pass(const uint64_t *in, void *out, RadixOut mode, uint32_t *row_out,
-                       uint32_t n_keys_bound, const uint32_t *n_keys_dev, int shift,
-                       uint32_t col_mask, int owner_shift, const uint32_t *hist,
+                       int32_t *outdeg, uint32_t n_keys_bound, const uint32_t *n_keys_dev,
+                       int shift, uint32_t col_mask, int owner_shift, const uint32_t *hist,
                        unsigned long long *status, uint32_t *ticket, Ctrl *ctrl,
                        cudaStream_t st) {
   const uint32_t grid = max(1u, (n_keys_bound + kSortTile - 1) / kSortTile);
   if (mode == kOutColRow)
     k_radix_pass<kOutColRow><<<grid, kSortThreads, 0, st>>>(
-        in, out, n_keys_bound, n_keys_dev, shift, col_mask, row_out, owner_shift, hist, status,
-        ticket, ctrl);
+        in, out, n_keys_bound, n_keys_dev, shift, col_mask, row_out, owner_shift, outdeg, hist,
+        status, ticket, ctrl);
   else if (mode == kOutRank)
     k_radix_pass<kOutRank><<<grid, kSortThreads, 0, st>>>(in, out, n_keys_bound, n_keys_dev,
-                                                          shift, col_mask, nullptr, 0, hist,
-                                                          status, ticket, ctrl);
+                                                          shift, col_mask, nullptr, 0, nullptr,
+                                                          hist, status, ticket, ctrl);
   else
     k_radix_pass<kOutKeys><<<grid, kSortThreads, 0, st>>>(in, out, n_keys_bound, n_keys_dev,
-                                                          shift, col_mask, nullptr, 0, hist,
-                                                          status, ticket, ctrl);
+                                                          shift, col_mask, nullptr, 0, nullptr,
+                                                          hist, status, ticket, ctrl);
   note_launch();
 }
 
@@ -548,11 +559,11 @@ void launch_unique_degree(const uint64_t *keys, uint32_t m_in, int b, int32_t *d
 }
 
 void launch_orient(const uint64_t *keys, uint32_t m_in, int b, const int32_t *rank,
-                   uint64_t *okeys, int32_t *outdeg, uint32_t *hist2, int passes2,
-                   unsigned long long *status, Ctrl *ctrl, cudaStream_t st) {
+                   uint64_t *okeys, uint32_t *hist2, int passes2, unsigned long long *status,
+                   Ctrl *ctrl, cudaStream_t st) {
   const uint32_t grid = max(1u, (m_in + kOrientTile - 1) / kOrientTile);
-  k_orient<<<grid, kOrientThreads, 0, st>>>(keys, m_in, b, rank, okeys, outdeg, hist2, passes2,
-                                            status, ctrl);
+  k_orient<<<grid, kOrientThreads, 0, st>>>(keys, m_in, b, rank, okeys, hist2, passes2, status,
+                                            ctrl);
   note_launch();
 }
 

@@ -200,8 +200,8 @@ tc_status run_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t
     unsigned long long *status;
     uint32_t *ticket;
     next_pass(&status, &ticket);
-    launch_radix_pass(in, out, kOutKeys, nullptr, m, nullptr, 8 * p, 0u, 0, hist + 256 * p,
-                      status, ticket, ctrl, st);
+    launch_radix_pass(in, out, kOutKeys, nullptr, nullptr, m, nullptr, 8 * p, 0u, 0,
+                      hist + 256 * p, status, ticket, ctrl, st);
     uint64_t *x = in;
     in = out;
     out = x;
@@ -224,7 +224,7 @@ tc_status run_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t
       next_pass(&status, &ticket);
       const bool last = p == passes_r - 1;
       launch_radix_pass(vin, last ? (void *)rank : (void *)vout, last ? kOutRank : kOutKeys,
-                        nullptr, (uint32_t)n, nullptr, b + 8 * p, id_mask, 0,
+                        nullptr, nullptr, (uint32_t)n, nullptr, b + 8 * p, id_mask, 0,
                         hist + 256 * (kRankSlot + p), status, ticket, ctrl, st);
       uint64_t *x = vin;
       vin = vout;
@@ -234,8 +234,7 @@ tc_status run_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t
   pt.stop(TC_PHASE_RANK);
 
   pt.start(TC_PHASE_ORIENT);
-  launch_orient(in, m, b, rank, out, outdeg, hist + 256 * kSort2Slot, passes2, st_orient, ctrl,
-                st);
+  launch_orient(in, m, b, rank, out, hist + 256 * kSort2Slot, passes2, st_orient, ctrl, st);
   pt.stop(TC_PHASE_ORIENT);
 
   pt.start(TC_PHASE_SORT2);
@@ -252,8 +251,9 @@ tc_status run_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t
     next_pass(&status, &ticket);
     const bool last = p == passes2 - 1;
     uint32_t *row_target = last ? reinterpret_cast<uint32_t *>(out) + m : nullptr;
-    launch_radix_pass(in, out, last ? kOutColRow : kOutKeys, row_target, m, &ctrl->m, b + 8 * p,
-                      id_mask, b, hist + 256 * (kSort2Slot + p), status, ticket, ctrl, st);
+    launch_radix_pass(in, out, last ? kOutColRow : kOutKeys, row_target, last ? outdeg : nullptr,
+                      m, &ctrl->m, b + 8 * p, id_mask, b, hist + 256 * (kSort2Slot + p), status,
+                      ticket, ctrl, st);
     if (!last) {
       uint64_t *x = in;
       in = out;

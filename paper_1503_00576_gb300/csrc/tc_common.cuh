@@ -140,12 +140,13 @@ void note_launch();
 void launch_canon(const int32_t *src, const int32_t *dst, uint32_t m_in, int32_t n, int b,
                   int passes, uint64_t *keys, uint32_t *hist, Ctrl *ctrl, cudaStream_t st);
 // Output of a radix pass: the keys themselves; the column array (low bits,
-// to `out`) plus the row array (key >> owner_shift, to `row_out`); or the
-// rank scatter rank[low bits] = sorted position (to `out`).
+// to `out`) plus the row array (key >> owner_shift, to `row_out`) with the
+// out-degrees added to `outdeg`; or the rank scatter rank[low bits] =
+// sorted position (to `out`).
 enum RadixOut { kOutKeys = 0, kOutColRow = 1, kOutRank = 2 };
 void launch_radix_pass(const uint64_t *in, void *out, RadixOut mode, uint32_t *row_out,
-                       uint32_t n_keys_bound, const uint32_t *n_keys_dev, int shift,
-                       uint32_t col_mask, int owner_shift, const uint32_t *hist,
+                       int32_t *outdeg, uint32_t n_keys_bound, const uint32_t *n_keys_dev,
+                       int shift, uint32_t col_mask, int owner_shift, const uint32_t *hist,
                        unsigned long long *status, uint32_t *ticket, Ctrl *ctrl,
                        cudaStream_t st);
 // Keys deg(v) << b | v for every vertex, with the digit histograms of the
@@ -155,8 +156,8 @@ void launch_rank_keys(const int32_t *deg, int32_t n, int b, int passes, uint64_t
 void launch_unique_degree(const uint64_t *keys, uint32_t m_in, int b, int32_t *deg,
                           cudaStream_t st);
 void launch_orient(const uint64_t *keys, uint32_t m_in, int b, const int32_t *rank,
-                   uint64_t *okeys, int32_t *outdeg, uint32_t *hist2, int passes2,
-                   unsigned long long *status, Ctrl *ctrl, cudaStream_t st);
+                   uint64_t *okeys, uint32_t *hist2, int passes2, unsigned long long *status,
+                   Ctrl *ctrl, cudaStream_t st);
 // Exclusive scan counts[0..n) -> off[0..n].  With row_off != nullptr the
 // entries are partner groups and are binned into warp_list / cta_list /
 // big_list by the length of their hashed list.
