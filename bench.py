@@ -57,6 +57,9 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--total-only", action="store_true",
                    help="time tc_count (T only) instead of tc_count_per_vertex")
+    p.add_argument("--no-batched", action="store_true",
+                   help="skip the 4096-graph batched vs per-graph-loop comparison")
+    p.add_argument("--batch-graphs", type=int, default=4096)
     return p.parse_args()
 
 
@@ -239,6 +242,66 @@ def time_oracle(src, dst, n, pairs: int) -> tuple[float, int]:
     return time.perf_counter() - t0, pairs
 
 
+# ---------------------------------------------------------------- batched
+def run_batched(args, tc) -> dict:
+    """Graphs/s of the persistent CUDA-graph batch engines (autotuned) against
+    the per-graph launch loop, on the same device-resident graphs; the
+    per-graph counts must be identical."""
+    import numpy as np
+    import torch
+
+    import graphgen
+    from paper_1503_00576_gb300 import autotune, batching
+
+    t0 = time.time()
+    gb = graphgen.graph_batch(args.batch_graphs, 1005)
+    gen_s = time.time() - t0
+    G = len(gb)
+    m_total = int(gb.edge_offsets[-1])
+    s = torch.from_numpy(gb.src).cuda()
+    d = torch.from_numpy(gb.dst).cuda()
+    eo, vn = gb.edge_offsets, gb.vertex_counts
+    cap = batching.Capacity()
+    log("batched: %d graphs, %d pairs generated in %.1fs" % (G, m_total, gen_s))
+
+    # per-graph launch loop (one warm pass over a prefix first)
+    batching.count_plain(s, d, eo[:65], vn[:64])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = batching.count_plain(s, d, eo, vn)
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+
+    t0 = time.time()
+    tuned = autotune.tune_batches(s, d, eo, vn, cap)
+    tune_s = time.time() - t0
+    with batching.BatchCounter(cap, tuning=tuned["tuning"]) as bc:
+        ref = bc.count(s, d, eo, vn)  # warm
+        times = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            got = bc.count(s, d, eo, vn)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            assert np.array_equal(got, ref)
+    batched_s = min(times)
+    exact = bool(np.array_equal(ref, plain))
+    plan = batching.plan_subbatches(eo, vn, cap)
+    return {"graphs": G, "pairs": m_total, "triangles": int(ref.sum()),
+            "graphs_per_s": G / batched_s, "edges_per_s": m_total / batched_s,
+            "plain_graphs_per_s": G / plain_s, "plain_edges_per_s": m_total / plain_s,
+            "speedup_vs_plain": plain_s / batched_s, "counts_identical": exact,
+            "batched_s": batched_s, "plain_s": plain_s, "subbatches": len(plan),
+            "engines": 2, "capacity": {"pairs": cap.pairs, "vertices": cap.vertices,
+                                        "graphs": cap.graphs},
+            "tuning": tuned["tuning"], "tuning_cached": tuned["cached"],
+            "autotune_s": round(tune_s, 1), "autotune_ms": tuned["ms"],
+            "workload": "4096 graphs: half Erdos-Renyi, half R-MAT (.57,.19,.19), n "
+                        "log-uniform in [2^8, 2^18], mean degree uniform in [4, 64], "
+                        "seed 1005; inputs resident in HBM; wall clock, device synchronised"}
+
+
 # ---------------------------------------------------------------- arms
 def run_reference(args, world, rank, pg):
     import graphgen
@@ -368,6 +431,11 @@ def run_ours(args, world, rank, local, pg):
                "sample": "first %d pairs of the %s edge array (a uniform edge sample: the "
                          "pairs are in random draw order), single-threaded C oracle, "
                          "%.1f s" % (pairs, args.workload, dt)}
+    batched = None
+    if not args.no_batched and world == 1:
+        del s, d, t_out, deg_out
+        torch.cuda.empty_cache()
+        batched = run_batched(args, tc)
     steps_ms = {k: round(v[0] / args.steps, 4) for k, v in prof.items()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -382,7 +450,7 @@ def run_ours(args, world, rank, local, pg):
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roofline(prof, args.steps, m_in, m, n, args.workload, args.total_only),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-        "phase_ms_per_step": steps_ms,
+        "phase_ms_per_step": steps_ms, "batched": batched,
     }
     print(json.dumps(line), flush=True)
 

@@ -18,6 +18,9 @@ are not available, so seeded synthetic graphs of the same families stand in):
   rgg4m     random geometric graph, n=4,194,304, r=sqrt(32/(pi n))
   rmat24    R-MAT scale 24, draws until 180,000,000 distinct edges
   rmat22    R-MAT scale 22, draws until 45,000,000 distinct edges (profiling)
+  batch4096 4096 graphs, half Erdos-Renyi, half R-MAT (a,b,c = .57,.19,.19),
+            n log-uniform in [2^8, 2^18], mean degree uniform in [4, 64]
+            (graph_batch(4096, 1005))
 """
 from __future__ import annotations
 
@@ -69,6 +72,10 @@ def _load():
             lib.gg_rgg.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, i32p, i32p,
                                    ctypes.c_int64]
             lib.gg_rgg.restype = ctypes.c_int64
+            lib.gg_rmat_graph.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                          i32p, i32p]
+            lib.gg_rmat_graph.restype = ctypes.c_int64
             f64p = ctypes.POINTER(ctypes.c_double)
             lib.gg_rgg_point_coords.argtypes = [ctypes.c_int32, ctypes.c_uint64, f64p, f64p]
             lib.gg_rgg_point_coords.restype = None
@@ -111,6 +118,80 @@ def rmat_distinct(scale: int, m: int, seed: int, abc=RMAT_ABC):
     if rc < 0:
         raise ValueError("gg_rmat_distinct failed: %d" % rc)
     return src, dst
+
+
+def rmat_graph(n: int, m: int, seed: int, abc=RMAT_ABC):
+    """One R-MAT graph on n vertices (any n >= 2) with m distinct edges."""
+    src = np.empty(m, np.int32)
+    dst = np.empty(m, np.int32)
+    rc = _load().gg_rmat_graph(n, m, abc[0], abc[1], abc[2], seed, _ptr(src), _ptr(dst))
+    if rc < 0:
+        raise ValueError("gg_rmat_graph(n=%d, m=%d) failed: %d" % (n, m, rc))
+    return src, dst
+
+
+class GraphBatch:
+    """Many graphs stored back to back: graph g has pairs
+    src[edge_offsets[g]:edge_offsets[g+1]] (ids local to the graph) and
+    vertex_counts[g] vertices; kinds[g] is 'er' or 'rmat'."""
+
+    def __init__(self, src, dst, edge_offsets, vertex_counts, kinds, seeds):
+        self.src, self.dst = src, dst
+        self.edge_offsets = np.asarray(edge_offsets, np.int64)
+        self.vertex_counts = np.asarray(vertex_counts, np.int32)
+        self.kinds, self.seeds = list(kinds), list(seeds)
+
+    def __len__(self):
+        return len(self.vertex_counts)
+
+    def graph(self, g):
+        a, b = self.edge_offsets[g], self.edge_offsets[g + 1]
+        return self.src[a:b], self.dst[a:b], int(self.vertex_counts[g])
+
+
+def batch_params(count: int, seed: int, log2_n=(8, 18), degree=(4.0, 64.0)):
+    """Seeded sizes of a batch: n log-uniform in [2^lo, 2^hi], mean degree
+    uniform, m = floor(n d / 2) distinct edges; even g Erdos-Renyi, odd
+    R-MAT."""
+    rng = np.random.default_rng(seed)
+    lo, hi = log2_n
+    n = np.floor(np.exp2(lo + (hi - lo) * rng.random(count))).astype(np.int64)
+    d = degree[0] + (degree[1] - degree[0]) * rng.random(count)
+    m = np.floor(n * d / 2).astype(np.int64)
+    m = np.minimum(m, n * (n - 1) // 4)  # keep well inside the simple-graph limit
+    kinds = ["er" if g % 2 == 0 else "rmat" for g in range(count)]
+    seeds = [int(seed) * 1_000_003 + g for g in range(count)]
+    return n.astype(np.int32), m, kinds, seeds
+
+
+def graph_batch(count: int, seed: int, log2_n=(8, 18), degree=(4.0, 64.0),
+                threads: int = 0) -> GraphBatch:
+    """Generate a batch of `count` graphs (in parallel; deterministic)."""
+    import concurrent.futures as cf
+
+    n, m, kinds, seeds = batch_params(count, seed, log2_n, degree)
+    eo = np.zeros(count + 1, np.int64)
+    eo[1:] = np.cumsum(m)
+    src = np.empty(int(eo[-1]), np.int32)
+    dst = np.empty(int(eo[-1]), np.int32)
+    lib = _load()
+
+    def one(g):
+        a, b = int(eo[g]), int(eo[g + 1])
+        ps = src[a:b].ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        pd = dst[a:b].ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        if kinds[g] == "er":
+            rc = lib.gg_er(int(n[g]), b - a, seeds[g], ps, pd)
+        else:
+            rc = lib.gg_rmat_graph(int(n[g]), b - a, RMAT_ABC[0], RMAT_ABC[1], RMAT_ABC[2],
+                                   seeds[g], ps, pd)
+        if rc < 0:
+            raise ValueError("graph %d (%s, n=%d, m=%d) failed: %d" % (g, kinds[g], n[g], b - a, rc))
+
+    workers = threads or (os.cpu_count() or 4)
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        list(ex.map(one, range(count)))
+    return GraphBatch(src, dst, eo, n, kinds, seeds)
 
 
 def rgg_radius(n: int, mean_degree: float = 32.0) -> float:

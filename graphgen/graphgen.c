@@ -359,6 +359,64 @@ int64_t gg_rmat_distinct(int scale, int64_t m_target, double a, double b, double
   }
 }
 
+/* One R-MAT graph on n vertices (n need not be a power of two): draws at
+ * scale ceil(log2 n), pairs with an id >= n rejected, ids permuted within
+ * [0, n), until m distinct non-loop undirected edges, each written once in
+ * its first direction.  Single-threaded (batches run many in parallel).
+ * Returns the draws used, or -1 (bad arguments), -2 (allocation failure),
+ * -4 (no m distinct edges within 256 m + 2^20 draws). */
+int64_t gg_rmat_graph(int32_t n, int64_t m, double a, double b, double c, uint64_t seed,
+                      int32_t *src, int32_t *dst) {
+  if (n < 2 || m < 0) return -1;
+  if (m == 0) return 0;
+  if ((double)m > 0.5 * (double)n * (double)(n - 1)) return -1;
+  int scale = 1;
+  while (((int64_t)1 << scale) < n) ++scale;
+  gg_rmat_ctx ctx;
+  if (gg_rmat_setup(&ctx, scale, a, b, c, seed)) return -1;
+  int32_t *perm = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  uint64_t cap = gg_pow2_at_least((uint64_t)m * 2 + 16);
+  uint64_t *tab = (uint64_t *)calloc(cap, sizeof(uint64_t));
+  if (!perm || !tab) { free(perm); free(tab); return -2; }
+  gg_permutation(perm, n, gg_key(seed, GG_S_RMAT_PERM));
+  const int words = (scale + 1) / 2;
+  const int64_t limit = 256 * m + (1 << 20);
+  int64_t got = 0, draws = 0;
+  while (got < m) {
+    if (draws >= limit) { free(perm); free(tab); return -4; }
+    const int64_t i = draws++;
+    uint32_t u = 0, v = 0;
+    uint64_t w = 0;
+    for (int lvl = 0; lvl < scale; ++lvl) {
+      if ((lvl & 1) == 0) w = gg_rand(ctx.key, (uint64_t)i * (uint64_t)words + (uint64_t)(lvl >> 1));
+      uint64_t r = (lvl & 1) ? (w >> 32) : (w & 0xffffffffULL);
+      uint32_t bu, bv;
+      if (r < ctx.ta) { bu = 0; bv = 0; }
+      else if (r < ctx.tab) { bu = 0; bv = 1; }
+      else if (r < ctx.tabc) { bu = 1; bv = 0; }
+      else { bu = 1; bv = 1; }
+      u = (u << 1) | bu;
+      v = (v << 1) | bv;
+    }
+    if (u >= (uint32_t)n || v >= (uint32_t)n || u == v) continue;
+    uint64_t k = gg_pair_key(u, v) + 1;
+    uint64_t h = gg_mix(k) & (cap - 1);
+    int fresh = 1;
+    while (tab[h]) {
+      if (tab[h] == k) { fresh = 0; break; }
+      h = (h + 1) & (cap - 1);
+    }
+    if (!fresh) continue;
+    tab[h] = k;
+    src[got] = perm[u];
+    dst[got] = perm[v];
+    ++got;
+  }
+  free(perm);
+  free(tab);
+  return draws;
+}
+
 /* ------------------------------------------------------------------ */
 /* random geometric graph                                               */
 /* ------------------------------------------------------------------ */

@@ -129,6 +129,77 @@ tc_status tc_count_ws(const int32_t *src, const int32_t *dst, int64_t m, int32_t
                       tc_stream_t stream, void *ws, size_t ws_bytes, uint64_t *total_out);
 
 /*
+ * Tuning of the counting layout (process-wide default for the calls above;
+ * engines take their own).  An autotuner varies these; counts never depend
+ * on them.
+ *   warp_max_list, warp_max_partners: a partner group (the edges whose longer
+ *     forward list is N+(h)) is counted by one warp when |N+(h)| and its
+ *     partner count are at most these (warp_max_list is capped at 128),
+ *     otherwise by a CTA.  Defaults 128 and 64.
+ *   heavy_ratio_pct (>= 100): the intersection strategy switch.  Edge (u,v)
+ *     with owner u is counted by hashing N+(v) and streaming N+(u) when
+ *     |N+(v)| * 100 > |N+(u)| * heavy_ratio_pct, else by hashing N+(u) and
+ *     streaming N+(v).  100 (default) always streams the shorter list.
+ * tc_set_tuning(NULL) restores the defaults.
+ */
+typedef struct tc_tuning {
+  int32_t warp_max_list;
+  int32_t warp_max_partners;
+  int32_t heavy_ratio_pct;
+} tc_tuning;
+tc_status tc_set_tuning(const tc_tuning *tuning);
+tc_status tc_get_tuning(tc_tuning *out);
+
+/*
+ * Batched counting: the triangle counts of G graphs in one pass.  The paper
+ * counts one graph per run; a batch is counted as the disjoint union of its
+ * graphs (ids shifted per graph), which has exactly the union of their
+ * triangles, so every per-graph count equals the graph's count alone.
+ *   src, dst        device int32 pairs of all graphs, graph g's pairs at
+ *                   [edge_offsets[g], edge_offsets[g+1]) with ids local to
+ *                   the graph, 0 <= id < vertex_counts[g]
+ *   edge_offsets    HOST int64[G+1], edge_offsets[0] = 0, non-decreasing
+ *   vertex_counts   HOST int32[G]
+ *   totals_out      HOST uint64[G]: triangles of each graph
+ * Limits: total pairs and total vertices <= 2^31 - 1 (TC_ERR_OVERFLOW).  An
+ * id out of range in any graph fails the whole batch (TC_ERR_ID_RANGE).
+ * Synchronises.
+ */
+tc_status tc_count_batch(const int32_t *src, const int32_t *dst, int32_t num_graphs,
+                         const int64_t *edge_offsets, const int32_t *vertex_counts,
+                         tc_stream_t stream, uint64_t *totals_out);
+
+/*
+ * Persistent batch engine: device buffers for max_pairs pairs, max_vertices
+ * union vertices and max_graphs graphs, allocated once, and the whole batch
+ * pipeline captured once as a CUDA graph and replayed for every batch
+ * (padding pairs past a batch's end are skipped, so the shape never changes).
+ *   tc_engine_create   tuning NULL: the process default at creation.
+ *   tc_engine_submit   copies the batch's pairs (host or device memory, per
+ *                      inputs_on_host) into the engine and launches the graph
+ *                      on the engine's own stream; returns without waiting.
+ *                      Host inputs must stay valid until tc_engine_wait;
+ *                      page-locked ones overlap with other work.
+ *   tc_engine_wait     waits for the submitted batch; totals_out HOST
+ *                      uint64[G] (may be NULL).
+ *   tc_engine_count    submit + wait.
+ * One batch in flight per engine; an engine is used by one thread at a time
+ * and on the device that was current at creation.  Two engines overlap.
+ */
+typedef struct tc_engine tc_engine;
+tc_status tc_engine_create(int64_t max_pairs, int32_t max_vertices, int32_t max_graphs,
+                           const tc_tuning *tuning, tc_engine **out);
+tc_status tc_engine_submit(tc_engine *engine, const int32_t *src, const int32_t *dst,
+                           int32_t inputs_on_host, int32_t num_graphs,
+                           const int64_t *edge_offsets, const int32_t *vertex_counts);
+tc_status tc_engine_wait(tc_engine *engine, uint64_t *totals_out);
+tc_status tc_engine_count(tc_engine *engine, const int32_t *src, const int32_t *dst,
+                          int32_t inputs_on_host, int32_t num_graphs,
+                          const int64_t *edge_offsets, const int32_t *vertex_counts,
+                          uint64_t *totals_out);
+tc_status tc_engine_destroy(tc_engine *engine);
+
+/*
  * Allocation-free count, for callers that cannot allocate device memory
  * while they run: for example a process whose own pool allocator reserves
  * all device memory at start-up and forbids driver allocations afterwards,

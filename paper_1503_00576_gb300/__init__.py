@@ -15,6 +15,10 @@ Functions mirror the C ABI names:
     tc_count_host(src, dst, n)             -> T          (numpy in, host copies timed inside)
     tc_count_per_vertex_host(src, dst, n)  -> (T, t, deg) (numpy in and out)
     tc_workspace_bytes(m, n), tc_count_ws(src, dst, n, ws)
+    tc_count_batch(src, dst, edge_offsets, vertex_counts) -> uint64[G]
+    Engine(max_pairs, max_vertices, max_graphs).count(...)  (tc_engine_*)
+    tc_set_tuning(dict), tc_get_tuning()
+    tc_count_noalloc(src, dst, n)
     tc_launch_count(), tc_profile_enable(on), tc_profile_read(reset)
 
 ``src`` / ``dst`` are int32 CUDA tensors of the same length (pair i is the
@@ -43,10 +47,23 @@ PHASES = ("canon", "sort1", "degree", "rank", "orient", "sort2", "offsets", "gro
 
 # Every symbol include/tc.h declares.
 EXPORTS = ("tc_count", "tc_count_per_vertex", "tc_clustering", "tc_count_host",
-           "tc_count_per_vertex_host", "tc_workspace_bytes", "tc_count_ws", "tc_count_noalloc",
-           "tc_last_error",
-           "tc_status_string", "tc_last_error_detail", "tc_launch_count", "tc_profile_enable",
-           "tc_profile_read", "tc_phase_name")
+           "tc_count_per_vertex_host", "tc_workspace_bytes", "tc_count_ws", "tc_set_tuning",
+           "tc_get_tuning", "tc_count_batch", "tc_engine_create", "tc_engine_submit",
+           "tc_engine_wait", "tc_engine_count", "tc_engine_destroy", "tc_count_noalloc",
+           "tc_last_error", "tc_status_string", "tc_last_error_detail", "tc_launch_count",
+           "tc_profile_enable", "tc_profile_read", "tc_phase_name")
+
+
+class Tuning(ctypes.Structure):
+    """tc_tuning: how partner groups map onto warps/CTAs and which list is hashed."""
+    _fields_ = [("warp_max_list", ctypes.c_int32), ("warp_max_partners", ctypes.c_int32),
+                ("heavy_ratio_pct", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+DEFAULT_TUNING = {"warp_max_list": 128, "warp_max_partners": 64, "heavy_ratio_pct": 100}
 
 
 class TCError(RuntimeError):
@@ -75,6 +92,14 @@ def _bind(lib):
         "tc_workspace_bytes": ([i64, i32], sz),
         "tc_count_ws": ([vp, vp, i64, i32, vp, vp, sz, c.POINTER(u64)], c.c_int),
         "tc_count_noalloc": ([vp, vp, i64, i32, vp, c.POINTER(u64)], c.c_int),
+        "tc_set_tuning": ([c.POINTER(Tuning)], c.c_int),
+        "tc_get_tuning": ([c.POINTER(Tuning)], c.c_int),
+        "tc_count_batch": ([vp, vp, i32, vp, vp, vp, vp], c.c_int),
+        "tc_engine_create": ([i64, i32, i32, c.POINTER(Tuning), c.POINTER(vp)], c.c_int),
+        "tc_engine_submit": ([vp, vp, vp, i32, i32, vp, vp], c.c_int),
+        "tc_engine_wait": ([vp, vp], c.c_int),
+        "tc_engine_count": ([vp, vp, vp, i32, i32, vp, vp, vp], c.c_int),
+        "tc_engine_destroy": ([vp], c.c_int),
         "tc_last_error": ([], c.c_int),
         "tc_status_string": ([c.c_int], c.c_char_p),
         "tc_last_error_detail": ([], c.c_char_p),
@@ -264,6 +289,133 @@ def tc_count_ws(src, dst, n: int, ws, stream=None) -> int:
                              ws.numel() * ws.element_size(), ctypes.byref(total))
     _check(rc)
     return int(total.value)
+
+
+def tc_set_tuning(tuning=None) -> None:
+    """Process-wide tuning for subsequent calls (None restores the defaults)."""
+    if tuning is None:
+        _check(load_library().tc_set_tuning(None))
+        return
+    t = Tuning(**{**DEFAULT_TUNING, **dict(tuning)})
+    _check(load_library().tc_set_tuning(ctypes.byref(t)))
+
+
+def tc_get_tuning() -> dict:
+    t = Tuning()
+    _check(load_library().tc_get_tuning(ctypes.byref(t)))
+    return t.as_dict()
+
+
+def _batch_arrays(edge_offsets, vertex_counts):
+    eo = np.ascontiguousarray(edge_offsets, dtype=np.int64)
+    vn = np.ascontiguousarray(vertex_counts, dtype=np.int32)
+    if eo.ndim != 1 or vn.ndim != 1 or len(eo) != len(vn) + 1:
+        raise ValueError("edge_offsets must have one entry more than vertex_counts")
+    return eo, vn
+
+
+def tc_count_batch(src, dst, edge_offsets, vertex_counts, stream=None) -> np.ndarray:
+    """Triangles of each graph of a batch (uint64[G]).
+
+    ``src``/``dst``: int32 CUDA tensors holding every graph's pairs back to
+    back, graph g at [edge_offsets[g], edge_offsets[g+1]) with ids local to
+    the graph (< vertex_counts[g]).  The batch is counted as one disjoint
+    union in a single pass."""
+    torch = _torch()
+    dev = _edges(src, dst)
+    eo, vn = _batch_arrays(edge_offsets, vertex_counts)
+    if eo[-1] > src.numel():
+        raise ValueError("edge_offsets run past the edge arrays")
+    out = np.zeros(len(vn), np.uint64)
+    lib = load_library()
+    with torch.cuda.device(dev):
+        rc = lib.tc_count_batch(src.data_ptr(), dst.data_ptr(), len(vn), eo.ctypes.data,
+                                vn.ctypes.data, _stream_of(stream, dev), out.ctypes.data)
+    _check(rc)
+    return out
+
+
+class Engine:
+    """Persistent batch engine (tc_engine_*): fixed device buffers and a
+    CUDA graph of the whole batch pipeline, replayed for every batch.
+
+    ``submit`` returns immediately (the batch runs on the engine's stream);
+    ``wait`` returns the per-graph counts.  Host inputs must stay alive (and
+    unmodified) until ``wait``; page-locked ones overlap best."""
+
+    def __init__(self, max_pairs: int, max_vertices: int, max_graphs: int, tuning=None,
+                 device=None):
+        torch = _torch()
+        self.lib = load_library()
+        self.max_pairs, self.max_vertices, self.max_graphs = max_pairs, max_vertices, max_graphs
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        self.tuning = {**DEFAULT_TUNING, **(dict(tuning) if tuning else {})}
+        t = Tuning(**self.tuning)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = self.lib.tc_engine_create(max_pairs, max_vertices, max_graphs, ctypes.byref(t),
+                                           ctypes.byref(h))
+        _check(rc)
+        self._h = h
+        self._pending = None
+
+    def submit(self, src, dst, edge_offsets, vertex_counts) -> None:
+        torch = _torch()
+        eo, vn = _batch_arrays(edge_offsets, vertex_counts)
+        if isinstance(src, np.ndarray):
+            s = np.ascontiguousarray(src, np.int32)
+            d = np.ascontiguousarray(dst, np.int32)
+            ps, pd, on_host = s.ctypes.data, d.ctypes.data, 1
+            keep = (s, d)
+        elif isinstance(src, torch.Tensor) and not src.is_cuda:
+            s, d = src.contiguous(), dst.contiguous()
+            if s.dtype != torch.int32 or d.dtype != torch.int32:
+                raise TypeError("edge arrays must be int32")
+            ps, pd, on_host = s.data_ptr(), d.data_ptr(), 1
+            keep = (s, d)
+        else:
+            _edges(src, dst)
+            ps, pd, on_host = src.data_ptr(), dst.data_ptr(), 0
+            keep = (src, dst)
+        if eo[-1] > (len(keep[0]) if on_host else keep[0].numel()):
+            raise ValueError("edge_offsets run past the edge arrays")
+        with torch.cuda.device(self.device):
+            rc = self.lib.tc_engine_submit(self._h, ps, pd, on_host, len(vn), eo.ctypes.data,
+                                           vn.ctypes.data)
+        _check(rc)
+        self._pending = (keep, eo, vn)
+
+    def wait(self) -> np.ndarray:
+        if self._pending is None:
+            raise RuntimeError("no batch submitted")
+        n = len(self._pending[2])
+        out = np.zeros(n, np.uint64)
+        rc = self.lib.tc_engine_wait(self._h, out.ctypes.data)
+        self._pending = None
+        _check(rc)
+        return out
+
+    def count(self, src, dst, edge_offsets, vertex_counts) -> np.ndarray:
+        self.submit(src, dst, edge_offsets, vertex_counts)
+        return self.wait()
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self.lib.tc_engine_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 TC_NOALLOC_SCRATCH_BYTES = 32 << 20

@@ -249,8 +249,8 @@ __device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__res
     }
   }
   found_total += found;
+  found_group += found;
   if (PV) {
-    found_group += found;
     if (run) atomicAdd(&ws.lc[run_r], run);
     __syncwarp();
     if (lane < k && ws.lc[lane])
@@ -275,7 +275,7 @@ template <bool PV, int THREADS, int SLOTS>
 __device__ __forceinline__ void cta_groups(const Lists &g, const int32_t *__restrict__ list,
                                            uint32_t n_list, uint32_t *cursor, int32_t *tab,
                                            uint32_t *cnt, WarpScratch *s_ws, CtaShared &sh,
-                                           int64_t *t, uint64_t &found_total) {
+                                           int64_t *t, int64_t *tg, uint64_t &found_total) {
   constexpr int WARPS = THREADS / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (;;) {
@@ -314,12 +314,16 @@ __device__ __forceinline__ void cta_groups(const Lists &g, const int32_t *__rest
       drain_table<PV>(tab, cnt, log_slots, tid, THREADS, t);
       if (s0 + seg_len < hd) __syncthreads();  // next segment refills the table
     }
-    if (PV) {
+    if (PV || tg) {
       found_group = warp_sum_u64(found_group);
       if (lane == 0 && found_group) atomicAdd(&sh.groupsum, (unsigned long long)found_group);
     }
     __syncthreads();
-    if (PV && tid == 0 && sh.groupsum) atomicAdd((unsigned long long *)&t[h], sh.groupsum);
+    // t(h) gains every triangle of the group; so does the group total
+    if (tid == 0 && sh.groupsum) {
+      if (PV) atomicAdd((unsigned long long *)&t[h], sh.groupsum);
+      else if (tg) atomicAdd((unsigned long long *)&tg[h], sh.groupsum);
+    }
   }
 }
 
@@ -329,7 +333,7 @@ template <bool PV>
 __device__ __forceinline__ void warp_groups(const Lists &g, const int32_t *__restrict__ list,
                                             uint32_t n_list, uint32_t *cursor, int32_t *wtab,
                                             uint32_t *wcnt, WarpScratch &ws, int64_t *t,
-                                            uint64_t &found_total) {
+                                            int64_t *tg, uint64_t &found_total) {
   const int lane = threadIdx.x & 31;
   for (;;) {
     uint32_t g0 = 0;
@@ -348,9 +352,10 @@ __device__ __forceinline__ void warp_groups(const Lists &g, const int32_t *__res
       for (int32_t c0 = 0; c0 < np; c0 += 32)
         probe_chunk<PV>(g, g.part + pb, np, c0, 32, wtab, wcnt, log_slots, ws, t, found_total,
                         found_group);
-      if (PV) {
+      if (PV || tg) {
         found_group = warp_sum_u64(found_group);
-        if (lane == 0 && found_group) atomicAdd((unsigned long long *)&t[h], found_group);
+        if (lane == 0 && found_group)
+          atomicAdd((unsigned long long *)(PV ? &t[h] : &tg[h]), (unsigned long long)found_group);
       }
       __syncwarp();
       drain_table<PV>(wtab, wcnt, log_slots, lane, 32, t);
@@ -363,7 +368,7 @@ __device__ __forceinline__ void warp_groups(const Lists &g, const int32_t *__res
 template <bool PV>
 __global__ void __launch_bounds__(kMainThreads)
 k_count(Lists g, const int32_t *__restrict__ warp_list, const int32_t *__restrict__ cta_list,
-        Ctrl *ctrl, int64_t *t) {
+        Ctrl *ctrl, int64_t *t, int64_t *tg) {
   __shared__ int32_t s_tab[kMainSlots];
   __shared__ uint32_t s_cnt[PV ? kMainSlots : 1];
   __shared__ WarpScratch s_ws[kMainWarps];
@@ -372,10 +377,10 @@ k_count(Lists g, const int32_t *__restrict__ warp_list, const int32_t *__restric
   clear_table<PV>(s_tab, s_cnt, kMainSlots, tid, kMainThreads);
   uint64_t found_total = 0;
   cta_groups<PV, kMainThreads, kMainSlots>(g, cta_list, ctrl->n_cta_groups,
-                                           &ctrl->next_cta_group, s_tab, s_cnt, s_ws, s_sh, t,
+                                           &ctrl->next_cta_group, s_tab, s_cnt, s_ws, s_sh, t, tg,
                                            found_total);
   warp_groups<PV>(g, warp_list, ctrl->n_warp_groups, &ctrl->next_warp_group,
-                  s_tab + warp * kWarpSlots, s_cnt + warp * kWarpSlots, s_ws[warp], t,
+                  s_tab + warp * kWarpSlots, s_cnt + warp * kWarpSlots, s_ws[warp], t, tg,
                   found_total);
   found_total = warp_sum_u64(found_total);
   if (lane == 0 && found_total) atomicAdd(&ctrl->total, (unsigned long long)found_total);
@@ -384,7 +389,8 @@ k_count(Lists g, const int32_t *__restrict__ warp_list, const int32_t *__restric
 // Groups whose hashed list is longer than kCtaMaxRow (rare).
 template <bool PV>
 __global__ void __launch_bounds__(kBigThreads)
-k_count_big(Lists g, const int32_t *__restrict__ big_list, Ctrl *ctrl, int64_t *t) {
+k_count_big(Lists g, const int32_t *__restrict__ big_list, Ctrl *ctrl, int64_t *t,
+            int64_t *tg) {
   extern __shared__ __align__(16) unsigned char smem[];
   int32_t *tab = reinterpret_cast<int32_t *>(smem);
   uint32_t *cnt = reinterpret_cast<uint32_t *>(smem + 4 * kBigSlots);
@@ -394,7 +400,7 @@ k_count_big(Lists g, const int32_t *__restrict__ big_list, Ctrl *ctrl, int64_t *
   clear_table<PV>(tab, cnt, kBigSlots, tid, kBigThreads);
   uint64_t found_total = 0;
   cta_groups<PV, kBigThreads, kBigSlots>(g, big_list, ctrl->n_big_groups, &ctrl->next_big_group,
-                                         tab, cnt, s_ws, s_sh, t, found_total);
+                                         tab, cnt, s_ws, s_sh, t, tg, found_total);
   found_total = warp_sum_u64(found_total);
   if (lane == 0 && found_total) atomicAdd(&ctrl->total, (unsigned long long)found_total);
 }
@@ -435,6 +441,26 @@ k_gather_counts(const int64_t *__restrict__ t_rank, const int32_t *__restrict__ 
   const uint32_t stride = gridDim.x * kClusterThreads;
   for (uint32_t v = blockIdx.x * kClusterThreads + threadIdx.x; v < (uint32_t)n; v += stride)
     t_out[v] = __ldg(t_rank + __ldg(rank + v));
+}
+
+// Per-graph sums over union vertex ranges: one warp per graph.
+__global__ void __launch_bounds__(kClusterThreads)
+k_segment_sums(const int64_t *__restrict__ vals, const BatchDesc *__restrict__ batch,
+               int32_t num_graphs_bound, int32_t divisor, unsigned long long *__restrict__ out) {
+  const int32_t ng = batch->num_graphs;
+  const int32_t *vo = batch->voff;
+  const int lane = threadIdx.x & 31;
+  const int32_t warps = gridDim.x * (kClusterThreads / 32);
+  for (int32_t gi = (blockIdx.x * kClusterThreads + threadIdx.x) >> 5; gi < num_graphs_bound;
+       gi += warps) {
+    unsigned long long s = 0;
+    if (gi < ng) {
+      const int32_t b = __ldg(vo + gi), e = __ldg(vo + gi + 1);
+      for (int32_t v = b + lane; v < e; v += 32) s += (unsigned long long)__ldg(vals + v);
+    }
+    s = warp_sum_u64(s);
+    if (lane == 0) out[gi] = gi < ng ? s / (unsigned long long)divisor : 0ull;
+  }
 }
 
 // transitivity = 3T / wedges with T = (sum t) / 3: one float64 division.
@@ -488,10 +514,17 @@ cudaError_t count_grid(bool pv, CountGrid *out) {
 
 }  // namespace
 
+cudaError_t prepare_count_kernels() {
+  CountGrid cg;
+  cudaError_t e = count_grid(true, &cg);
+  if (e == cudaSuccess) e = count_grid(false, &cg);
+  return e;
+}
+
 cudaError_t launch_count(const int32_t *off, const int32_t *col, const int32_t *goff,
                          const int32_t *part, const int32_t *warp_groups,
                          const int32_t *cta_groups, const int32_t *big_groups, Ctrl *ctrl,
-                         int64_t *t, cudaStream_t st) {
+                         int64_t *t, int64_t *tg, cudaStream_t st) {
   const bool pv = t != nullptr;
   CountGrid cg;
   cudaError_t e = count_grid(pv, &cg);
@@ -500,11 +533,15 @@ cudaError_t launch_count(const int32_t *off, const int32_t *col, const int32_t *
   const Lists g{off, col, goff, part};
   // the long lists first, on their own wide CTAs
   if (pv) {
-    k_count_big<true><<<cg.big_blocks, kBigThreads, big_smem, st>>>(g, big_groups, ctrl, t);
-    k_count<true><<<cg.main_blocks, kMainThreads, 0, st>>>(g, warp_groups, cta_groups, ctrl, t);
+    k_count_big<true><<<cg.big_blocks, kBigThreads, big_smem, st>>>(g, big_groups, ctrl, t,
+                                                                    nullptr);
+    k_count<true><<<cg.main_blocks, kMainThreads, 0, st>>>(g, warp_groups, cta_groups, ctrl, t,
+                                                           nullptr);
   } else {
-    k_count_big<false><<<cg.big_blocks, kBigThreads, big_smem, st>>>(g, big_groups, ctrl, t);
-    k_count<false><<<cg.main_blocks, kMainThreads, 0, st>>>(g, warp_groups, cta_groups, ctrl, t);
+    k_count_big<false><<<cg.big_blocks, kBigThreads, big_smem, st>>>(g, big_groups, ctrl,
+                                                                     nullptr, tg);
+    k_count<false><<<cg.main_blocks, kMainThreads, 0, st>>>(g, warp_groups, cta_groups, ctrl,
+                                                            nullptr, tg);
   }
   note_launch();
   note_launch();
@@ -530,6 +567,15 @@ void launch_gather_counts(const int64_t *t_rank, const int32_t *rank, int32_t n,
   const uint32_t want = ((uint32_t)n + kClusterThreads * 4 - 1) / (kClusterThreads * 4);
   const uint32_t grid = max(1u, min(want, (uint32_t)(sms > 0 ? sms : 1) * 8));
   k_gather_counts<<<grid, kClusterThreads, 0, st>>>(t_rank, rank, n, t_out);
+  note_launch();
+}
+
+void launch_segment_sums(const int64_t *vals, const BatchDesc *batch, int32_t num_graphs,
+                         int32_t divisor, unsigned long long *out, cudaStream_t st) {
+  const uint32_t warps_per_block = kClusterThreads / 32;
+  const uint32_t grid =
+      max(1u, min(((uint32_t)num_graphs + warps_per_block - 1) / warps_per_block, 4096u));
+  k_segment_sums<<<grid, kClusterThreads, 0, st>>>(vals, batch, num_graphs, divisor, out);
   note_launch();
 }
 

@@ -23,11 +23,13 @@ namespace {
 
 constexpr int kGroupThreads = 256;
 
+// heavy_ratio_pct = 100: the longer list is always the one hashed; larger
+// values keep an edge at its owner unless v's list is that much longer.
 __device__ __forceinline__ void split_edge(const int32_t *__restrict__ off, int32_t u, int32_t v,
-                                           int32_t &h, int32_t &l) {
-  const int32_t du = __ldg(off + u + 1) - __ldg(off + u);
-  const int32_t dv = __ldg(off + v + 1) - __ldg(off + v);
-  if (dv > du) {
+                                           int32_t heavy_ratio_pct, int32_t &h, int32_t &l) {
+  const int64_t du = __ldg(off + u + 1) - __ldg(off + u);
+  const int64_t dv = __ldg(off + v + 1) - __ldg(off + v);
+  if (dv * 100 > du * heavy_ratio_pct) {
     h = v;
     l = u;
   } else {
@@ -38,12 +40,13 @@ __device__ __forceinline__ void split_edge(const int32_t *__restrict__ off, int3
 
 __global__ void __launch_bounds__(kGroupThreads)
 k_group_count(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
-              const int32_t *__restrict__ off, const Ctrl *__restrict__ ctrl, int32_t *gcnt) {
+              const int32_t *__restrict__ off, int32_t heavy_ratio_pct,
+              const Ctrl *__restrict__ ctrl, int32_t *gcnt) {
   const uint32_t m = ctrl->m;
   const uint32_t stride = gridDim.x * kGroupThreads;
   for (uint32_t e = blockIdx.x * kGroupThreads + threadIdx.x; e < m; e += stride) {
     int32_t h, l;
-    split_edge(off, __ldg(row + e), __ldg(col + e), h, l);
+    split_edge(off, __ldg(row + e), __ldg(col + e), heavy_ratio_pct, h, l);
     const uint32_t active = __activemask();
     const uint32_t peers = __match_any_sync(active, h);
     const int lane = threadIdx.x & 31;
@@ -54,13 +57,14 @@ k_group_count(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
 // gcnt[h] holds the group sizes on entry and is counted down to 0.
 __global__ void __launch_bounds__(kGroupThreads)
 k_group_fill(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
-             const int32_t *__restrict__ off, const Ctrl *__restrict__ ctrl,
-             const int32_t *__restrict__ goff, int32_t *gcnt, int32_t *__restrict__ part) {
+             const int32_t *__restrict__ off, int32_t heavy_ratio_pct,
+             const Ctrl *__restrict__ ctrl, const int32_t *__restrict__ goff, int32_t *gcnt,
+             int32_t *__restrict__ part) {
   const uint32_t m = ctrl->m;
   const uint32_t stride = gridDim.x * kGroupThreads;
   for (uint32_t e = blockIdx.x * kGroupThreads + threadIdx.x; e < m; e += stride) {
     int32_t h, l;
-    split_edge(off, __ldg(row + e), __ldg(col + e), h, l);
+    split_edge(off, __ldg(row + e), __ldg(col + e), heavy_ratio_pct, h, l);
     const uint32_t active = __activemask();
     const uint32_t peers = __match_any_sync(active, h);
     const int lane = threadIdx.x & 31;
@@ -84,16 +88,18 @@ uint32_t group_grid(uint32_t m_bound) {
 }  // namespace
 
 void launch_group_count(const int32_t *row, const int32_t *col, const int32_t *off,
-                        uint32_t m_bound, Ctrl *ctrl, int32_t *gcnt, cudaStream_t st) {
-  k_group_count<<<group_grid(m_bound), kGroupThreads, 0, st>>>(row, col, off, ctrl, gcnt);
+                        uint32_t m_bound, int32_t heavy_ratio_pct, Ctrl *ctrl, int32_t *gcnt,
+                        cudaStream_t st) {
+  k_group_count<<<group_grid(m_bound), kGroupThreads, 0, st>>>(row, col, off, heavy_ratio_pct,
+                                                               ctrl, gcnt);
   note_launch();
 }
 
 void launch_group_fill(const int32_t *row, const int32_t *col, const int32_t *off,
-                       uint32_t m_bound, Ctrl *ctrl, const int32_t *goff, int32_t *gcnt,
-                       int32_t *part, cudaStream_t st) {
-  k_group_fill<<<group_grid(m_bound), kGroupThreads, 0, st>>>(row, col, off, ctrl, goff, gcnt,
-                                                              part);
+                       uint32_t m_bound, int32_t heavy_ratio_pct, Ctrl *ctrl,
+                       const int32_t *goff, int32_t *gcnt, int32_t *part, cudaStream_t st) {
+  k_group_fill<<<group_grid(m_bound), kGroupThreads, 0, st>>>(row, col, off, heavy_ratio_pct,
+                                                              ctrl, goff, gcnt, part);
   note_launch();
 }
 

@@ -145,24 +145,46 @@ constexpr int kCanonThreads = 256;
 
 __global__ void __launch_bounds__(kCanonThreads)
 k_canon(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, uint32_t m_in,
-        int32_t n, int b, int passes, uint64_t *__restrict__ keys, uint32_t *__restrict__ hist,
-        Ctrl *ctrl) {
+        int32_t n, int b, int passes, const BatchDesc *__restrict__ batch,
+        uint64_t *__restrict__ keys, uint32_t *__restrict__ hist, Ctrl *ctrl) {
   __shared__ uint32_t sh[kMaxSort1Passes * 256];
   for (int i = threadIdx.x; i < passes * 256; i += kCanonThreads) sh[i] = 0;
   __syncthreads();
   const uint64_t sentinel = (1ull << (2 * b)) - 1;  // > every valid key; 2b <= 62
+  // batch: graph g owns pairs [eo[g], eo[g+1]) and union ids from vo[g]
+  int32_t ng = 0;
+  const int32_t *eo = nullptr, *vo = nullptr;
+  uint32_t m_real = m_in;
+  if (batch) {
+    ng = batch->num_graphs;
+    eo = batch->edge_off;
+    vo = batch->voff;
+    m_real = min((uint32_t)__ldg(eo + ng), m_in);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->m_in = m_real;
   bool bad = false;
   const uint32_t stride = gridDim.x * kCanonThreads;
-  for (uint32_t i = blockIdx.x * kCanonThreads + threadIdx.x; i < m_in; i += stride) {
-    const int32_t u = __ldg(src + i), v = __ldg(dst + i);
+  // pairs past m_real are batch padding: not keyed, not sorted
+  for (uint32_t i = blockIdx.x * kCanonThreads + threadIdx.x; i < m_real; i += stride) {
+    int32_t u = __ldg(src + i), v = __ldg(dst + i);
+    int32_t lim = n, shift = 0;
+    if (batch) {
+      int32_t lo = 0, hi = ng;  // the last graph g with eo[g] <= i
+      while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if ((uint32_t)__ldg(eo + mid) <= i) lo = mid; else hi = mid;
+      }
+      shift = __ldg(vo + lo);
+      lim = __ldg(vo + lo + 1) - shift;
+    }
     uint64_t key;
-    if ((uint32_t)u >= (uint32_t)n || (uint32_t)v >= (uint32_t)n) {
+    if ((uint32_t)u >= (uint32_t)lim || (uint32_t)v >= (uint32_t)lim) {
       bad = true;
       key = sentinel;
     } else if (u == v) {
       key = sentinel;  // self-loop: sorts last, dropped with the sentinels
     } else {
-      const uint32_t lo = (uint32_t)min(u, v), hi = (uint32_t)max(u, v);
+      const uint32_t lo = (uint32_t)(min(u, v) + shift), hi = (uint32_t)(max(u, v) + shift);
       key = ((uint64_t)lo << b) | hi;
     }
     keys[i] = key;
@@ -322,7 +344,9 @@ k_radix_pass(const uint64_t *__restrict__ in, void *__restrict__ out, uint32_t n
 constexpr int kDegThreads = 256;
 
 __global__ void __launch_bounds__(kDegThreads)
-k_unique_degree(const uint64_t *__restrict__ keys, uint32_t m_in, int b, int32_t *deg) {
+k_unique_degree(const uint64_t *__restrict__ keys, const Ctrl *__restrict__ ctrl, int b,
+                int32_t *deg) {
+  const uint32_t m_in = ctrl->m_in;
   const uint64_t sentinel = (1ull << (2 * b)) - 1;
   const uint64_t mask = (1ull << b) - 1;
   const uint32_t stride = gridDim.x * kDegThreads;
@@ -370,7 +394,7 @@ k_rank_keys(const int32_t *__restrict__ deg, int32_t n, int b, int passes,
 // orient: compact distinct edges, orient by rank (= (degree, id) order)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kOrientThreads)
-k_orient(const uint64_t *__restrict__ keys, uint32_t m_in, int b,
+k_orient(const uint64_t *__restrict__ keys, int b,
          const int32_t *__restrict__ rank, uint64_t *__restrict__ okeys,
          uint32_t *__restrict__ hist2, int passes2, unsigned long long *status, Ctrl *ctrl) {
   constexpr int KPT = kOrientKeysPerThread, TILE = kOrientTile;
@@ -379,6 +403,7 @@ k_orient(const uint64_t *__restrict__ keys, uint32_t m_in, int b,
   __shared__ uint32_t s_excl;
   __shared__ uint32_t s_hist[kMaxSort2Passes * 256];
   const int tid = threadIdx.x;
+  const uint32_t m_in = ctrl->m_in;
   if (tid == 0) s_tile = atomicAdd(&ctrl->tile_ticket[kTicketOrient], 1u);
   for (int i = tid; i < passes2 * 256; i += kOrientThreads) s_hist[i] = 0;
   __syncthreads();
@@ -436,7 +461,7 @@ template <bool GROUPS>
 __global__ void __launch_bounds__(kScanThreads)
 k_offsets(const int32_t *__restrict__ counts, int32_t n, int32_t *__restrict__ off,
           const int32_t *__restrict__ row_off, int32_t *__restrict__ warp_list,
-          int32_t *__restrict__ cta_list, int32_t *__restrict__ big_list,
+          int32_t *__restrict__ cta_list, int32_t *__restrict__ big_list, Tuning tune,
           unsigned long long *status, uint32_t *ticket, Ctrl *ctrl) {
   constexpr int IPT = kScanItemsPerThread, TILE = kScanTile;
   __shared__ uint32_t s_scratch[32];
@@ -477,7 +502,7 @@ k_offsets(const int32_t *__restrict__ counts, int32_t n, int32_t *__restrict__ o
     if (v < (uint32_t)n && d[i] > 0) dh = __ldg(row_off + v + 1) - __ldg(row_off + v);
     // a warp takes a group only if both its list and its partner count are
     // short: one warp streaming thousands of partners would finish last
-    const bool is_warp = dh >= 2 && dh <= kWarpMaxRow && d[i] <= kWarpMaxPartners;
+    const bool is_warp = dh >= 2 && dh <= tune.warp_max_list && d[i] <= tune.warp_max_partners;
     const bool is_cta = dh >= 2 && dh <= kCtaMaxRow && !is_warp;
     const bool is_big = dh > kCtaMaxRow;
     const uint32_t bw = __ballot_sync(kFull, is_warp), bc = __ballot_sync(kFull, is_cta);
@@ -513,11 +538,13 @@ int num_sms() {
 }  // namespace
 
 void launch_canon(const int32_t *src, const int32_t *dst, uint32_t m_in, int32_t n, int b,
-                  int passes, uint64_t *keys, uint32_t *hist, Ctrl *ctrl, cudaStream_t st) {
+                  int passes, const BatchDesc *batch, uint64_t *keys, uint32_t *hist,
+                  Ctrl *ctrl, cudaStream_t st) {
   const uint32_t want = (m_in + kCanonThreads * 8 - 1) / (kCanonThreads * 8);
   const uint32_t cap = (uint32_t)num_sms() * 8;
   const uint32_t grid = max(1u, min(want, cap));
-  k_canon<<<grid, kCanonThreads, 0, st>>>(src, dst, m_in, n, b, passes, keys, hist, ctrl);
+  k_canon<<<grid, kCanonThreads, 0, st>>>(src, dst, m_in, n, b, passes, batch, keys, hist,
+                                          ctrl);
   note_launch();
 }
 
@@ -550,11 +577,11 @@ void launch_rank_keys(const int32_t *deg, int32_t n, int b, int passes, uint64_t
   note_launch();
 }
 
-void launch_unique_degree(const uint64_t *keys, uint32_t m_in, int b, int32_t *deg,
-                          cudaStream_t st) {
+void launch_unique_degree(const uint64_t *keys, uint32_t m_in, const Ctrl *ctrl, int b,
+                          int32_t *deg, cudaStream_t st) {
   const uint32_t want = (m_in + kDegThreads * 8 - 1) / (kDegThreads * 8);
   const uint32_t grid = max(1u, min(want, (uint32_t)num_sms() * 8));
-  k_unique_degree<<<grid, kDegThreads, 0, st>>>(keys, m_in, b, deg);
+  k_unique_degree<<<grid, kDegThreads, 0, st>>>(keys, ctrl, b, deg);
   note_launch();
 }
 
@@ -562,22 +589,22 @@ void launch_orient(const uint64_t *keys, uint32_t m_in, int b, const int32_t *ra
                    uint64_t *okeys, uint32_t *hist2, int passes2, unsigned long long *status,
                    Ctrl *ctrl, cudaStream_t st) {
   const uint32_t grid = max(1u, (m_in + kOrientTile - 1) / kOrientTile);
-  k_orient<<<grid, kOrientThreads, 0, st>>>(keys, m_in, b, rank, okeys, hist2, passes2, status,
-                                            ctrl);
+  k_orient<<<grid, kOrientThreads, 0, st>>>(keys, b, rank, okeys, hist2, passes2, status, ctrl);
   note_launch();
 }
 
 void launch_offsets(const int32_t *counts, int32_t n, int32_t *off, const int32_t *row_off,
-                    int32_t *warp_list, int32_t *cta_list, int32_t *big_list,
+                    int32_t *warp_list, int32_t *cta_list, int32_t *big_list, Tuning tune,
                     unsigned long long *status, uint32_t *ticket, Ctrl *ctrl, cudaStream_t st) {
   const uint32_t items = (uint32_t)n + 1;
   const uint32_t grid = max(1u, (items + kScanTile - 1) / kScanTile);
+  tune.warp_max_list = min(max(tune.warp_max_list, 0), kWarpMaxRow);  // warp tables hold 4x
   if (row_off)
     k_offsets<true><<<grid, kScanThreads, 0, st>>>(counts, n, off, row_off, warp_list, cta_list,
-                                                   big_list, status, ticket, ctrl);
+                                                   big_list, tune, status, ticket, ctrl);
   else
     k_offsets<false><<<grid, kScanThreads, 0, st>>>(counts, n, off, nullptr, nullptr, nullptr,
-                                                    nullptr, status, ticket, ctrl);
+                                                    nullptr, tune, status, ticket, ctrl);
   note_launch();
 }
 

@@ -2,6 +2,7 @@
 // phase sequence, host-buffer variants, errors and instrumentation.
 #include <atomic>
 #include <cstdarg>
+#include <vector>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -137,16 +138,23 @@ tc_status check_args(const int32_t *src, const int32_t *dst, int64_t m, int32_t 
   return TC_OK;
 }
 
-// All phases on `st` using workspace `ws` laid out by L.  t_out == nullptr
-// counts the total only.  Synchronises `st` and writes T to *total.  The
-// control block is read back into `staging` when given (any host memory),
-// else into this thread's pinned buffer; `profile` = false never records
-// phase events.
-tc_status run_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t n,
-                   cudaStream_t st, unsigned char *ws, const Layout &L, int64_t *t_out,
-                   int32_t *deg_out, uint64_t *total, Ctrl *staging = nullptr,
-                   bool profile = true) {
-  PhaseTimer pt(st, profile);
+// Extra inputs and outputs of a batched run (several graphs counted as one
+// disjoint union).
+struct BatchRun {
+  const BatchDesc *desc;        // device descriptor of the graphs
+  int32_t num_graphs_bound;     // grid bound of the per-graph sums
+  unsigned long long *totals;   // device: triangles per graph
+};
+
+// Enqueues every phase on `st` using workspace `ws` laid out by L, ending
+// with a copy of the control block into `staging` (host).  Nothing here
+// synchronises or allocates, so the whole sequence can be captured in a
+// CUDA graph.  t_out == nullptr counts the total only (per graph with a
+// batch: group totals, summed per graph).
+tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t n,
+                       cudaStream_t st, unsigned char *ws, const Layout &L, int64_t *t_out,
+                       int32_t *deg_out, const BatchRun *batch, const Tuning &tune,
+                       PhaseTimer &pt, Ctrl *staging) {
   const uint32_t m = (uint32_t)m_in;
   const int b = id_bits(n);
   // radix passes: undirected keys (2b bits), rank keys (degree bits < 2^b),
@@ -170,7 +178,10 @@ tc_status run_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t
   int32_t *cta_groups = reinterpret_cast<int32_t *>(ws + L.cta_groups);
   int32_t *big_groups = reinterpret_cast<int32_t *>(ws + L.big_groups);
   int32_t *rank = reinterpret_cast<int32_t *>(ws + L.rank);
-  int64_t *t_rank = t_out ? reinterpret_cast<int64_t *>(ws + L.t_rank) : nullptr;
+  // per-vertex counts, or per-group totals of a batch, in rank space
+  int64_t *t_rank = (t_out || batch) ? reinterpret_cast<int64_t *>(ws + L.t_rank) : nullptr;
+  // group totals back in union ids (the rank keys are free by then)
+  int64_t *tg_union = reinterpret_cast<int64_t *>(ws + L.vkeys_a);
   const size_t words = L.st_sort_words_per_pass;
   // look-back status and tile tickets: one slot per radix pass, in the order
   // the passes run (sort 1, rank sort, sort 2)
@@ -191,7 +202,7 @@ tc_status run_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t
   if (t_rank) TC_CUDA(cudaMemsetAsync(t_rank, 0, sizeof(int64_t) * (size_t)n, st), "memset t");
 
   pt.start(TC_PHASE_CANON);
-  launch_canon(src, dst, m, n, b, passes1, keys_a, hist, ctrl, st);
+  launch_canon(src, dst, m, n, b, passes1, batch ? batch->desc : nullptr, keys_a, hist, ctrl, st);
   pt.stop(TC_PHASE_CANON);
 
   pt.start(TC_PHASE_SORT1);
@@ -200,7 +211,7 @@ tc_status run_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t
     unsigned long long *status;
     uint32_t *ticket;
     next_pass(&status, &ticket);
-    launch_radix_pass(in, out, kOutKeys, nullptr, nullptr, m, nullptr, 8 * p, 0u, 0,
+    launch_radix_pass(in, out, kOutKeys, nullptr, nullptr, m, &ctrl->m_in, 8 * p, 0u, 0,
                       hist + 256 * p, status, ticket, ctrl, st);
     uint64_t *x = in;
     in = out;
@@ -209,7 +220,7 @@ tc_status run_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t
   pt.stop(TC_PHASE_SORT1);
 
   pt.start(TC_PHASE_DEGREE);
-  launch_unique_degree(in, m, b, deg, st);
+  launch_unique_degree(in, m, ctrl, b, deg, st);
   pt.stop(TC_PHASE_DEGREE);
 
   // rank of every vertex in the (degree, id) order
@@ -266,7 +277,7 @@ tc_status run_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t
   pt.stop(TC_PHASE_SORT2);
 
   pt.start(TC_PHASE_OFFSETS);
-  launch_offsets(outdeg, n, off, nullptr, nullptr, nullptr, nullptr, st_scan,
+  launch_offsets(outdeg, n, off, nullptr, nullptr, nullptr, nullptr, tune, st_scan,
                  &ctrl->tile_ticket[kTicketScan], ctrl, st);
   pt.stop(TC_PHASE_OFFSETS);
 
@@ -275,31 +286,63 @@ tc_status run_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t
   pt.start(TC_PHASE_GROUPS);
   int32_t *gcnt = outdeg;
   TC_CUDA(cudaMemsetAsync(gcnt, 0, sizeof(int32_t) * (size_t)n, st), "memset groups");
-  launch_group_count(row, col, off, m, ctrl, gcnt, st);
-  launch_offsets(gcnt, n, goff, off, warp_groups, cta_groups, big_groups, st_scan2,
+  launch_group_count(row, col, off, m, tune.heavy_ratio_pct, ctrl, gcnt, st);
+  launch_offsets(gcnt, n, goff, off, warp_groups, cta_groups, big_groups, tune, st_scan2,
                  &ctrl->tile_ticket[kTicketGroupScan], ctrl, st);
-  launch_group_fill(row, col, off, m, ctrl, goff, gcnt, part, st);
+  launch_group_fill(row, col, off, m, tune.heavy_ratio_pct, ctrl, goff, gcnt, part, st);
   pt.stop(TC_PHASE_GROUPS);
 
   pt.start(TC_PHASE_COUNT);
-  cudaError_t e =
-      launch_count(off, col, goff, part, warp_groups, cta_groups, big_groups, ctrl, t_rank, st);
+  cudaError_t e = launch_count(off, col, goff, part, warp_groups, cta_groups, big_groups, ctrl,
+                               t_out ? t_rank : nullptr, t_out ? nullptr : t_rank, st);
   if (e == cudaSuccess && t_out) launch_gather_counts(t_rank, rank, n, t_out, st);
+  if (e == cudaSuccess && batch) {
+    if (t_out) {  // per graph: (sum of t) / 3
+      launch_segment_sums(t_out, batch->desc, batch->num_graphs_bound, 3, batch->totals, st);
+    } else {      // per graph: sum of the group totals
+      launch_gather_counts(t_rank, rank, n, tg_union, st);
+      launch_segment_sums(tg_union, batch->desc, batch->num_graphs_bound, 1, batch->totals, st);
+    }
+  }
   pt.stop(TC_PHASE_COUNT);
   if (e != cudaSuccess) return cuda_fail(e, "count kernel");
   TC_CUDA(cudaGetLastError(), "kernel launch");
+  TC_CUDA(cudaMemcpyAsync(staging, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st), "read result");
+  return TC_OK;
+}
 
-  Ctrl *h = staging ? staging : host_ctrl();
-  if (!h) return set_status(TC_ERR_OOM, "pinned staging buffer");
-  TC_CUDA(cudaMemcpyAsync(h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st), "read result");
-  TC_CUDA(cudaStreamSynchronize(st), "synchronize");
-  pt.fold();
+// Status of a run from its control block (after the stream has synchronised).
+tc_status finish_core(const Ctrl *h, int32_t n, uint64_t *total) {
   if (h->err & kErrIdRange)
-    return set_status(TC_ERR_ID_RANGE, "a vertex id is outside [0, %d)", n);
+    return set_status(TC_ERR_ID_RANGE, "a vertex id is outside [0, %d) of its graph", n);
   if (h->err & kErrTimeout)
     return set_status(TC_ERR_TIMEOUT, "a device-side wait reached its iteration limit");
-  *total = (uint64_t)h->total;
+  if (total) *total = (uint64_t)h->total;
   return set_status(TC_OK);
+}
+
+Tuning g_tuning = kDefaultTuning;
+std::mutex g_tuning_mu;
+
+Tuning current_tuning() {
+  std::lock_guard<std::mutex> lk(g_tuning_mu);
+  return g_tuning;
+}
+
+// One synchronous single-graph run: enqueue, synchronise, read the status.
+tc_status run_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t n,
+                   cudaStream_t st, unsigned char *ws, const Layout &L, int64_t *t_out,
+                   int32_t *deg_out, uint64_t *total, Ctrl *staging = nullptr,
+                   bool profile = true) {
+  PhaseTimer pt(st, profile);
+  Ctrl *h = staging ? staging : host_ctrl();
+  if (!h) return set_status(TC_ERR_OOM, "pinned staging buffer");
+  tc_status s = enqueue_core(src, dst, m_in, n, st, ws, L, t_out, deg_out, nullptr,
+                             current_tuning(), pt, h);
+  if (s != TC_OK) return s;
+  TC_CUDA(cudaStreamSynchronize(st), "synchronize");
+  pt.fold();
+  return finish_core(h, n, total);
 }
 
 tc_status count_impl(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
@@ -422,6 +465,197 @@ tc_status noalloc_scratch(unsigned char **out) {
   return TC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Batches: several graphs counted as one disjoint union.
+// ---------------------------------------------------------------------------
+// Host-side check of a batch and the int32 offset block the device needs:
+// edge offsets [G+1] followed by union vertex offsets [G+1].
+struct BatchPlan {
+  int32_t graphs = 0;
+  int64_t pairs = 0;
+  int64_t vertices = 0;
+  std::vector<int32_t> block;
+};
+
+tc_status plan_batch(int32_t G, const int64_t *eo, const int32_t *vn, int64_t max_pairs,
+                     int64_t max_vertices, BatchPlan *p) {
+  if (G < 0 || (G > 0 && (!eo || !vn)))
+    return set_status(TC_ERR_INVALID_ARG, "num_graphs < 0 or a NULL offset array");
+  p->graphs = G;
+  p->block.assign(2 * (size_t)(G + 1), 0);
+  if (G == 0) return TC_OK;
+  if (eo[0] != 0) return set_status(TC_ERR_INVALID_ARG, "edge_offsets[0] must be 0");
+  int64_t nv = 0;
+  for (int32_t g = 0; g < G; ++g) {
+    if (eo[g + 1] < eo[g]) return set_status(TC_ERR_INVALID_ARG, "edge_offsets decrease at %d", g);
+    if (vn[g] < 0) return set_status(TC_ERR_INVALID_ARG, "vertex_counts[%d] < 0", g);
+    nv += vn[g];
+  }
+  if (eo[G] > max_pairs || nv > max_vertices)
+    return set_status(TC_ERR_OVERFLOW, "batch of %lld pairs and %lld vertices exceeds %lld / %lld",
+                      (long long)eo[G], (long long)nv, (long long)max_pairs,
+                      (long long)max_vertices);
+  nv = 0;
+  for (int32_t g = 0; g <= G; ++g) {
+    p->block[g] = (int32_t)eo[g];
+    p->block[G + 1 + g] = (int32_t)nv;
+    if (g < G) nv += vn[g];
+  }
+  p->pairs = eo[G];
+  p->vertices = nv;
+  return TC_OK;
+}
+
+// Device batch region: descriptor, offset block, per-graph totals.
+struct BatchRegion {
+  size_t desc, block, totals, bytes;
+};
+BatchRegion batch_region(int32_t max_graphs) {
+  BatchRegion r;
+  r.desc = 0;
+  r.block = align256(sizeof(BatchDesc));
+  r.totals = align256(r.block + sizeof(int32_t) * 2 * ((size_t)max_graphs + 1));
+  r.bytes = align256(r.totals + sizeof(unsigned long long) * (size_t)max_graphs);
+  return r;
+}
+
+tc_status batch_impl(const int32_t *src, const int32_t *dst, int32_t G, const int64_t *eo,
+                     const int32_t *vn, cudaStream_t st, uint64_t *totals_out) {
+  BatchPlan p;
+  tc_status s = plan_batch(G, eo, vn, INT32_MAX, INT32_MAX, &p);
+  if (s != TC_OK) return s;
+  if (G > 0 && !totals_out) return set_status(TC_ERR_INVALID_ARG, "totals_out is NULL");
+  if (p.pairs > 0 && (!src || !dst)) return set_status(TC_ERR_INVALID_ARG, "src/dst is NULL");
+  if (p.pairs == 0) {
+    for (int32_t g = 0; g < G; ++g) totals_out[g] = 0;
+    return set_status(TC_OK);
+  }
+  if (p.vertices == 0) return set_status(TC_ERR_ID_RANGE, "edges but no vertices");
+  const Layout L = make_layout(p.pairs, (int32_t)p.vertices);
+  const BatchRegion R = batch_region(G);
+  keep_pool_memory();
+  unsigned char *ws = nullptr;
+  TC_CUDA(cudaMallocAsync((void **)&ws, L.total + R.bytes, st), "workspace allocation");
+  unsigned char *bd = ws + L.total;
+  std::vector<unsigned char> staging(R.totals);
+  BatchDesc desc{G, 0, reinterpret_cast<int32_t *>(bd + R.block),
+                 reinterpret_cast<int32_t *>(bd + R.block) + (G + 1)};
+  memcpy(staging.data(), &desc, sizeof(desc));
+  memcpy(staging.data() + R.block, p.block.data(), sizeof(int32_t) * p.block.size());
+  auto *totals_dev = reinterpret_cast<unsigned long long *>(bd + R.totals);
+  s = TC_OK;
+  cudaError_t e = cudaMemcpyAsync(bd, staging.data(), staging.size(), cudaMemcpyHostToDevice, st);
+  Ctrl *h = host_ctrl();
+  PhaseTimer pt(st, true);
+  if (e != cudaSuccess) s = cuda_fail(e, "batch descriptor copy");
+  else if (!h) s = set_status(TC_ERR_OOM, "pinned staging buffer");
+  if (s == TC_OK) {
+    const BatchRun br{reinterpret_cast<const BatchDesc *>(bd), G, totals_dev};
+    s = enqueue_core(src, dst, p.pairs, (int32_t)p.vertices, st, ws, L, nullptr, nullptr, &br,
+                     current_tuning(), pt, h);
+  }
+  if (s == TC_OK) {
+    e = cudaMemcpyAsync(totals_out, totals_dev, sizeof(uint64_t) * G, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) s = cuda_fail(e, "totals copy");
+  }
+  cudaFreeAsync(ws, st);
+  e = cudaStreamSynchronize(st);
+  if (s != TC_OK) return s;
+  if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+  pt.fold();
+  return finish_core(h, (int32_t)p.vertices, nullptr);
+}
+
+}  // namespace
+
+// A persistent batch engine: device buffers sized once, and the whole batch
+// pipeline captured once as a CUDA graph.  Every batch runs with the same
+// shape -- capacity pairs and vertices, the pairs past the batch's end being
+// padding that is never keyed -- so one instantiated graph is replayed for
+// all of them; the batch's offsets reach the device through a copy node that
+// reads a pinned staging block rewritten before each launch.
+struct tc_engine {
+  int device = -1;
+  int64_t max_pairs = 0;
+  int32_t max_vertices = 0, max_graphs = 0;
+  Tuning tune = kDefaultTuning;
+  cudaStream_t st = nullptr;
+  unsigned char *dbuf = nullptr;   // device: src, dst, workspace, batch region
+  unsigned char *hbuf = nullptr;   // pinned: descriptor + offsets, control block, totals
+  int32_t *src = nullptr, *dst = nullptr;
+  unsigned char *ws = nullptr, *bd = nullptr;
+  Layout L{};
+  BatchRegion R{};
+  Ctrl *ctrl_h = nullptr;
+  unsigned long long *totals_h = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool busy = false;
+  int32_t pending_graphs = 0;
+  int32_t pending_vertices = 0;
+};
+
+namespace {
+
+void engine_release(tc_engine *e) {
+  if (!e) return;
+  if (e->st) cudaStreamSynchronize(e->st);
+  if (e->exec) cudaGraphExecDestroy(e->exec);
+  if (e->graph) cudaGraphDestroy(e->graph);
+  if (e->dbuf) cudaFree(e->dbuf);
+  if (e->hbuf) cudaFreeHost(e->hbuf);
+  if (e->st) cudaStreamDestroy(e->st);
+  delete e;
+}
+
+tc_status engine_build(tc_engine *e) {
+  TC_CUDA(cudaGetDevice(&e->device), "current device");
+  TC_CUDA(prepare_count_kernels(), "count kernel attributes");
+  TC_CUDA(cudaStreamCreateWithFlags(&e->st, cudaStreamNonBlocking), "stream");
+  e->L = make_layout(e->max_pairs, e->max_vertices);
+  e->R = batch_region(e->max_graphs);
+  const size_t in_bytes = align256(sizeof(int32_t) * (size_t)e->max_pairs);
+  TC_CUDA(cudaMalloc((void **)&e->dbuf, 2 * in_bytes + e->L.total + e->R.bytes),
+          "engine device memory");
+  e->src = reinterpret_cast<int32_t *>(e->dbuf);
+  e->dst = reinterpret_cast<int32_t *>(e->dbuf + in_bytes);
+  e->ws = e->dbuf + 2 * in_bytes;
+  e->bd = e->ws + e->L.total;
+  const size_t h_ctrl = align256(e->R.totals);
+  const size_t h_totals = align256(h_ctrl + sizeof(Ctrl));
+  TC_CUDA(cudaMallocHost((void **)&e->hbuf, h_totals + sizeof(unsigned long long) *
+                                                           (size_t)e->max_graphs),
+          "engine pinned memory");
+  e->ctrl_h = reinterpret_cast<Ctrl *>(e->hbuf + h_ctrl);
+  e->totals_h = reinterpret_cast<unsigned long long *>(e->hbuf + h_totals);
+  BatchDesc desc{0, 0, reinterpret_cast<int32_t *>(e->bd + e->R.block),
+                 reinterpret_cast<int32_t *>(e->bd + e->R.block) + (e->max_graphs + 1)};
+  memcpy(e->hbuf, &desc, sizeof(desc));
+  memset(e->hbuf + e->R.block, 0, sizeof(int32_t) * 2 * ((size_t)e->max_graphs + 1));
+
+  // capture: offsets in, the pipeline, control block and totals out
+  TC_CUDA(cudaStreamBeginCapture(e->st, cudaStreamCaptureModeThreadLocal), "begin capture");
+  PhaseTimer pt(e->st, false);
+  auto *totals_dev = reinterpret_cast<unsigned long long *>(e->bd + e->R.totals);
+  const BatchRun br{reinterpret_cast<const BatchDesc *>(e->bd), e->max_graphs, totals_dev};
+  cudaError_t ce = cudaMemcpyAsync(e->bd, e->hbuf, e->R.totals, cudaMemcpyHostToDevice, e->st);
+  tc_status s = TC_OK;
+  if (ce == cudaSuccess)
+    s = enqueue_core(e->src, e->dst, e->max_pairs, e->max_vertices, e->st, e->ws, e->L, nullptr,
+                     nullptr, &br, e->tune, pt, e->ctrl_h);
+  if (ce == cudaSuccess && s == TC_OK)
+    ce = cudaMemcpyAsync(e->totals_h, totals_dev, sizeof(unsigned long long) * e->max_graphs,
+                         cudaMemcpyDeviceToHost, e->st);
+  cudaGraph_t g = nullptr;
+  const cudaError_t end = cudaStreamEndCapture(e->st, &g);
+  e->graph = g;
+  if (s != TC_OK) return s;
+  if (ce != cudaSuccess) return cuda_fail(ce, "capture");
+  if (end != cudaSuccess) return cuda_fail(end, "end capture");
+  TC_CUDA(cudaGraphInstantiate(&e->exec, e->graph, 0), "graph instantiate");
+  return TC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -516,6 +750,123 @@ tc_status tc_count_noalloc(const int32_t *src, const int32_t *dst, int64_t m, in
   Ctrl staging;  // pageable host memory: no pinned allocation either
   return run_core(src, dst, m, n, (cudaStream_t)stream, ws, L, nullptr, nullptr, total_out,
                   &staging, false);
+}
+
+tc_status tc_count_batch(const int32_t *src, const int32_t *dst, int32_t num_graphs,
+                         const int64_t *edge_offsets, const int32_t *vertex_counts,
+                         tc_stream_t stream, uint64_t *totals_out) {
+  return batch_impl(src, dst, num_graphs, edge_offsets, vertex_counts, (cudaStream_t)stream,
+                    totals_out);
+}
+
+tc_status tc_engine_create(int64_t max_pairs, int32_t max_vertices, int32_t max_graphs,
+                           const tc_tuning *tuning, tc_engine **out) {
+  if (!out) return set_status(TC_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (max_pairs < 1 || max_vertices < 1 || max_graphs < 1)
+    return set_status(TC_ERR_INVALID_ARG, "capacities must be positive");
+  if (max_pairs > (int64_t)INT32_MAX) return set_status(TC_ERR_OVERFLOW, "max_pairs > 2^31-1");
+  tc_engine *e = new tc_engine;
+  e->max_pairs = max_pairs;
+  e->max_vertices = max_vertices;
+  e->max_graphs = max_graphs;
+  e->tune = tuning ? Tuning{tuning->warp_max_list, tuning->warp_max_partners,
+                            max(tuning->heavy_ratio_pct, 100)}
+                   : current_tuning();
+  tc_status s = engine_build(e);
+  if (s != TC_OK) {
+    const tc_status keep = s;
+    char detail[256];
+    memcpy(detail, t_detail, sizeof(detail));
+    engine_release(e);
+    t_last = keep;
+    memcpy(t_detail, detail, sizeof(detail));
+    return keep;
+  }
+  *out = e;
+  return set_status(TC_OK);
+}
+
+tc_status tc_engine_submit(tc_engine *e, const int32_t *src, const int32_t *dst,
+                           int32_t inputs_on_host, int32_t num_graphs,
+                           const int64_t *edge_offsets, const int32_t *vertex_counts) {
+  if (!e) return set_status(TC_ERR_INVALID_ARG, "engine is NULL");
+  if (e->busy) return set_status(TC_ERR_INVALID_ARG, "engine busy: wait for the last batch");
+  if (num_graphs > e->max_graphs)
+    return set_status(TC_ERR_OVERFLOW, "%d graphs exceed the engine's %d", num_graphs,
+                      e->max_graphs);
+  BatchPlan p;
+  tc_status s = plan_batch(num_graphs, edge_offsets, vertex_counts, e->max_pairs,
+                           e->max_vertices, &p);
+  if (s != TC_OK) return s;
+  if (p.pairs > 0 && (!src || !dst)) return set_status(TC_ERR_INVALID_ARG, "src/dst is NULL");
+  int dev = -1;
+  TC_CUDA(cudaGetDevice(&dev), "current device");
+  if (dev != e->device) return set_status(TC_ERR_INVALID_ARG, "engine belongs to device %d", e->device);
+  const cudaMemcpyKind kind = inputs_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const size_t bytes = sizeof(int32_t) * (size_t)p.pairs;
+  if (bytes) {
+    TC_CUDA(cudaMemcpyAsync(e->src, src, bytes, kind, e->st), "copy src");
+    TC_CUDA(cudaMemcpyAsync(e->dst, dst, bytes, kind, e->st), "copy dst");
+  }
+  // the staging block keeps its layout: edge offsets then vertex offsets,
+  // max_graphs + 1 slots each; the graph's copy node moves it to the device
+  reinterpret_cast<BatchDesc *>(e->hbuf)->num_graphs = num_graphs;
+  memcpy(e->hbuf + e->R.block, p.block.data(), sizeof(int32_t) * (size_t)(num_graphs + 1));
+  memcpy(e->hbuf + e->R.block + sizeof(int32_t) * ((size_t)e->max_graphs + 1),
+         p.block.data() + num_graphs + 1, sizeof(int32_t) * (size_t)(num_graphs + 1));
+  TC_CUDA(cudaGraphLaunch(e->exec, e->st), "graph launch");
+  note_launch();
+  e->busy = true;
+  e->pending_graphs = num_graphs;
+  e->pending_vertices = (int32_t)p.vertices;
+  return set_status(TC_OK);
+}
+
+tc_status tc_engine_wait(tc_engine *e, uint64_t *totals_out) {
+  if (!e) return set_status(TC_ERR_INVALID_ARG, "engine is NULL");
+  if (!e->busy) return set_status(TC_ERR_INVALID_ARG, "no batch submitted");
+  const cudaError_t ce = cudaStreamSynchronize(e->st);
+  e->busy = false;
+  if (ce != cudaSuccess) return cuda_fail(ce, "synchronize");
+  tc_status s = finish_core(e->ctrl_h, e->pending_vertices, nullptr);
+  if (s != TC_OK) return s;
+  if (totals_out)
+    for (int32_t g = 0; g < e->pending_graphs; ++g) totals_out[g] = e->totals_h[g];
+  return s;
+}
+
+tc_status tc_engine_count(tc_engine *e, const int32_t *src, const int32_t *dst,
+                          int32_t inputs_on_host, int32_t num_graphs,
+                          const int64_t *edge_offsets, const int32_t *vertex_counts,
+                          uint64_t *totals_out) {
+  tc_status s = tc_engine_submit(e, src, dst, inputs_on_host, num_graphs, edge_offsets,
+                                 vertex_counts);
+  if (s != TC_OK) return s;
+  return tc_engine_wait(e, totals_out);
+}
+
+tc_status tc_engine_destroy(tc_engine *e) {
+  engine_release(e);
+  return set_status(TC_OK);
+}
+
+tc_status tc_set_tuning(const tc_tuning *t) {
+  if (t && (t->warp_max_list < 0 || t->warp_max_partners < 0 || t->heavy_ratio_pct < 100))
+    return set_status(TC_ERR_INVALID_ARG, "tuning values out of range");
+  std::lock_guard<std::mutex> lk(g_tuning_mu);
+  g_tuning = t ? Tuning{t->warp_max_list, t->warp_max_partners, t->heavy_ratio_pct}
+               : kDefaultTuning;
+  return set_status(TC_OK);
+}
+
+tc_status tc_get_tuning(tc_tuning *out) {
+  if (!out) return set_status(TC_ERR_INVALID_ARG, "out is NULL");
+  const Tuning t = current_tuning();
+  out->warp_max_list = t.warp_max_list;
+  out->warp_max_partners = t.warp_max_partners;
+  out->heavy_ratio_pct = t.heavy_ratio_pct;
+  return set_status(TC_OK);
 }
 
 tc_status tc_last_error(void) { return t_last; }

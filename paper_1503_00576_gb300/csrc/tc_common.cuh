@@ -37,7 +37,8 @@ struct Ctrl {
   uint32_t next_cta_group;
   uint32_t next_big_group;
   unsigned long long total;        // triangle count T
-  uint32_t pad[2];
+  uint32_t m_in;                   // input pairs that are real (not batch padding)
+  uint32_t pad[1];
 };
 static_assert(sizeof(Ctrl) % 16 == 0, "Ctrl must keep 16-byte alignment");
 
@@ -61,6 +62,26 @@ constexpr unsigned long long kValueMask = (1ull << 62) - 1;
 constexpr int kWarpMaxRow = 128;
 constexpr int kWarpMaxPartners = 64;
 constexpr int kCtaMaxRow = 1024;
+
+// Runtime tuning of the counting layout (what an autotuner varies).
+struct Tuning {
+  int32_t warp_max_list;      // a group goes to one warp if its hashed list has
+  int32_t warp_max_partners;  //   at most this many entries and partners
+  int32_t heavy_ratio_pct;    // edge (u,v) is grouped at v when |N+(v)| * 100 >
+                              //   |N+(u)| * heavy_ratio_pct, else at its owner u
+};
+constexpr Tuning kDefaultTuning = {128, 64, 100};
+
+// A batch of graphs counted as one disjoint union (device-side descriptor).
+// Graph g owns input pairs [edge_off[g], edge_off[g+1]) and union vertex ids
+// [voff[g], voff[g+1]); pairs at or beyond edge_off[num_graphs] are padding
+// and are dropped like self-loops.
+struct BatchDesc {
+  int32_t num_graphs;
+  int32_t pad_;
+  const int32_t *edge_off;  // [num_graphs + 1]
+  const int32_t *voff;      // [num_graphs + 1]
+};
 
 // Workspace layout for an input of m_in pairs and n vertices.  All offsets
 // are 256-byte aligned.
@@ -137,8 +158,12 @@ inline int id_bits(int32_t n) {
 void note_launch();
 
 // ---- launchers (preprocess.cu) ----
+// batch == nullptr: one graph on ids [0, n).  Otherwise ids of pair i are
+// local to its graph, checked against that graph's vertex count, and
+// shifted by the graph's first union id.
 void launch_canon(const int32_t *src, const int32_t *dst, uint32_t m_in, int32_t n, int b,
-                  int passes, uint64_t *keys, uint32_t *hist, Ctrl *ctrl, cudaStream_t st);
+                  int passes, const BatchDesc *batch, uint64_t *keys, uint32_t *hist,
+                  Ctrl *ctrl, cudaStream_t st);
 // Output of a radix pass: the keys themselves; the column array (low bits,
 // to `out`) plus the row array (key >> owner_shift, to `row_out`) with the
 // out-degrees added to `outdeg`; or the rank scatter rank[low bits] =
@@ -153,8 +178,8 @@ void launch_radix_pass(const uint64_t *in, void *out, RadixOut mode, uint32_t *r
 // degree field (the rank sort).
 void launch_rank_keys(const int32_t *deg, int32_t n, int b, int passes, uint64_t *vkeys,
                       uint32_t *hist, cudaStream_t st);
-void launch_unique_degree(const uint64_t *keys, uint32_t m_in, int b, int32_t *deg,
-                          cudaStream_t st);
+void launch_unique_degree(const uint64_t *keys, uint32_t m_in, const Ctrl *ctrl, int b,
+                          int32_t *deg, cudaStream_t st);
 void launch_orient(const uint64_t *keys, uint32_t m_in, int b, const int32_t *rank,
                    uint64_t *okeys, uint32_t *hist2, int passes2, unsigned long long *status,
                    Ctrl *ctrl, cudaStream_t st);
@@ -162,19 +187,29 @@ void launch_orient(const uint64_t *keys, uint32_t m_in, int b, const int32_t *ra
 // entries are partner groups and are binned into warp_list / cta_list /
 // big_list by the length of their hashed list.
 void launch_offsets(const int32_t *counts, int32_t n, int32_t *off, const int32_t *row_off,
-                    int32_t *warp_list, int32_t *cta_list, int32_t *big_list,
+                    int32_t *warp_list, int32_t *cta_list, int32_t *big_list, Tuning tune,
                     unsigned long long *status, uint32_t *ticket, Ctrl *ctrl, cudaStream_t st);
 // ---- launchers (group.cu) ----
 void launch_group_count(const int32_t *row, const int32_t *col, const int32_t *off,
-                        uint32_t m_bound, Ctrl *ctrl, int32_t *gcnt, cudaStream_t st);
+                        uint32_t m_bound, int32_t heavy_ratio_pct, Ctrl *ctrl, int32_t *gcnt,
+                        cudaStream_t st);
 void launch_group_fill(const int32_t *row, const int32_t *col, const int32_t *off,
-                       uint32_t m_bound, Ctrl *ctrl, const int32_t *goff, int32_t *gcnt,
-                       int32_t *part, cudaStream_t st);
+                       uint32_t m_bound, int32_t heavy_ratio_pct, Ctrl *ctrl,
+                       const int32_t *goff, int32_t *gcnt, int32_t *part, cudaStream_t st);
 // ---- launchers (count.cu) ----
+// t != nullptr: per-vertex counts (rank space).  Otherwise, if tg is not
+// nullptr, tg[h] += triangles found in group h (their sum per graph is the
+// graph's count).
 cudaError_t launch_count(const int32_t *off, const int32_t *col, const int32_t *goff,
                          const int32_t *part, const int32_t *warp_groups,
                          const int32_t *cta_groups, const int32_t *big_groups, Ctrl *ctrl,
-                         int64_t *t, cudaStream_t st);
+                         int64_t *t, int64_t *tg, cudaStream_t st);
+// Sets the counting kernels' attributes and occupancy for the current
+// device (done lazily otherwise; needed before capturing a CUDA graph).
+cudaError_t prepare_count_kernels();
+// out[g] = (sum of vals over graph g's union ids) / divisor.
+void launch_segment_sums(const int64_t *vals, const BatchDesc *batch, int32_t num_graphs,
+                         int32_t divisor, unsigned long long *out, cudaStream_t st);
 // ---- clustering (count.cu) ----
 void launch_clustering(const int64_t *t, const int32_t *deg, int32_t n, double *cc,
                        unsigned long long *sums /* [2]: sum t, sum C(deg,2) */, cudaStream_t st);

@@ -110,3 +110,26 @@ def test_rgg_mean_degree():
     s, d = graphgen.rgg(n, graphgen.rgg_radius(n), 3)
     mean = 2 * len(s) / n
     assert 31.0 < mean < 32.0  # boundary effects lower it slightly below 32
+
+
+def test_graph_batch_deterministic_and_simple():
+    a = graphgen.graph_batch(24, 3, log2_n=(6, 11))
+    b = graphgen.graph_batch(24, 3, log2_n=(6, 11), threads=1)
+    assert np.array_equal(a.src, b.src) and np.array_equal(a.dst, b.dst)
+    assert np.array_equal(a.edge_offsets, b.edge_offsets)
+    n, m, kinds, _ = graphgen.batch_params(24, 3, log2_n=(6, 11))
+    assert np.array_equal(np.diff(a.edge_offsets), m)
+    assert kinds[0] == "er" and kinds[1] == "rmat"
+    for g in range(len(a)):
+        s, d, nv = a.graph(g)
+        assert nv == n[g] and len(s) == m[g]
+        assert np.all(s != d) and s.min(initial=0) >= 0 and max(s.max(initial=0), d.max(initial=0)) < nv
+        assert len(np.unique(_canon(s, d))) == len(s)
+
+
+def test_batch_params_ranges():
+    n, m, kinds, _ = graphgen.batch_params(4096, 1005)
+    assert n.min() >= 256 and n.max() <= 1 << 18
+    d = 2 * m / n
+    assert d.min() >= 3.9 and d.max() <= 64.0
+    assert kinds.count("er") == kinds.count("rmat") == 2048
