@@ -162,8 +162,9 @@ tc_status tc_get_tuning(tc_tuning *out);
  *   vertex_counts   HOST int32[G]
  *   totals_out      HOST uint64[G]: triangles of each graph
  * Limits: total pairs and total vertices <= 2^31 - 1 (TC_ERR_OVERFLOW).  An
- * id out of range in any graph fails the whole batch (TC_ERR_ID_RANGE).
- * Synchronises.
+ * id out of range fails only the graph that holds it: the call returns
+ * TC_ERR_ID_RANGE, that graph's total is TC_COUNT_ERROR and every other
+ * total is still written and exact.  Synchronises.
  */
 tc_status tc_count_batch(const int32_t *src, const int32_t *dst, int32_t num_graphs,
                          const int64_t *edge_offsets, const int32_t *vertex_counts,
@@ -181,7 +182,9 @@ tc_status tc_count_batch(const int32_t *src, const int32_t *dst, int32_t num_gra
  *                      Host inputs must stay valid until tc_engine_wait;
  *                      page-locked ones overlap with other work.
  *   tc_engine_wait     waits for the submitted batch; totals_out HOST
- *                      uint64[G] (may be NULL).
+ *                      uint64[G] (may be NULL).  As with tc_count_batch,
+ *                      a graph with an id out of range gets TC_COUNT_ERROR
+ *                      and the status TC_ERR_ID_RANGE; the others are exact.
  *   tc_engine_count    submit + wait.
  * One batch in flight per engine; an engine is used by one thread at a time
  * and on the device that was current at creation.  Two engines overlap.
@@ -193,6 +196,16 @@ tc_status tc_engine_submit(tc_engine *engine, const int32_t *src, const int32_t 
                            int32_t inputs_on_host, int32_t num_graphs,
                            const int64_t *edge_offsets, const int32_t *vertex_counts);
 tc_status tc_engine_wait(tc_engine *engine, uint64_t *totals_out);
+/* Like tc_engine_submit, for graphs held in separate arrays: graph g has
+ * pair_counts[g] pairs at srcs[g], dsts[g] (all in host memory, or all on the
+ * device, per inputs_on_host), each copied straight into the engine. */
+tc_status tc_engine_submit_parts(tc_engine *engine, int32_t num_graphs,
+                                 const int32_t *const *srcs, const int32_t *const *dsts,
+                                 const int64_t *pair_counts, const int32_t *vertex_counts,
+                                 int32_t inputs_on_host);
+/* 1 if the engine has no batch running (tc_engine_wait will not block), 0 if
+ * its last batch is still running. */
+int32_t tc_engine_poll(tc_engine *engine);
 tc_status tc_engine_count(tc_engine *engine, const int32_t *src, const int32_t *dst,
                           int32_t inputs_on_host, int32_t num_graphs,
                           const int64_t *edge_offsets, const int32_t *vertex_counts,

@@ -459,7 +459,11 @@ k_segment_sums(const int64_t *__restrict__ vals, const BatchDesc *__restrict__ b
       for (int32_t v = b + lane; v < e; v += 32) s += (unsigned long long)__ldg(vals + v);
     }
     s = warp_sum_u64(s);
-    if (lane == 0) out[gi] = gi < ng ? s / (unsigned long long)divisor : 0ull;
+    if (lane == 0) {
+      unsigned long long r = 0ull;
+      if (gi < ng) r = batch->gerr[gi] ? ~0ull : s / (unsigned long long)divisor;
+      out[gi] = r;  // ~0: the graph had an id out of range (TC_COUNT_ERROR)
+    }
   }
 }
 

@@ -167,19 +167,22 @@ k_canon(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, uint32
   // pairs past m_real are batch padding: not keyed, not sorted
   for (uint32_t i = blockIdx.x * kCanonThreads + threadIdx.x; i < m_real; i += stride) {
     int32_t u = __ldg(src + i), v = __ldg(dst + i);
-    int32_t lim = n, shift = 0;
+    int32_t lim = n, shift = 0, lo_graph = 0;
     if (batch) {
       int32_t lo = 0, hi = ng;  // the last graph g with eo[g] <= i
       while (hi - lo > 1) {
         const int32_t mid = (lo + hi) >> 1;
         if ((uint32_t)__ldg(eo + mid) <= i) lo = mid; else hi = mid;
       }
+      lo_graph = lo;
       shift = __ldg(vo + lo);
       lim = __ldg(vo + lo + 1) - shift;
     }
     uint64_t key;
     if ((uint32_t)u >= (uint32_t)lim || (uint32_t)v >= (uint32_t)lim) {
-      bad = true;
+      // a batch fails only the graph that holds the pair; the pair is dropped
+      // so the other graphs of the union are counted exactly
+      if (batch) batch->gerr[lo_graph] = 1; else bad = true;
       key = sentinel;
     } else if (u == v) {
       key = sentinel;  // self-loop: sorts last, dropped with the sentinels

@@ -507,16 +507,35 @@ tc_status plan_batch(int32_t G, const int64_t *eo, const int32_t *vn, int64_t ma
 }
 
 // Device batch region: descriptor, offset block, per-graph totals.
+// Device region of a batch: descriptor, offsets block (edge_off then voff,
+// max_graphs + 1 each), per-graph error flags, per-graph totals.  Everything
+// before `totals` is one host-to-device copy per batch (the flags travel as
+// zeros), the totals one copy back.
 struct BatchRegion {
-  size_t desc, block, totals, bytes;
+  size_t desc, block, gerr, totals, bytes;
 };
 BatchRegion batch_region(int32_t max_graphs) {
   BatchRegion r;
   r.desc = 0;
   r.block = align256(sizeof(BatchDesc));
-  r.totals = align256(r.block + sizeof(int32_t) * 2 * ((size_t)max_graphs + 1));
+  r.gerr = align256(r.block + sizeof(int32_t) * 2 * ((size_t)max_graphs + 1));
+  r.totals = align256(r.gerr + sizeof(int32_t) * (size_t)max_graphs);
   r.bytes = align256(r.totals + sizeof(unsigned long long) * (size_t)max_graphs);
   return r;
+}
+
+// Graphs of a finished batch whose total is TC_COUNT_ERROR had an id out
+// of range: the batch status is TC_ERR_ID_RANGE, every other total is exact.
+tc_status batch_id_status(const uint64_t *totals, int32_t G) {
+  int32_t first = -1, bad = 0;
+  for (int32_t g = 0; g < G; ++g)
+    if (totals[g] == TC_COUNT_ERROR) {
+      if (first < 0) first = g;
+      ++bad;
+    }
+  if (!bad) return set_status(TC_OK);
+  return set_status(TC_ERR_ID_RANGE, "graph %d (%d of %d graphs) has an id outside [0, n_g)",
+                    first, bad, G);
 }
 
 tc_status batch_impl(const int32_t *src, const int32_t *dst, int32_t G, const int64_t *eo,
@@ -539,7 +558,8 @@ tc_status batch_impl(const int32_t *src, const int32_t *dst, int32_t G, const in
   unsigned char *bd = ws + L.total;
   std::vector<unsigned char> staging(R.totals);
   BatchDesc desc{G, 0, reinterpret_cast<int32_t *>(bd + R.block),
-                 reinterpret_cast<int32_t *>(bd + R.block) + (G + 1)};
+                 reinterpret_cast<int32_t *>(bd + R.block) + (G + 1),
+                 reinterpret_cast<int32_t *>(bd + R.gerr)};
   memcpy(staging.data(), &desc, sizeof(desc));
   memcpy(staging.data() + R.block, p.block.data(), sizeof(int32_t) * p.block.size());
   auto *totals_dev = reinterpret_cast<unsigned long long *>(bd + R.totals);
@@ -563,7 +583,9 @@ tc_status batch_impl(const int32_t *src, const int32_t *dst, int32_t G, const in
   if (s != TC_OK) return s;
   if (e != cudaSuccess) return cuda_fail(e, "synchronize");
   pt.fold();
-  return finish_core(h, (int32_t)p.vertices, nullptr);
+  s = finish_core(h, (int32_t)p.vertices, nullptr);
+  if (s != TC_OK) return s;
+  return batch_id_status(totals_out, G);
 }
 
 }  // namespace
@@ -629,9 +651,10 @@ tc_status engine_build(tc_engine *e) {
   e->ctrl_h = reinterpret_cast<Ctrl *>(e->hbuf + h_ctrl);
   e->totals_h = reinterpret_cast<unsigned long long *>(e->hbuf + h_totals);
   BatchDesc desc{0, 0, reinterpret_cast<int32_t *>(e->bd + e->R.block),
-                 reinterpret_cast<int32_t *>(e->bd + e->R.block) + (e->max_graphs + 1)};
+                 reinterpret_cast<int32_t *>(e->bd + e->R.block) + (e->max_graphs + 1),
+                 reinterpret_cast<int32_t *>(e->bd + e->R.gerr)};
   memcpy(e->hbuf, &desc, sizeof(desc));
-  memset(e->hbuf + e->R.block, 0, sizeof(int32_t) * 2 * ((size_t)e->max_graphs + 1));
+  memset(e->hbuf + e->R.block, 0, e->R.totals - e->R.block);  // offsets; error flags stay 0
 
   // capture: offsets in, the pipeline, control block and totals out
   TC_CUDA(cudaStreamBeginCapture(e->st, cudaStreamCaptureModeThreadLocal), "begin capture");
@@ -823,6 +846,54 @@ tc_status tc_engine_submit(tc_engine *e, const int32_t *src, const int32_t *dst,
   return set_status(TC_OK);
 }
 
+tc_status tc_engine_submit_parts(tc_engine *e, int32_t num_graphs, const int32_t *const *srcs,
+                                 const int32_t *const *dsts, const int64_t *pair_counts,
+                                 const int32_t *vertex_counts, int32_t inputs_on_host) {
+  if (!e) return set_status(TC_ERR_INVALID_ARG, "engine is NULL");
+  if (e->busy) return set_status(TC_ERR_INVALID_ARG, "engine busy: wait for the last batch");
+  if (num_graphs < 0 || num_graphs > e->max_graphs)
+    return set_status(TC_ERR_OVERFLOW, "%d graphs for an engine of %d", num_graphs,
+                      e->max_graphs);
+  if (num_graphs > 0 && (!srcs || !dsts || !pair_counts))
+    return set_status(TC_ERR_INVALID_ARG, "NULL part arrays");
+  std::vector<int64_t> eo((size_t)num_graphs + 1, 0);
+  for (int32_t g = 0; g < num_graphs; ++g) {
+    if (pair_counts[g] < 0) return set_status(TC_ERR_INVALID_ARG, "pair_counts[%d] < 0", g);
+    if (pair_counts[g] > 0 && (!srcs[g] || !dsts[g]))
+      return set_status(TC_ERR_INVALID_ARG, "part %d is NULL", g);
+    eo[g + 1] = eo[g] + pair_counts[g];
+  }
+  BatchPlan p;
+  tc_status s = plan_batch(num_graphs, eo.data(), vertex_counts, e->max_pairs, e->max_vertices, &p);
+  if (s != TC_OK) return s;
+  int dev = -1;
+  TC_CUDA(cudaGetDevice(&dev), "current device");
+  if (dev != e->device)
+    return set_status(TC_ERR_INVALID_ARG, "engine belongs to device %d", e->device);
+  const cudaMemcpyKind kind = inputs_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  for (int32_t g = 0; g < num_graphs; ++g) {
+    const size_t bytes = sizeof(int32_t) * (size_t)pair_counts[g];
+    if (!bytes) continue;
+    TC_CUDA(cudaMemcpyAsync(e->src + eo[g], srcs[g], bytes, kind, e->st), "copy src part");
+    TC_CUDA(cudaMemcpyAsync(e->dst + eo[g], dsts[g], bytes, kind, e->st), "copy dst part");
+  }
+  reinterpret_cast<BatchDesc *>(e->hbuf)->num_graphs = num_graphs;
+  memcpy(e->hbuf + e->R.block, p.block.data(), sizeof(int32_t) * (size_t)(num_graphs + 1));
+  memcpy(e->hbuf + e->R.block + sizeof(int32_t) * ((size_t)e->max_graphs + 1),
+         p.block.data() + num_graphs + 1, sizeof(int32_t) * (size_t)(num_graphs + 1));
+  TC_CUDA(cudaGraphLaunch(e->exec, e->st), "graph launch");
+  note_launch();
+  e->busy = true;
+  e->pending_graphs = num_graphs;
+  e->pending_vertices = (int32_t)p.vertices;
+  return set_status(TC_OK);
+}
+
+int32_t tc_engine_poll(tc_engine *e) {
+  if (!e || !e->busy) return 1;
+  return cudaStreamQuery(e->st) == cudaErrorNotReady ? 0 : 1;
+}
+
 tc_status tc_engine_wait(tc_engine *e, uint64_t *totals_out) {
   if (!e) return set_status(TC_ERR_INVALID_ARG, "engine is NULL");
   if (!e->busy) return set_status(TC_ERR_INVALID_ARG, "no batch submitted");
@@ -833,7 +904,7 @@ tc_status tc_engine_wait(tc_engine *e, uint64_t *totals_out) {
   if (s != TC_OK) return s;
   if (totals_out)
     for (int32_t g = 0; g < e->pending_graphs; ++g) totals_out[g] = e->totals_h[g];
-  return s;
+  return batch_id_status(reinterpret_cast<const uint64_t *>(e->totals_h), e->pending_graphs);
 }
 
 tc_status tc_engine_count(tc_engine *e, const int32_t *src, const int32_t *dst,

@@ -81,6 +81,7 @@ struct BatchDesc {
   int32_t pad_;
   const int32_t *edge_off;  // [num_graphs + 1]
   const int32_t *voff;      // [num_graphs + 1]
+  int32_t *gerr;            // [num_graphs], zero on entry; set: an id outside its graph
 };
 
 // Workspace layout for an input of m_in pairs and n vertices.  All offsets

@@ -107,13 +107,29 @@ def test_tuning_never_changes_counts(tc, batch, expected, tuning):
     assert tc.tc_get_tuning() == tc.DEFAULT_TUNING
 
 
-def test_batch_errors(tc, batch):
+def test_batch_errors(tc, batch, expected):
     s = batch.src.copy()
     g = 7
     s[batch.edge_offsets[g]] = batch.vertex_counts[g]  # one id past its graph
     with pytest.raises(tc.TCError) as e:
         tc.tc_count_batch(dev(s), dev(batch.dst), batch.edge_offsets, batch.vertex_counts)
     assert e.value.code == tc.TC_ERR_ID_RANGE
+    # only graph g fails; every other total is still exact
+    want = expected.copy()
+    want[g] = np.uint64(tc.TC_COUNT_ERROR)
+    assert np.array_equal(e.value.totals, want)
+    s[batch.edge_offsets[30] + 1] = -1  # a second bad graph, negative id
+    want[30] = np.uint64(tc.TC_COUNT_ERROR)
+    with tc.Engine(int(batch.edge_offsets[-1]), int(batch.vertex_counts.sum()),
+                   len(batch)) as eng:
+        for _ in range(2):
+            with pytest.raises(tc.TCError) as e:
+                eng.count(s, batch.dst, batch.edge_offsets, batch.vertex_counts)
+            assert e.value.code == tc.TC_ERR_ID_RANGE
+            assert np.array_equal(e.value.totals, want)
+        # the error flags are cleared for the next batch
+        assert np.array_equal(eng.count(batch.src, batch.dst, batch.edge_offsets,
+                                        batch.vertex_counts), expected)
     bad = batch.edge_offsets.copy()
     bad[0] = 1
     with pytest.raises(tc.TCError) as e:
