@@ -196,9 +196,19 @@ def committed_traffic(kernel: str, workload: str):
 
 
 def roofline(prof: dict, steps: int, m_in: int, m: int, n: int, workload: str,
-             total_only: bool = False) -> dict:
+             work: dict, total_only: bool = False) -> dict:
     """Dominant kernel by device time; achieved = algorithmic bytes per
-    launch / average launch duration (CUDA events on the launch stream)."""
+    launch / average launch duration (CUDA events on the launch stream).
+
+    The counting phase is one unit: its two kernels (k_count_big for the
+    partner groups with the longest hashed lists, then k_count) split one
+    work list and run back to back once per step, followed by the small
+    gather of t[] to vertex ids.  Its algorithmic bytes are the forward-list
+    elements the hash intersections read -- each partner group's hashed list
+    once (inserts) and, per forward edge, the list streamed through it
+    (lookups), 4 bytes each, counted exactly by tc_count_work -- plus the
+    partner ids (4m), both offset arrays (8(n+1)) and, per vertex, t[] in
+    rank space written, gathered and written again (28n)."""
     b = max(1, (max(n, 2) - 1).bit_length())
     passes1, passes2 = (2 * b + 7) // 8, (b + 7) // 8
     per_kernel = {}
@@ -209,18 +219,30 @@ def roofline(prof: dict, steps: int, m_in: int, m: int, n: int, workload: str,
         a[1] += launches
     kernel = max(per_kernel, key=lambda k: per_kernel[k][0])
     ms_total, launches = per_kernel[kernel]
+    extra = {}
     if kernel == "k_count":
-        # compulsory: the CSR read once (col 4m, offsets 4(n+1)) and t[] written once (8n)
-        bytes_per_launch = 4 * m + 4 * (n + 1) + (0 if total_only else 8 * n)
-        how = "CSR read once (4m + 4(n+1)) + t written once (8n)"
+        kernel = "k_count+k_count_big"
+        units = steps
+        lists = 4 * (work["lookups"] + work["inserts"])
+        bytes_per_launch = lists + 4 * m + 8 * (n + 1) + (0 if total_only else 28 * n)
+        how = ("one counting phase: 4 B per list element read by the hash intersections "
+               "(lookups %d + inserts %d) + partner ids 4m + offsets 8(n+1)%s"
+               % (work["lookups"], work["inserts"], "" if total_only else " + t[] 28n"))
+        t = ms_total / 1e3 / units
+        extra = {"merge_equivalent_gbs": round(4 * work["merge_work"] / t / 1e9, 1),
+                 "merge_work_W": work["merge_work"],
+                 "compulsory_gbs": round((4 * m + 4 * (n + 1) + (0 if total_only else 8 * n))
+                                         / t / 1e9, 1)}
     elif kernel == "k_radix_pass":
+        units = launches
         total = passes1 * 16 * m_in + (passes2 - 1) * 16 * m + 12 * m
         bytes_per_launch = total / (passes1 + passes2)
         how = "8-byte key read + 8-byte key write per key per pass (last pass writes 4 bytes)"
     else:
+        units = launches
         bytes_per_launch = 16 * m_in
         how = "16 bytes per input pair"
-    per_launch_s = ms_total / 1e3 / max(launches, 1)
+    per_launch_s = ms_total / 1e3 / max(units, 1)
     achieved = bytes_per_launch / per_launch_s / 1e9
     peaks = measured_peaks()
     peak = peaks.get("hbm_gbs")
@@ -231,7 +253,7 @@ def roofline(prof: dict, steps: int, m_in: int, m: int, n: int, workload: str,
             "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": src,
             "traffic": committed_traffic(kernel, workload),
             "algorithmic_bytes_per_launch": int(bytes_per_launch), "bytes_rule": how,
-            "launches_timed": launches, "ms_per_launch": round(per_launch_s * 1e3, 4)}
+            "launches_timed": units, "ms_per_launch": round(per_launch_s * 1e3, 4), **extra}
 
 
 # ---------------------------------------------------------------- CPU oracle timing
@@ -421,6 +443,8 @@ def run_ours(args, world, rank, local, pg):
     if args.total_only:
         tc.tc_count_per_vertex(s, d, n, stream=stream, t_out=t_out, deg_out=deg_out)
     m = int((deg_out.to(torch.int64).sum() // 2).item())
+    work = tc.tc_count_work(s, d, n)  # untimed: the counting phase's exact work
+    assert work["edges"] == m and work["triangles"] == T
 
     clocks = ClockSampler(gpu_uuid(dev))
     tc.tc_profile_read(reset=True)
@@ -503,7 +527,8 @@ def run_ours(args, world, rank, local, pg):
                    "l2": "no flush: inputs %.2f GB and key buffers %.2f GB exceed L2"
                          % (8 * m_in / 1e9, 16 * m_in / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": roofline(prof, args.steps, m_in, m, n, args.workload, args.total_only),
+        "roofline": roofline(prof, args.steps, m_in, m, n, args.workload, work,
+                             args.total_only),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "phase_ms_per_step": steps_ms, "batched": batched,
     }

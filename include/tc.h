@@ -213,6 +213,34 @@ tc_status tc_engine_count(tc_engine *engine, const int32_t *src, const int32_t *
 tc_status tc_engine_destroy(tc_engine *engine);
 
 /*
+ * Work of the counting phase (instrumentation; the paper reports running
+ * times only).  Runs the same pipeline as tc_count with the current tuning,
+ * plus one reduction kernel over the forward edges, and reports what the
+ * counting phase does for this graph:
+ *   edges          m, distinct undirected edges = forward edges (Sec. II-B)
+ *   lookups        sum over forward edges {u, v} of the forward-list length
+ *                  streamed through the hash set (the shorter of N+(u),
+ *                  N+(v) under the default tuning)
+ *   inserts        sum over partner groups of the hashed list length
+ *   merge_work     W = sum over forward edges of d+(u) + d+(v): the elements
+ *                  a sorted-list merge of Sec. II-B would read
+ *   max_out_degree the largest d+(v), at most sqrt(2m) (Sec. II-B)
+ *   triangles      T
+ * Same arguments and errors as tc_count; synchronises `stream`.
+ */
+typedef struct tc_work {
+  int64_t edges;
+  int64_t lookups;
+  int64_t inserts;
+  int64_t merge_work;
+  uint64_t triangles;
+  int32_t max_out_degree;
+  int32_t vertices;
+} tc_work;
+tc_status tc_count_work(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
+                        tc_stream_t stream, tc_work *out);
+
+/*
  * Allocation-free count, for callers that cannot allocate device memory
  * while they run: for example a process whose own pool allocator reserves
  * all device memory at start-up and forbids driver allocations afterwards,

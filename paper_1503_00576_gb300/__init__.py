@@ -50,9 +50,17 @@ EXPORTS = ("tc_count", "tc_count_per_vertex", "tc_clustering", "tc_count_host",
            "tc_count_per_vertex_host", "tc_workspace_bytes", "tc_count_ws", "tc_set_tuning",
            "tc_get_tuning", "tc_count_batch", "tc_engine_create", "tc_engine_submit",
            "tc_engine_wait", "tc_engine_submit_parts", "tc_engine_poll", "tc_engine_count",
-           "tc_engine_destroy", "tc_count_noalloc",
+           "tc_engine_destroy", "tc_count_work", "tc_count_noalloc",
            "tc_last_error", "tc_status_string", "tc_last_error_detail", "tc_launch_count",
            "tc_profile_enable", "tc_profile_read", "tc_phase_name")
+
+
+class Work(ctypes.Structure):
+    """tc_work: what the counting phase does for one graph."""
+    _fields_ = [("edges", ctypes.c_int64), ("lookups", ctypes.c_int64),
+                ("inserts", ctypes.c_int64), ("merge_work", ctypes.c_int64),
+                ("triangles", ctypes.c_uint64), ("max_out_degree", ctypes.c_int32),
+                ("vertices", ctypes.c_int32)]
 
 
 class Tuning(ctypes.Structure):
@@ -93,6 +101,7 @@ def _bind(lib):
         "tc_workspace_bytes": ([i64, i32], sz),
         "tc_count_ws": ([vp, vp, i64, i32, vp, vp, sz, c.POINTER(u64)], c.c_int),
         "tc_count_noalloc": ([vp, vp, i64, i32, vp, c.POINTER(u64)], c.c_int),
+        "tc_count_work": ([vp, vp, i64, i32, vp, vp], c.c_int),
         "tc_set_tuning": ([c.POINTER(Tuning)], c.c_int),
         "tc_get_tuning": ([c.POINTER(Tuning)], c.c_int),
         "tc_count_batch": ([vp, vp, i32, vp, vp, vp, vp], c.c_int),
@@ -460,6 +469,21 @@ class Engine:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def tc_count_work(src, dst, n: int, stream=None) -> dict:
+    """Work of the counting phase for this graph (tc_work as a dict): hash
+    lookups and inserts, the merge work W of a sorted-list merge, the largest
+    out-degree, m and T.  Instrumentation: runs the whole pipeline once."""
+    torch = _torch()
+    dev = _edges(src, dst)
+    w = Work()
+    lib = load_library()
+    with torch.cuda.device(dev):
+        rc = lib.tc_count_work(src.data_ptr(), dst.data_ptr(), src.numel(), n,
+                               _stream_of(stream, dev), ctypes.byref(w))
+    _check(rc)
+    return {f: int(getattr(w, f)) for f, _ in w._fields_}
 
 
 TC_NOALLOC_SCRATCH_BYTES = 32 << 20

@@ -77,6 +77,45 @@ k_group_fill(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
   }
 }
 
+// Work of the counting phase, for instrumentation only (never on the path
+// of a count): per forward edge, the list streamed through the hash set,
+// d+(l) lookups, and the merge work d+(u) + d+(v) of Sec. II-B; per partner
+// group, the list hashed once, d+(h) inserts; the largest d+.
+__global__ void __launch_bounds__(kGroupThreads)
+k_work(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
+       const int32_t *__restrict__ off, const int32_t *__restrict__ goff, int32_t n,
+       int32_t heavy_ratio_pct, Ctrl *ctrl) {
+  const uint32_t m = ctrl->m;
+  const uint32_t stride = gridDim.x * kGroupThreads;
+  unsigned long long lookups = 0, inserts = 0, merge = 0, dmax = 0;
+  for (uint32_t e = blockIdx.x * kGroupThreads + threadIdx.x; e < m; e += stride) {
+    const int32_t u = __ldg(row + e), v = __ldg(col + e);
+    int32_t h, l;
+    split_edge(off, u, v, heavy_ratio_pct, h, l);
+    lookups += (unsigned long long)(__ldg(off + l + 1) - __ldg(off + l));
+    merge += (unsigned long long)(__ldg(off + u + 1) - __ldg(off + u)) +
+             (unsigned long long)(__ldg(off + v + 1) - __ldg(off + v));
+  }
+  for (uint32_t v = blockIdx.x * kGroupThreads + threadIdx.x; v < (uint32_t)n; v += stride) {
+    const unsigned long long d = (unsigned long long)(__ldg(off + v + 1) - __ldg(off + v));
+    if (__ldg(goff + v + 1) > __ldg(goff + v)) inserts += d;
+    dmax = d > dmax ? d : dmax;
+  }
+  for (int o = 16; o; o >>= 1) {
+    lookups += __shfl_xor_sync(0xffffffffu, lookups, o);
+    inserts += __shfl_xor_sync(0xffffffffu, inserts, o);
+    merge += __shfl_xor_sync(0xffffffffu, merge, o);
+    const unsigned long long x = __shfl_xor_sync(0xffffffffu, dmax, o);
+    dmax = x > dmax ? x : dmax;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&ctrl->work[0], lookups);
+    atomicAdd(&ctrl->work[1], inserts);
+    atomicAdd(&ctrl->work[2], merge);
+    atomicMax(&ctrl->work[3], dmax);
+  }
+}
+
 uint32_t group_grid(uint32_t m_bound) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -100,6 +139,14 @@ void launch_group_fill(const int32_t *row, const int32_t *col, const int32_t *of
                        const int32_t *goff, int32_t *gcnt, int32_t *part, cudaStream_t st) {
   k_group_fill<<<group_grid(m_bound), kGroupThreads, 0, st>>>(row, col, off, heavy_ratio_pct,
                                                               ctrl, goff, gcnt, part);
+  note_launch();
+}
+
+void launch_work(const int32_t *row, const int32_t *col, const int32_t *off, const int32_t *goff,
+                 uint32_t m_bound, int32_t n, int32_t heavy_ratio_pct, Ctrl *ctrl,
+                 cudaStream_t st) {
+  k_work<<<group_grid(max(m_bound, (uint32_t)n)), kGroupThreads, 0, st>>>(row, col, off, goff, n,
+                                                                          heavy_ratio_pct, ctrl);
   note_launch();
 }
 

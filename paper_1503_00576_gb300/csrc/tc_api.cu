@@ -154,7 +154,7 @@ struct BatchRun {
 tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t n,
                        cudaStream_t st, unsigned char *ws, const Layout &L, int64_t *t_out,
                        int32_t *deg_out, const BatchRun *batch, const Tuning &tune,
-                       PhaseTimer &pt, Ctrl *staging) {
+                       PhaseTimer &pt, Ctrl *staging, bool work_stats = false) {
   const uint32_t m = (uint32_t)m_in;
   const int b = id_bits(n);
   // radix passes: undirected keys (2b bits), rank keys (degree bits < 2^b),
@@ -291,6 +291,7 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
                  &ctrl->tile_ticket[kTicketGroupScan], ctrl, st);
   launch_group_fill(row, col, off, m, tune.heavy_ratio_pct, ctrl, goff, gcnt, part, st);
   pt.stop(TC_PHASE_GROUPS);
+  if (work_stats) launch_work(row, col, off, goff, m, n, tune.heavy_ratio_pct, ctrl, st);
 
   pt.start(TC_PHASE_COUNT);
   cudaError_t e = launch_count(off, col, goff, part, warp_groups, cta_groups, big_groups, ctrl,
@@ -915,6 +916,41 @@ tc_status tc_engine_count(tc_engine *e, const int32_t *src, const int32_t *dst,
                                  vertex_counts);
   if (s != TC_OK) return s;
   return tc_engine_wait(e, totals_out);
+}
+
+tc_status tc_count_work(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
+                        tc_stream_t stream, tc_work *out) {
+  if (!out) return set_status(TC_ERR_INVALID_ARG, "out is NULL");
+  memset(out, 0, sizeof(*out));
+  tc_status s = check_args(src, dst, m, n);
+  if (s != TC_OK) return s;
+  if (m > 0 && n == 0) return set_status(TC_ERR_ID_RANGE, "n = 0 but m > 0");
+  out->vertices = n;
+  if (m == 0) return set_status(TC_OK);
+  cudaStream_t st = (cudaStream_t)stream;
+  const Layout L = make_layout(m, n);
+  keep_pool_memory();
+  unsigned char *ws = nullptr;
+  TC_CUDA(cudaMallocAsync((void **)&ws, L.total, st), "workspace allocation");
+  Ctrl *h = host_ctrl();
+  PhaseTimer pt(st, false);
+  if (!h) s = set_status(TC_ERR_OOM, "pinned staging buffer");
+  else s = enqueue_core(src, dst, m, n, st, ws, L, nullptr, nullptr, nullptr, current_tuning(), pt,
+                        h, true);
+  cudaFreeAsync(ws, st);
+  const cudaError_t e = cudaStreamSynchronize(st);
+  if (s != TC_OK) return s;
+  if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+  uint64_t T = 0;
+  s = finish_core(h, n, &T);
+  if (s != TC_OK) return s;
+  out->edges = h->m;
+  out->triangles = T;
+  out->lookups = (int64_t)h->work[0];
+  out->inserts = (int64_t)h->work[1];
+  out->merge_work = (int64_t)h->work[2];
+  out->max_out_degree = (int32_t)h->work[3];
+  return set_status(TC_OK);
 }
 
 tc_status tc_engine_destroy(tc_engine *e) {

@@ -39,6 +39,9 @@ struct Ctrl {
   unsigned long long total;        // triangle count T
   uint32_t m_in;                   // input pairs that are real (not batch padding)
   uint32_t pad[1];
+  // work of the counting phase (filled only when asked for; see launch_work):
+  // hash lookups, hash inserts, merge work W, max out-degree
+  unsigned long long work[4];
 };
 static_assert(sizeof(Ctrl) % 16 == 0, "Ctrl must keep 16-byte alignment");
 
@@ -197,6 +200,10 @@ void launch_group_count(const int32_t *row, const int32_t *col, const int32_t *o
 void launch_group_fill(const int32_t *row, const int32_t *col, const int32_t *off,
                        uint32_t m_bound, int32_t heavy_ratio_pct, Ctrl *ctrl,
                        const int32_t *goff, int32_t *gcnt, int32_t *part, cudaStream_t st);
+// Instrumentation: adds the counting phase's work into ctrl->work.
+void launch_work(const int32_t *row, const int32_t *col, const int32_t *off, const int32_t *goff,
+                 uint32_t m_bound, int32_t n, int32_t heavy_ratio_pct, Ctrl *ctrl,
+                 cudaStream_t st);
 // ---- launchers (count.cu) ----
 // t != nullptr: per-vertex counts (rank space).  Otherwise, if tg is not
 // nullptr, tg[h] += triangles found in group h (their sum per graph is the

@@ -1,0 +1,77 @@
+"""Work counters of the counting phase (tc_count_work) against the oracle.
+
+The oracle gives every forward-list length d+(v) (Sec. II-B orientation);
+from it and the cleaned edge set the expected work follows directly:
+lookups = sum over edges of the streamed (shorter, ties to the non-owner)
+list, inserts = the hashed lists of the partner groups, W = sum over edges
+of d+(u) + d+(v) = sum over v of deg(v) d+(v), max d+ <= sqrt(2m).
+"""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tc():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1503_00576_gb300 as lib
+
+    lib.load_library()
+    return lib
+
+
+def expected_work(src, dst, n):
+    s = np.asarray(src, np.int64)
+    d = np.asarray(dst, np.int64)
+    keep = s != d
+    a, b = np.minimum(s, d)[keep], np.maximum(s, d)[keep]
+    key = np.unique(a * n + b)
+    a, b = key // n, key % n
+    deg = np.bincount(a, minlength=n) + np.bincount(b, minlength=n)
+    dp = oracle.out_degrees(src, dst, n).astype(np.int64)
+    # owner = the endpoint lower in the (degree, id) order
+    a_first = (deg[a] < deg[b]) | ((deg[a] == deg[b]) & (a < b))
+    u = np.where(a_first, a, b)
+    v = np.where(a_first, b, a)
+    du, dv = dp[u], dp[v]
+    h = np.where(dv > du, v, u)  # the longer list is hashed; ties stay at the owner
+    lookups = np.minimum(du, dv).sum()
+    inserts = dp[np.unique(h)].sum()
+    W = (du + dv).sum()
+    assert W == (deg * dp).sum()  # the two forms of the merge work agree
+    assert dp.sum() == len(key)
+    return {"edges": len(key), "lookups": int(lookups), "inserts": int(inserts),
+            "merge_work": int(W), "max_out_degree": int(dp.max()) if n else 0}
+
+
+@pytest.mark.parametrize("case", ["rmat12", "er", "k9", "rgg"])
+def test_work_matches_oracle(tc, case):
+    import torch
+
+    if case == "rmat12":
+        src, dst = graphgen.rmat(12, 16 << 12, 9)
+        n = 1 << 12
+    elif case == "er":
+        src, dst = graphgen.er(3000, 20000, 4)
+        n = 3000
+    elif case == "k9":
+        src, dst = (np.asarray(x, np.int32) for x in np.triu_indices(9, 1))
+        n = 9
+    else:
+        src, dst = graphgen.rgg(1 << 13, graphgen.rgg_radius(1 << 13, 12.0), 6)
+        n = 1 << 13
+    want = expected_work(src, dst, n)
+    want["triangles"] = oracle.forward(src, dst, n, per_vertex=False)["T"]
+    want["vertices"] = n
+    got = tc.tc_count_work(torch.from_numpy(np.ascontiguousarray(src, np.int32)).cuda(),
+                           torch.from_numpy(np.ascontiguousarray(dst, np.int32)).cuda(), n)
+    assert got == want
+    assert got["max_out_degree"] ** 2 <= 2 * got["edges"]
+    if case == "k9":  # K_n: d+ = n-1, ..., 0, so W = (n-1) C(n,2) and lookups = C(n,3)
+        assert got["merge_work"] == 8 * 36 and got["lookups"] == 84 == got["triangles"]
