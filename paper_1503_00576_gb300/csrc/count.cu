@@ -9,14 +9,14 @@
 //
 //  * N+(h) is staged once in shared memory as an open-addressing hash set
 //    (multiplicative hashing, linear probing, load <= 1/4; <= 1/2 past 4096
-//    entries), by one warp when |N+(h)| <= 128, else by a whole CTA whose
-//    warps claim chunks of 32 partners from a shared counter;
-//  * for the <= 32 partners l of a chunk, the lists N+(l) are read back to
-//    back as one flat sequence: in each 32-wide window lane p takes flat
-//    element p and finds its list by a ballot over the list starts plus an
-//    OR-reduction of the starts inside the window.  Loads are coalesced,
-//    every lane works however short the lists are, and four windows of loads
-//    are in flight per warp before any is probed;
+//    entries), by one warp when the group is small, else by a whole CTA
+//    whose warps claim chunks of partners from a shared counter;
+//  * the lists N+(l) of a chunk of <= 32 partners are read back to back as
+//    one flat sequence of aligned 16-byte words of the padded column array
+//    (each list padded with -1 to whole words, group.cu): lane p takes words
+//    p, p+32, ... and keeps a cursor on the list that holds its word.  Loads
+//    are coalesced 16-byte loads, every lane works however the lists are
+//    cut, and each lane has kWindows words in flight before it probes;
 //  * counts stay in registers and are reduced per warp (shuffles) into one
 //    uint64 atomic per warp at the end (the paper's reduction, fused).
 //
@@ -27,7 +27,7 @@
 // slot, so global atomics scale with the number of forward edges, not with
 // the number of triangles.
 //
-// A hashed list longer than 8192 entries (never seen in the workloads, but
+// A hashed list longer than 4096 entries (never seen in the workloads, but
 // allowed by |N+(v)| <= sqrt(2m)) is hashed in segments.  No step needs the
 // lists in sorted order: membership is by hashing, not by merging.
 #include "tc_common.cuh"
@@ -38,18 +38,21 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarpSlots = 4 * kWarpMaxRow;  // per-warp table
 constexpr int kGroupChunk = 8;               // warp groups per atomic
-constexpr int kWindows = 4;                  // 32-wide windows of loads in flight
+constexpr int kWindows = 4;                  // positions per lane loaded before probing
+constexpr int kBigWindows = 2;               // ... in the long-list kernel (40 registers)
 
 // Main kernel: 256-thread CTAs; CTA tables of 4096 slots serve hashed lists
 // of up to kCtaMaxRow entries (load <= 1/8 up to 512, <= 1/4 up to 1024).
 constexpr int kMainThreads = 256;
 constexpr int kMainWarps = kMainThreads / 32;
 constexpr int kMainSlots = 4096;
+constexpr int kMainMinBlocks = 4;  // 64 registers per thread
 // Long-list kernel: 512-thread CTAs, 8192 slots (lists up to 4096 entries
 // at once; longer lists in segments).
 constexpr int kBigThreads = 512;
 constexpr int kBigWarps = kBigThreads / 32;
 constexpr int kBigSlots = 8192;
+constexpr int kBigMinBlocks = 3;
 static_assert(kWarpSlots * kMainWarps <= kMainSlots, "warp tables must fit the CTA table");
 static_assert(4 * kCtaMaxRow <= kMainSlots, "CTA lists must fit at load <= 1/4");
 
@@ -58,7 +61,8 @@ static_assert(4 * kCtaMaxRow <= kMainSlots, "CTA lists must fit at load <= 1/4")
 // was displaced further along (linear probing).  A lookup whose home slot is
 // neither the key nor flagged is a miss after one read: with the table at
 // most 1/4 full, almost every unsuccessful lookup stops there, which keeps
-// the lanes of a warp in step.
+// the lanes of a warp in step.  The padding id -1 never matches: a slot's
+// low 31 bits are non-negative.
 constexpr int32_t kEmpty = 0x7fffffff;
 constexpr uint32_t kDisplaced = 0x80000000u;
 
@@ -80,8 +84,9 @@ __device__ __forceinline__ int table_log_slots(int32_t len, int capacity) {
 
 // Read-only view of the forward lists and partner groups.
 struct Lists {
-  const int32_t *__restrict__ off;   // node array (rank space)
-  const int32_t *__restrict__ col;   // forward lists
+  const int32_t *__restrict__ off;   // node array (rank space): list lengths
+  const int32_t *__restrict__ voff;  // node array of col4, in 16-byte words
+  const int32_t *__restrict__ col4;  // forward lists, each padded with -1 to whole words
   const int32_t *__restrict__ goff;  // partner-group offsets
   const int32_t *__restrict__ part;  // partners
 };
@@ -92,11 +97,14 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t x) {
   return x;
 }
 
+// Per-warp description of the chunk being probed: the non-empty partner
+// lists r = 0 .. k-1 in flat order.
 struct WarpScratch {
-  int32_t start[32];  // flat start of each non-empty partner list of the chunk
-  int32_t base[32];   // col index of flat position 0 of that list
-  int32_t l[32];      // the partner owning the list (per-vertex mode)
-  uint32_t lc[32];    // triangles found through that partner
+  int2 bn[32];         // word mode: {col4 word of flat position 0 of list r, flat start of r+1}
+  long long eb[32];    // element mode: col4 element of flat position 0 of list r
+  int32_t enext[32];   // element mode: flat start of list r+1
+  int32_t l[32];       // the partner owning list r (per-vertex mode)
+  uint32_t lc[32];     // triangles found through that partner
 };
 
 // Empties tab[0..slots) and its per-slot counters.
@@ -109,12 +117,12 @@ __device__ __forceinline__ void clear_table(int32_t *tab, uint32_t *cnt, int slo
   }
 }
 
-// Inserts g.col[beg..beg+len) (distinct ids) into the empty hash set.
-__device__ __forceinline__ void fill_table(const Lists &g, int32_t beg, int32_t len, int32_t *tab,
-                                           int log_slots, int rank, int group) {
+// Inserts list[0..len) (distinct ids) into the empty hash set.
+__device__ __forceinline__ void fill_table(const int32_t *__restrict__ list, int32_t len,
+                                           int32_t *tab, int log_slots, int rank, int group) {
   const uint32_t msk = (1u << log_slots) - 1u;
   for (int32_t i = rank; i < len; i += group) {
-    const int32_t x = __ldg(g.col + beg + i);
+    const int32_t x = __ldg(list + i);
     const uint32_t home = hash_slot((uint32_t)x, log_slots);
     uint32_t h = home;
     for (;;) {
@@ -153,7 +161,7 @@ __device__ __forceinline__ bool member(int32_t x, const int32_t *tab, int log_sl
     *slot = h;
     return true;
   }
-  if (!((uint32_t)y & kDisplaced)) return false;
+  if (y >= 0) return false;  // home slot not flagged: x was never displaced past it
   const uint32_t msk = (1u << log_slots) - 1u;
   for (;;) {
     h = (h + 1u) & msk;
@@ -166,14 +174,58 @@ __device__ __forceinline__ bool member(int32_t x, const int32_t *tab, int log_sl
   }
 }
 
-// Streams N+(l) for the partners l = part[c0 .. c0+cs) (of np, cs <= 32)
-// through the hash set of the group's list.  The chunk's non-empty lists are concatenated into one flat
-// sequence; lane p takes flat positions p, p+32, ... and keeps a cursor on
-// the list that holds its position (lists average ~200 entries, so the
-// cursor rarely moves).  Matches are counted in registers; per partner they
-// reach shared memory only when a lane's cursor leaves that partner; per w
-// they go to the counter beside w's slot.
+// Inclusive warp scan of one int32 per lane.
+__device__ __forceinline__ int32_t warp_incl_scan(int32_t x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// Counts the matches of one element; per-vertex mode also bumps the counter
+// beside the matched slot (t(w)).
 template <bool PV>
+__device__ __forceinline__ uint32_t probe1(int32_t x, const int32_t *tab, uint32_t *cnt,
+                                           int log_slots) {
+  uint32_t slot = 0;
+  const bool hit = member(x, tab, log_slots, &slot);
+  if (PV && hit) atomicAdd(&cnt[slot], 1u);
+  return hit ? 1u : 0u;
+}
+
+// Adds a lane's matches of list r to the chunk's per-partner counters,
+// flushing the previous list's run when the lane moves on.
+template <bool PV>
+__device__ __forceinline__ void note_run(WarpScratch &ws, int r, uint32_t hits, uint32_t &run,
+                                         int &run_r) {
+  if (!PV || hits == 0) return;
+  if (r != run_r) {
+    if (run) atomicAdd(&ws.lc[run_r], run);
+    run = 0;
+    run_r = r;
+  }
+  run += hits;
+}
+
+// Streams N+(l) for the partners l = part[c0 .. c0+cs) (of np, cs <= 32)
+// through the hash set of the group's list.  The chunk's non-empty lists are
+// concatenated into one flat sequence; lane p takes flat positions p, p+32,
+// ... and keeps a cursor on the list that holds its position (the cursor
+// only moves forward).  Two granularities, chosen per chunk by which needs
+// fewer warp steps:
+//  * words: a position is one aligned 16-byte word of the padded column
+//    array (int4), four entries probed per load; padding entries are -1 and
+//    never match;
+//  * elements: a position is one list entry (one 4-byte load), for chunks
+//    of a few short lists, where whole words would be mostly padding.
+// W positions per lane are loaded before any is probed.  Matches are
+// counted in registers; per partner they reach shared memory only when a
+// lane's cursor leaves that partner; per w they go to the counter beside
+// w's slot.
+template <bool PV, int W>
 __device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__restrict__ part,
                                             int32_t np, int32_t c0, int32_t cs,
                                             const int32_t *tab, uint32_t *cnt, int log_slots,
@@ -181,26 +233,32 @@ __device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__res
                                             uint64_t &found_group) {
   const int lane = threadIdx.x & 31;
   const int32_t j = c0 + lane;
-  int32_t l = 0, lb = 0, dl = 0;
+  int32_t l = 0, dl = 0, vb = 0;
   if (lane < cs && j < np) {
     l = __ldg(part + j);
-    lb = __ldg(g.off + l);
-    dl = __ldg(g.off + l + 1) - lb;
+    dl = __ldg(g.off + l + 1) - __ldg(g.off + l);
+    vb = __ldg(g.voff + l);
   }
   const uint32_t nonempty = __ballot_sync(kFull, dl > 0);
   if (nonempty == 0) return;
   const int k = __popc(nonempty);
   const int rank = __popc(nonempty & ((1u << lane) - 1u));
-  int32_t incl = dl;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int32_t y = __shfl_up_sync(kFull, incl, o);
-    if (lane >= o) incl += y;
-  }
-  const int32_t total = __shfl_sync(kFull, incl, 31);
+  const int32_t nv = (dl + 3) >> 2;
+  const int32_t incl_e = warp_incl_scan(dl);
+  const int32_t incl_v = warp_incl_scan(nv);
+  const int32_t total_e = __shfl_sync(kFull, incl_e, 31);
+  const int32_t total_v = __shfl_sync(kFull, incl_v, 31);
+  // a word step probes four entries, an element step one: cost ~3:1
+  const bool words = 3 * ((total_v + 31) >> 5) < ((total_e + 31) >> 5);
+  // list r+1 starts where list r ends (empty lists add nothing to the scans)
+  const bool last = rank == k - 1;
   if (dl > 0) {
-    ws.start[rank] = incl - dl;
-    ws.base[rank] = lb - (incl - dl);
+    if (words) {
+      ws.bn[rank] = make_int2(vb - (incl_v - nv), last ? INT32_MAX : incl_v);
+    } else {
+      ws.eb[rank] = 4ll * vb - (incl_e - dl);
+      ws.enext[rank] = last ? INT32_MAX : incl_e;
+    }
     if (PV) {
       ws.l[rank] = l;
       ws.lc[rank] = 0u;
@@ -208,43 +266,62 @@ __device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__res
   }
   __syncwarp();
   int r = 0;
-  int32_t base = ws.base[0];
-  int32_t next = k > 1 ? ws.start[1] : INT32_MAX;
-  uint32_t found = 0;     // matches of this lane in this chunk
-  uint32_t run = 0;       // matches of this lane for partner run_r
+  uint32_t found = 0;  // matches of this lane in this chunk
+  uint32_t run = 0;    // matches of this lane for list run_r
   int run_r = 0;
-  for (int32_t p0 = lane; p0 < total; p0 += 32 * kWindows) {
-    int32_t x[kWindows];
-    int rq[kWindows];
+  if (words) {
+    const int4 *__restrict__ col4v = reinterpret_cast<const int4 *>(g.col4);
+    int2 bn = ws.bn[0];
+    for (int32_t p0 = lane; p0 < total_v; p0 += 32 * W) {
+      int4 x[W];
+      int rq[W];
 #pragma unroll
-    for (int q = 0; q < kWindows; ++q) {
-      const int32_t p = p0 + 32 * q;
-      x[q] = -1;
-      rq[q] = r;
-      if (p < total) {
-        while (p >= next) {
-          ++r;
-          base = ws.base[r];
-          next = r + 1 < k ? ws.start[r + 1] : INT32_MAX;
+      for (int q = 0; q < W; ++q) {
+        const int32_t p = p0 + 32 * q;
+        rq[q] = -1;
+        if (p < total_v) {
+          while (p >= bn.y) bn = ws.bn[++r];
+          x[q] = __ldg(col4v + (bn.x + p));
+          rq[q] = r;
         }
-        x[q] = __ldg(g.col + base + p);
-        rq[q] = r;
+      }
+#pragma unroll
+      for (int q = 0; q < W; ++q) {
+        if (rq[q] < 0) continue;
+        const uint32_t hits = probe1<PV>(x[q].x, tab, cnt, log_slots) +
+                              probe1<PV>(x[q].y, tab, cnt, log_slots) +
+                              probe1<PV>(x[q].z, tab, cnt, log_slots) +
+                              probe1<PV>(x[q].w, tab, cnt, log_slots);
+        found += hits;
+        note_run<PV>(ws, rq[q], hits, run, run_r);
       }
     }
+  } else {
+    long long eb = ws.eb[0];
+    int32_t next = ws.enext[0];
+    for (int32_t p0 = lane; p0 < total_e; p0 += 32 * W) {
+      int32_t x[W];
+      int rq[W];
 #pragma unroll
-    for (int q = 0; q < kWindows; ++q) {
-      if (x[q] < 0) continue;
-      uint32_t slot = 0;
-      const bool hit = member(x[q], tab, log_slots, &slot);
-      found += hit;
-      if (PV && hit) {
-        if (rq[q] != run_r) {
-          if (run) atomicAdd(&ws.lc[run_r], run);
-          run = 0;
-          run_r = rq[q];
+      for (int q = 0; q < W; ++q) {
+        const int32_t p = p0 + 32 * q;
+        rq[q] = -1;
+        if (p < total_e) {
+          while (p >= next) {
+            ++r;
+            eb = ws.eb[r];
+            next = ws.enext[r];
+          }
+          x[q] = __ldg(g.col4 + (eb + p));
+          rq[q] = r;
         }
-        ++run;
-        atomicAdd(&cnt[slot], 1u);
+      }
+#pragma unroll
+      for (int q = 0; q < W; ++q) {
+        if (rq[q] < 0) continue;
+        const uint32_t hits = probe1<PV>(x[q], tab, cnt, log_slots);
+        found += hits;
+        note_run<PV>(ws, rq[q], hits, run, run_r);
       }
     }
   }
@@ -271,7 +348,7 @@ struct CtaShared {
 // hashed in equal segments, one after another, each probed by all partners:
 // N+(h) & N+(l) is the disjoint union of the segments' intersections.  The
 // table (SLOTS slots) is empty on entry and on exit.
-template <bool PV, int THREADS, int SLOTS>
+template <bool PV, int THREADS, int SLOTS, int W>
 __device__ __forceinline__ void cta_groups(const Lists &g, const int32_t *__restrict__ list,
                                            uint32_t n_list, uint32_t *cursor, int32_t *tab,
                                            uint32_t *cnt, WarpScratch *s_ws, CtaShared &sh,
@@ -289,7 +366,8 @@ __device__ __forceinline__ void cta_groups(const Lists &g, const int32_t *__rest
     // lists are filled in about ascending rank, and high ranks (high
     // degrees) carry the most work: take them first to shorten the tail
     const int32_t h = __ldg(list + (n_list - 1 - gi));
-    const int32_t hb = __ldg(g.off + h), hd = __ldg(g.off + h + 1) - hb;
+    const int32_t hd = __ldg(g.off + h + 1) - __ldg(g.off + h);
+    const int32_t *hl = g.col4 + 4 * (size_t)__ldg(g.voff + h);
     const int32_t pb = __ldg(g.goff + h), np = __ldg(g.goff + h + 1) - pb;
     const int32_t nseg = (hd + SLOTS / 2 - 1) / (SLOTS / 2);
     const int32_t seg_len = (hd + nseg - 1) / nseg;
@@ -299,7 +377,7 @@ __device__ __forceinline__ void cta_groups(const Lists &g, const int32_t *__rest
     for (int32_t s0 = 0; s0 < hd; s0 += seg_len) {
       const int32_t len = min(seg_len, hd - s0);
       if (tid == 0) sh.chunk = 0u;
-      fill_table(g, hb + s0, len, tab, log_slots, tid, THREADS);
+      fill_table(hl + s0, len, tab, log_slots, tid, THREADS);
       __syncthreads();
       for (;;) {
         uint32_t c = 0;
@@ -307,8 +385,8 @@ __device__ __forceinline__ void cta_groups(const Lists &g, const int32_t *__rest
         c = __shfl_sync(kFull, c, 0);
         const int32_t c0 = (int32_t)c * cs;
         if (c0 >= np) break;
-        probe_chunk<PV>(g, g.part + pb, np, c0, cs, tab, cnt, log_slots, s_ws[warp], t,
-                        found_total, found_group);
+        probe_chunk<PV, W>(g, g.part + pb, np, c0, cs, tab, cnt, log_slots, s_ws[warp], t,
+                           found_total, found_group);
       }
       __syncthreads();
       drain_table<PV>(tab, cnt, log_slots, tid, THREADS, t);
@@ -343,15 +421,16 @@ __device__ __forceinline__ void warp_groups(const Lists &g, const int32_t *__res
     const uint32_t g1 = min(g0 + (uint32_t)kGroupChunk, n_list);
     for (uint32_t gi = g0; gi < g1; ++gi) {
       const int32_t h = __ldg(list + (n_list - 1 - gi));  // heavy (high-rank) groups first
-      const int32_t hb = __ldg(g.off + h), hd = __ldg(g.off + h + 1) - hb;
+      const int32_t hd = __ldg(g.off + h + 1) - __ldg(g.off + h);
+      const int32_t *hl = g.col4 + 4 * (size_t)__ldg(g.voff + h);
       const int32_t pb = __ldg(g.goff + h), np = __ldg(g.goff + h + 1) - pb;
       const int log_slots = table_log_slots(hd, kWarpSlots);
-      fill_table(g, hb, hd, wtab, log_slots, lane, 32);
+      fill_table(hl, hd, wtab, log_slots, lane, 32);
       __syncwarp();
       uint64_t found_group = 0;
       for (int32_t c0 = 0; c0 < np; c0 += 32)
-        probe_chunk<PV>(g, g.part + pb, np, c0, 32, wtab, wcnt, log_slots, ws, t, found_total,
-                        found_group);
+        probe_chunk<PV, kWindows>(g, g.part + pb, np, c0, 32, wtab, wcnt, log_slots, ws, t,
+                                  found_total, found_group);
       if (PV || tg) {
         found_group = warp_sum_u64(found_group);
         if (lane == 0 && found_group)
@@ -366,7 +445,7 @@ __device__ __forceinline__ void warp_groups(const Lists &g, const int32_t *__res
 
 // Main counting kernel: CTA groups first (the heavy ones), then warp groups.
 template <bool PV>
-__global__ void __launch_bounds__(kMainThreads)
+__global__ void __launch_bounds__(kMainThreads, kMainMinBlocks)
 k_count(Lists g, const int32_t *__restrict__ warp_list, const int32_t *__restrict__ cta_list,
         Ctrl *ctrl, int64_t *t, int64_t *tg) {
   __shared__ int32_t s_tab[kMainSlots];
@@ -376,9 +455,9 @@ k_count(Lists g, const int32_t *__restrict__ warp_list, const int32_t *__restric
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   clear_table<PV>(s_tab, s_cnt, kMainSlots, tid, kMainThreads);
   uint64_t found_total = 0;
-  cta_groups<PV, kMainThreads, kMainSlots>(g, cta_list, ctrl->n_cta_groups,
-                                           &ctrl->next_cta_group, s_tab, s_cnt, s_ws, s_sh, t, tg,
-                                           found_total);
+  cta_groups<PV, kMainThreads, kMainSlots, kWindows>(g, cta_list, ctrl->n_cta_groups,
+                                                     &ctrl->next_cta_group, s_tab, s_cnt, s_ws,
+                                                     s_sh, t, tg, found_total);
   warp_groups<PV>(g, warp_list, ctrl->n_warp_groups, &ctrl->next_warp_group,
                   s_tab + warp * kWarpSlots, s_cnt + warp * kWarpSlots, s_ws[warp], t, tg,
                   found_total);
@@ -388,7 +467,7 @@ k_count(Lists g, const int32_t *__restrict__ warp_list, const int32_t *__restric
 
 // Groups whose hashed list is longer than kCtaMaxRow (rare).
 template <bool PV>
-__global__ void __launch_bounds__(kBigThreads)
+__global__ void __launch_bounds__(kBigThreads, kBigMinBlocks)
 k_count_big(Lists g, const int32_t *__restrict__ big_list, Ctrl *ctrl, int64_t *t,
             int64_t *tg) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -399,8 +478,9 @@ k_count_big(Lists g, const int32_t *__restrict__ big_list, Ctrl *ctrl, int64_t *
   const int tid = threadIdx.x, lane = tid & 31;
   clear_table<PV>(tab, cnt, kBigSlots, tid, kBigThreads);
   uint64_t found_total = 0;
-  cta_groups<PV, kBigThreads, kBigSlots>(g, big_list, ctrl->n_big_groups, &ctrl->next_big_group,
-                                         tab, cnt, s_ws, s_sh, t, tg, found_total);
+  cta_groups<PV, kBigThreads, kBigSlots, kBigWindows>(g, big_list, ctrl->n_big_groups,
+                                                      &ctrl->next_big_group, tab, cnt, s_ws,
+                                                      s_sh, t, tg, found_total);
   found_total = warp_sum_u64(found_total);
   if (lane == 0 && found_total) atomicAdd(&ctrl->total, (unsigned long long)found_total);
 }
@@ -525,8 +605,8 @@ cudaError_t prepare_count_kernels() {
   return e;
 }
 
-cudaError_t launch_count(const int32_t *off, const int32_t *col, const int32_t *goff,
-                         const int32_t *part, const int32_t *warp_groups,
+cudaError_t launch_count(const int32_t *off, const int32_t *voff, const int32_t *col4,
+                         const int32_t *goff, const int32_t *part, const int32_t *warp_groups,
                          const int32_t *cta_groups, const int32_t *big_groups, Ctrl *ctrl,
                          int64_t *t, int64_t *tg, cudaStream_t st) {
   const bool pv = t != nullptr;
@@ -534,7 +614,7 @@ cudaError_t launch_count(const int32_t *off, const int32_t *col, const int32_t *
   cudaError_t e = count_grid(pv, &cg);
   if (e != cudaSuccess) return e;
   const size_t big_smem = (size_t)4 * kBigSlots * (pv ? 2 : 1);
-  const Lists g{off, col, goff, part};
+  const Lists g{off, voff, col4, goff, part};
   // the long lists first, on their own wide CTAs
   if (pv) {
     k_count_big<true><<<cg.big_blocks, kBigThreads, big_smem, st>>>(g, big_groups, ctrl, t,

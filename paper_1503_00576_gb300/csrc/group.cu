@@ -38,15 +38,27 @@ __device__ __forceinline__ void split_edge(const int32_t *__restrict__ off, int3
   }
 }
 
+// Group sizes, and the copy of every forward list into the padded column
+// array: list u occupies words [voff[u], voff[u+1]) of col4, its entries in
+// the order of col, and the rest of its last word holds -1 (an id no hash
+// slot ever matches), so the counting kernel can stream lists as whole
+// aligned 16-byte words.
 __global__ void __launch_bounds__(kGroupThreads)
 k_group_count(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
-              const int32_t *__restrict__ off, int32_t heavy_ratio_pct,
-              const Ctrl *__restrict__ ctrl, int32_t *gcnt) {
+              const int32_t *__restrict__ off, const int32_t *__restrict__ voff,
+              int32_t heavy_ratio_pct, const Ctrl *__restrict__ ctrl, int32_t *gcnt,
+              int32_t *__restrict__ col4) {
   const uint32_t m = ctrl->m;
   const uint32_t stride = gridDim.x * kGroupThreads;
   for (uint32_t e = blockIdx.x * kGroupThreads + threadIdx.x; e < m; e += stride) {
+    const int32_t u = __ldg(row + e), v = __ldg(col + e);
     int32_t h, l;
-    split_edge(off, __ldg(row + e), __ldg(col + e), heavy_ratio_pct, h, l);
+    split_edge(off, u, v, heavy_ratio_pct, h, l);
+    const int32_t ub = __ldg(off + u), ue = __ldg(off + u + 1);
+    int32_t *dst = col4 + 4 * (size_t)__ldg(voff + u);
+    dst[(int32_t)e - ub] = v;
+    if ((int32_t)e == ue - 1)  // the list's last entry pads its word
+      for (int32_t j = ue - ub; j & 3; ++j) dst[j] = -1;
     const uint32_t active = __activemask();
     const uint32_t peers = __match_any_sync(active, h);
     const int lane = threadIdx.x & 31;
@@ -127,10 +139,11 @@ uint32_t group_grid(uint32_t m_bound) {
 }  // namespace
 
 void launch_group_count(const int32_t *row, const int32_t *col, const int32_t *off,
-                        uint32_t m_bound, int32_t heavy_ratio_pct, Ctrl *ctrl, int32_t *gcnt,
-                        cudaStream_t st) {
-  k_group_count<<<group_grid(m_bound), kGroupThreads, 0, st>>>(row, col, off, heavy_ratio_pct,
-                                                               ctrl, gcnt);
+                        const int32_t *voff, uint32_t m_bound, int32_t heavy_ratio_pct,
+                        Ctrl *ctrl, int32_t *gcnt, int32_t *col4, cudaStream_t st) {
+  k_group_count<<<group_grid(m_bound), kGroupThreads, 0, st>>>(row, col, off, voff,
+                                                               heavy_ratio_pct, ctrl, gcnt,
+                                                               col4);
   note_launch();
 }
 

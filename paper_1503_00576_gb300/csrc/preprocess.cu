@@ -455,12 +455,16 @@ k_orient(const uint64_t *__restrict__ keys, int b,
 
 // ---------------------------------------------------------------------------
 // offsets: exclusive scan of per-vertex counts.  Used for the node array
-// (counts = out-degrees) and for the partner groups of the counting phase
-// (counts = partners per group), where it also bins the groups that can
-// hold a triangle (>= 1 partner, >= 2 entries in the hashed list) by the
-// length of the hashed list: one warp, or a whole CTA.
+// (counts = out-degrees), for the node array of the padded column array
+// (counts = out-degrees rounded up to whole 16-byte words, in words) and for
+// the partner groups of the counting phase (counts = partners per group),
+// where it also bins the groups that can hold a triangle (>= 1 partner,
+// >= 2 entries in the hashed list) by the length of the hashed list: one
+// warp, or a whole CTA.
 // ---------------------------------------------------------------------------
-template <bool GROUPS>
+enum { kScanPlain = 0, kScanGroups = 1, kScanWords = 2 };
+
+template <int KIND>
 __global__ void __launch_bounds__(kScanThreads)
 k_offsets(const int32_t *__restrict__ counts, int32_t n, int32_t *__restrict__ off,
           const int32_t *__restrict__ row_off, int32_t *__restrict__ warp_list,
@@ -483,6 +487,7 @@ k_offsets(const int32_t *__restrict__ counts, int32_t n, int32_t *__restrict__ o
   for (int i = 0; i < IPT; ++i) {
     const uint32_t v = first + i;
     d[i] = v < (uint32_t)n ? __ldg(counts + v) : 0;
+    if (KIND == kScanWords) d[i] = (d[i] + 3) >> 2;
     sum += (uint32_t)d[i];
   }
   uint32_t tile_sum;
@@ -496,7 +501,7 @@ k_offsets(const int32_t *__restrict__ counts, int32_t n, int32_t *__restrict__ o
     if (v < items) off[v] = (int32_t)run;
     run += (uint32_t)d[i];
   }
-  if constexpr (GROUPS) {
+  if constexpr (KIND == kScanGroups) {
   // bin groups: one appending atomic per warp and list
 #pragma unroll
   for (int i = 0; i < IPT; ++i) {
@@ -603,11 +608,24 @@ void launch_offsets(const int32_t *counts, int32_t n, int32_t *off, const int32_
   const uint32_t grid = max(1u, (items + kScanTile - 1) / kScanTile);
   tune.warp_max_list = min(max(tune.warp_max_list, 0), kWarpMaxRow);  // warp tables hold 4x
   if (row_off)
-    k_offsets<true><<<grid, kScanThreads, 0, st>>>(counts, n, off, row_off, warp_list, cta_list,
-                                                   big_list, tune, status, ticket, ctrl);
+    k_offsets<kScanGroups><<<grid, kScanThreads, 0, st>>>(counts, n, off, row_off, warp_list,
+                                                          cta_list, big_list, tune, status,
+                                                          ticket, ctrl);
   else
-    k_offsets<false><<<grid, kScanThreads, 0, st>>>(counts, n, off, nullptr, nullptr, nullptr,
-                                                    nullptr, tune, status, ticket, ctrl);
+    k_offsets<kScanPlain><<<grid, kScanThreads, 0, st>>>(counts, n, off, nullptr, nullptr,
+                                                         nullptr, nullptr, tune, status, ticket,
+                                                         ctrl);
+  note_launch();
+}
+
+void launch_word_offsets(const int32_t *counts, int32_t n, int32_t *voff,
+                         unsigned long long *status, uint32_t *ticket, Ctrl *ctrl,
+                         cudaStream_t st) {
+  const uint32_t items = (uint32_t)n + 1;
+  const uint32_t grid = max(1u, (items + kScanTile - 1) / kScanTile);
+  k_offsets<kScanWords><<<grid, kScanThreads, 0, st>>>(counts, n, voff, nullptr, nullptr,
+                                                       nullptr, nullptr, kDefaultTuning, status,
+                                                       ticket, ctrl);
   note_launch();
 }
 

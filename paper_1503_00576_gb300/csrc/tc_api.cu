@@ -166,6 +166,7 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   auto *st_orient = reinterpret_cast<unsigned long long *>(ws + L.st_orient);
   auto *st_scan = reinterpret_cast<unsigned long long *>(ws + L.st_scan);
   auto *st_scan2 = reinterpret_cast<unsigned long long *>(ws + L.st_scan2);
+  auto *st_scan3 = reinterpret_cast<unsigned long long *>(ws + L.st_scan3);
   uint64_t *keys_a = reinterpret_cast<uint64_t *>(ws + L.keys_a);
   uint64_t *keys_b = reinterpret_cast<uint64_t *>(ws + L.keys_b);
   uint64_t *vkeys_a = reinterpret_cast<uint64_t *>(ws + L.vkeys_a);
@@ -173,6 +174,8 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   int32_t *deg = deg_out ? deg_out : reinterpret_cast<int32_t *>(ws + L.deg);
   int32_t *outdeg = reinterpret_cast<int32_t *>(ws + L.outdeg);
   int32_t *off = reinterpret_cast<int32_t *>(ws + L.off);
+  int32_t *voff = reinterpret_cast<int32_t *>(ws + L.voff);
+  int32_t *col4 = reinterpret_cast<int32_t *>(ws + L.col4);
   int32_t *goff = reinterpret_cast<int32_t *>(ws + L.goff);
   int32_t *warp_groups = reinterpret_cast<int32_t *>(ws + L.warp_groups);
   int32_t *cta_groups = reinterpret_cast<int32_t *>(ws + L.cta_groups);
@@ -279,14 +282,16 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   pt.start(TC_PHASE_OFFSETS);
   launch_offsets(outdeg, n, off, nullptr, nullptr, nullptr, nullptr, tune, st_scan,
                  &ctrl->tile_ticket[kTicketScan], ctrl, st);
+  launch_word_offsets(outdeg, n, voff, st_scan3, &ctrl->tile_ticket[kTicketVecScan], ctrl, st);
   pt.stop(TC_PHASE_OFFSETS);
 
   // partner groups: each forward edge goes to the endpoint with the longer
-  // forward list; gcnt reuses the out-degree array
+  // forward list; gcnt reuses the out-degree array.  The same pass copies
+  // the lists into the padded column array col4.
   pt.start(TC_PHASE_GROUPS);
   int32_t *gcnt = outdeg;
   TC_CUDA(cudaMemsetAsync(gcnt, 0, sizeof(int32_t) * (size_t)n, st), "memset groups");
-  launch_group_count(row, col, off, m, tune.heavy_ratio_pct, ctrl, gcnt, st);
+  launch_group_count(row, col, off, voff, m, tune.heavy_ratio_pct, ctrl, gcnt, col4, st);
   launch_offsets(gcnt, n, goff, off, warp_groups, cta_groups, big_groups, tune, st_scan2,
                  &ctrl->tile_ticket[kTicketGroupScan], ctrl, st);
   launch_group_fill(row, col, off, m, tune.heavy_ratio_pct, ctrl, goff, gcnt, part, st);
@@ -294,8 +299,8 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   if (work_stats) launch_work(row, col, off, goff, m, n, tune.heavy_ratio_pct, ctrl, st);
 
   pt.start(TC_PHASE_COUNT);
-  cudaError_t e = launch_count(off, col, goff, part, warp_groups, cta_groups, big_groups, ctrl,
-                               t_out ? t_rank : nullptr, t_out ? nullptr : t_rank, st);
+  cudaError_t e = launch_count(off, voff, col4, goff, part, warp_groups, cta_groups, big_groups,
+                               ctrl, t_out ? t_rank : nullptr, t_out ? nullptr : t_rank, st);
   if (e == cudaSuccess && t_out) launch_gather_counts(t_rank, rank, n, t_out, st);
   if (e == cudaSuccess && batch) {
     if (t_out) {  // per graph: (sum of t) / 3

@@ -50,9 +50,10 @@ enum {
   kTicketSort = 0 /* .. kMaxPasses-1, one per radix pass */,
   kTicketOrient = kMaxPasses,
   kTicketScan = kMaxPasses + 1,
-  kTicketGroupScan = kMaxPasses + 2
+  kTicketGroupScan = kMaxPasses + 2,
+  kTicketVecScan = kMaxPasses + 3
 };
-static_assert(kTicketGroupScan < 24, "ticket slots");
+static_assert(kTicketVecScan < 24, "ticket slots");
 
 // Look-back status words: value in the low 62 bits, flag in the top 2.
 constexpr unsigned long long kFlagAggregate = 1ull << 62;
@@ -90,8 +91,9 @@ struct BatchDesc {
 // Workspace layout for an input of m_in pairs and n vertices.  All offsets
 // are 256-byte aligned.
 struct Layout {
-  size_t ctrl, hist, st_sort, st_orient, st_scan, st_scan2;
-  size_t keys_a, keys_b, deg, outdeg, off, goff, warp_groups, cta_groups, big_groups;
+  size_t ctrl, hist, st_sort, st_orient, st_scan, st_scan2, st_scan3;
+  size_t keys_a, keys_b, deg, outdeg, off, voff, goff, warp_groups, cta_groups, big_groups;
+  size_t col4;
   size_t rank, vkeys_a, vkeys_b, t_rank;
   size_t total;
   uint32_t sort_tiles, orient_tiles, scan_tiles;
@@ -113,6 +115,17 @@ constexpr int kScanTile = kScanThreads * kScanItemsPerThread;
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Number of bits that hold any id in [0, n): at least 1.
+inline int id_bits(int32_t n) {
+  int b = 1;
+  while (b < 31 && ((int64_t)1 << b) < (int64_t)n) ++b;
+  return b;
+}
+
+// Radix passes of one run over ids of b bits: the undirected keys (2b
+// bits), the rank keys (degree < 2^b) and the oriented keys (owner bits).
+inline int radix_passes(int b) { return (2 * b + 7) / 8 + 2 * ((b + 7) / 8); }
+
 inline Layout make_layout(int64_t m_in, int32_t n) {
   Layout L{};
   size_t p = 0;
@@ -130,15 +143,20 @@ inline Layout make_layout(int64_t m_in, int32_t n) {
   L.st_sort_words_per_pass = (size_t)L.sort_tiles * 256;
   L.ctrl = take(sizeof(Ctrl));
   L.hist = take(sizeof(uint32_t) * 256 * kMaxPasses);
-  L.st_sort = take(sizeof(unsigned long long) * L.st_sort_words_per_pass * kMaxPasses);
+  // look-back status words for the passes that ids of [0, n) need (a run
+  // with fewer vertices needs no more)
+  L.st_sort = take(sizeof(unsigned long long) * L.st_sort_words_per_pass *
+                   (size_t)radix_passes(id_bits(n > 0 ? n : 1)));
   L.st_orient = take(sizeof(unsigned long long) * L.orient_tiles);
   L.st_scan = take(sizeof(unsigned long long) * L.scan_tiles);
   L.st_scan2 = take(sizeof(unsigned long long) * L.scan_tiles);
+  L.st_scan3 = take(sizeof(unsigned long long) * L.scan_tiles);
   L.keys_a = take(sizeof(uint64_t) * m);
   L.keys_b = take(sizeof(uint64_t) * m);
   L.deg = take(sizeof(int32_t) * nv);
   L.outdeg = take(sizeof(int32_t) * nv);
   L.off = take(sizeof(int32_t) * (nv + 1));
+  L.voff = take(sizeof(int32_t) * (nv + 1));
   L.goff = take(sizeof(int32_t) * (nv + 1));
   L.warp_groups = take(sizeof(int32_t) * nv);
   L.cta_groups = take(sizeof(int32_t) * nv);
@@ -147,16 +165,13 @@ inline Layout make_layout(int64_t m_in, int32_t n) {
   L.vkeys_a = take(sizeof(uint64_t) * nv);
   L.vkeys_b = take(sizeof(uint64_t) * nv);
   L.t_rank = take(sizeof(int64_t) * nv);
+  // forward lists padded to whole 16-byte words: at most m + 3 min(n, m)
+  // elements, since each non-empty list adds at most 3
+  L.col4 = take(sizeof(int32_t) * (m + 3 * (nv < m ? nv : m)));
   L.total = p;
   return L;
 }
 
-// Number of bits that hold any id in [0, n): at least 1.
-inline int id_bits(int32_t n) {
-  int b = 1;
-  while (b < 31 && ((int64_t)1 << b) < (int64_t)n) ++b;
-  return b;
-}
 
 // Kernel-launch bookkeeping (defined in tc_api.cu).
 void note_launch();
@@ -193,10 +208,17 @@ void launch_orient(const uint64_t *keys, uint32_t m_in, int b, const int32_t *ra
 void launch_offsets(const int32_t *counts, int32_t n, int32_t *off, const int32_t *row_off,
                     int32_t *warp_list, int32_t *cta_list, int32_t *big_list, Tuning tune,
                     unsigned long long *status, uint32_t *ticket, Ctrl *ctrl, cudaStream_t st);
+// Exclusive scan of ceil(counts / 4) -> voff[0..n]: the node array of the
+// padded column array, in 16-byte words.
+void launch_word_offsets(const int32_t *counts, int32_t n, int32_t *voff,
+                         unsigned long long *status, uint32_t *ticket, Ctrl *ctrl,
+                         cudaStream_t st);
 // ---- launchers (group.cu) ----
+// Also copies every forward list into the padded column array col4 (list v
+// starts at word voff[v]; the rest of its last word is -1).
 void launch_group_count(const int32_t *row, const int32_t *col, const int32_t *off,
-                        uint32_t m_bound, int32_t heavy_ratio_pct, Ctrl *ctrl, int32_t *gcnt,
-                        cudaStream_t st);
+                        const int32_t *voff, uint32_t m_bound, int32_t heavy_ratio_pct,
+                        Ctrl *ctrl, int32_t *gcnt, int32_t *col4, cudaStream_t st);
 void launch_group_fill(const int32_t *row, const int32_t *col, const int32_t *off,
                        uint32_t m_bound, int32_t heavy_ratio_pct, Ctrl *ctrl,
                        const int32_t *goff, int32_t *gcnt, int32_t *part, cudaStream_t st);
@@ -208,8 +230,8 @@ void launch_work(const int32_t *row, const int32_t *col, const int32_t *off, con
 // t != nullptr: per-vertex counts (rank space).  Otherwise, if tg is not
 // nullptr, tg[h] += triangles found in group h (their sum per graph is the
 // graph's count).
-cudaError_t launch_count(const int32_t *off, const int32_t *col, const int32_t *goff,
-                         const int32_t *part, const int32_t *warp_groups,
+cudaError_t launch_count(const int32_t *off, const int32_t *voff, const int32_t *col4,
+                         const int32_t *goff, const int32_t *part, const int32_t *warp_groups,
                          const int32_t *cta_groups, const int32_t *big_groups, Ctrl *ctrl,
                          int64_t *t, int64_t *tg, cudaStream_t st);
 // Sets the counting kernels' attributes and occupancy for the current
