@@ -36,16 +36,16 @@ namespace tc {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kWarpSlots = 4 * kWarpMaxRow;  // per-warp table
+constexpr int kWarpSlots = 8 * kWarpMaxRow;  // per-warp table
 constexpr int kGroupChunk = 8;               // warp groups per atomic
 constexpr int kWindows = 4;                  // positions per lane loaded before probing
 constexpr int kBigWindows = 2;               // ... in the long-list kernel (40 registers)
 
-// Main kernel: 256-thread CTAs; CTA tables of 4096 slots serve hashed lists
-// of up to kCtaMaxRow entries (load <= 1/8 up to 512, <= 1/4 up to 1024).
+// Main kernel: 256-thread CTAs; CTA tables of 8192 slots serve hashed lists
+// of up to kCtaMaxRow entries (load <= 1/16 up to 512, <= 1/8 up to 1024).
 constexpr int kMainThreads = 256;
 constexpr int kMainWarps = kMainThreads / 32;
-constexpr int kMainSlots = 4096;
+constexpr int kMainSlots = 8192;
 constexpr int kMainMinBlocks = 4;  // 64 registers per thread
 // Long-list kernel: 512-thread CTAs, 8192 slots (lists up to 4096 entries
 // at once; longer lists in segments).
@@ -54,7 +54,7 @@ constexpr int kBigWarps = kBigThreads / 32;
 constexpr int kBigSlots = 8192;
 constexpr int kBigMinBlocks = 3;
 static_assert(kWarpSlots * kMainWarps <= kMainSlots, "warp tables must fit the CTA table");
-static_assert(4 * kCtaMaxRow <= kMainSlots, "CTA lists must fit at load <= 1/4");
+static_assert(8 * kCtaMaxRow <= kMainSlots, "CTA lists must fit at load <= 1/8");
 
 // Hash-set slots.  Ids are < 2^31 - 1, so 0x7fffffff marks an empty slot and
 // bit 31 of an occupied slot records that some key whose home is this slot
@@ -74,10 +74,12 @@ __device__ __forceinline__ int ceil_log2(uint32_t x) {
   return x <= 1 ? 0 : 32 - __clz(x - 1);
 }
 
-// Table size for a list of len entries: load <= 1/8 when it fits, else as
-// large as the capacity allows; -1 if even load 1/2 does not fit.
+// Table size for a list of len entries: load <= 1/16 when it fits, else as
+// large as the capacity allows; -1 if even load 1/2 does not fit.  A miss
+// costs one shared-memory read unless its home slot is flagged, and at load
+// 1/16 only ~0.2% of the slots are.
 __device__ __forceinline__ int table_log_slots(int32_t len, int capacity) {
-  int lg = ceil_log2(8u * (uint32_t)len);
+  int lg = ceil_log2(16u * (uint32_t)len);
   while ((1 << lg) > capacity && (1 << lg) >= 4 * len) --lg;
   return (1 << lg) <= capacity ? lg : -1;
 }
@@ -100,26 +102,62 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t x) {
 // Per-warp description of the chunk being probed: the non-empty partner
 // lists r = 0 .. k-1 in flat order.
 struct WarpScratch {
-  int2 bn[32];         // word mode: {col4 word of flat position 0 of list r, flat start of r+1}
-  long long eb[32];    // element mode: col4 element of flat position 0 of list r
-  int32_t enext[32];   // element mode: flat start of list r+1
-  int32_t l[32];       // the partner owning list r (per-vertex mode)
-  uint32_t lc[32];     // triangles found through that partner
+  union {
+    int2 bn[32];  // word mode: {col4 word of flat position 0 of list r, flat start of r+1}
+    struct {
+      long long eb[32];   // element mode: col4 element of flat position 0 of list r
+      int32_t enext[32];  // element mode: flat start of list r+1
+    };
+  };
+  int32_t l[32];    // the partner owning list r (per-vertex mode)
+  uint32_t lc[32];  // triangles found through that partner
 };
 
-// Empties tab[0..slots) and its per-slot counters.
+// Per-slot match counters of per-vertex mode: how many partners (of one
+// batch) hold the slot's key w in their lists, i.e. the triangles the group
+// adds to t(w).  With 16-bit counters two share a word; a batch has at most
+// kPartnerBatch partners and a list holds w at most once, so a counter never
+// carries into its neighbour.
+constexpr int kCounterBits = 16;
+static_assert(kCounterBits == 32 || kPartnerBatch <= 65535, "16-bit slot counters");
+
+__host__ __device__ constexpr int counter_words(int slots) {
+  return kCounterBits == 16 ? slots / 2 : slots;
+}
+
+__device__ __forceinline__ void count_add(uint32_t *cnt, uint32_t slot) {
+  if (kCounterBits == 16)
+    atomicAdd(&cnt[slot >> 1], 1u << ((slot & 1u) << 4));
+  else
+    atomicAdd(&cnt[slot], 1u);
+}
+
+// Reads and zeroes the counter of a slot (atomically: two share a word).
+__device__ __forceinline__ uint32_t count_take(uint32_t *cnt, uint32_t slot) {
+  if (kCounterBits == 16) {
+    const uint32_t hi = slot & 1u;
+    const uint32_t old = atomicAnd(&cnt[slot >> 1], hi ? 0x0000ffffu : 0xffff0000u);
+    return hi ? old >> 16 : old & 0xffffu;
+  }
+  const uint32_t c = cnt[slot];
+  cnt[slot] = 0u;
+  return c;
+}
+
+// Empties tab[0..slots) and the counters.
 template <bool PV>
 __device__ __forceinline__ void clear_table(int32_t *tab, uint32_t *cnt, int slots, int rank,
                                             int group) {
-  for (int i = rank; i < slots; i += group) {
-    tab[i] = kEmpty;
-    if (PV) cnt[i] = 0u;
-  }
+  for (int i = rank; i < slots; i += group) tab[i] = kEmpty;
+  if (PV)
+    for (int i = rank; i < counter_words(slots); i += group) cnt[i] = 0u;
 }
 
-// Inserts list[0..len) (distinct ids) into the empty hash set.
+// Inserts list[0..len) (distinct ids) into the empty hash set; the slot of
+// list[i] goes to slot_of[i].
 __device__ __forceinline__ void fill_table(const int32_t *__restrict__ list, int32_t len,
-                                           int32_t *tab, int log_slots, int rank, int group) {
+                                           int32_t *tab, uint16_t *slot_of, int log_slots,
+                                           int rank, int group) {
   const uint32_t msk = (1u << log_slots) - 1u;
   for (int32_t i = rank; i < len; i += group) {
     const int32_t x = __ldg(list + i);
@@ -131,47 +169,78 @@ __device__ __forceinline__ void fill_table(const int32_t *__restrict__ list, int
       if (h == home && !((uint32_t)old & kDisplaced)) atomicOr((unsigned *)&tab[h], kDisplaced);
       h = (h + 1u) & msk;
     }
+    slot_of[i] = (uint16_t)h;
   }
 }
 
-// Empties the first 2^log_slots slots again; in per-vertex mode, first adds
-// each slot's count to t(w) of the w stored there.
-template <bool PV>
-__device__ __forceinline__ void drain_table(int32_t *tab, uint32_t *cnt, int log_slots, int rank,
-                                            int group, int64_t *t) {
-  const int slots = 1 << log_slots;
-  for (int i = rank; i < slots; i += group) {
-    if (PV) {
-      const uint32_t c = cnt[i];
-      if (c) {
-        atomicAdd((unsigned long long *)&t[tab[i] & 0x7fffffff], (unsigned long long)c);
-        cnt[i] = 0u;
-      }
-    }
-    tab[i] = kEmpty;
+// Per-vertex mode: adds the counter of each of the len filled slots to t(w)
+// of its key and zeroes it.
+__device__ __forceinline__ void flush_counts(const int32_t *tab, uint32_t *cnt,
+                                             const uint16_t *slot_of, int32_t len, int rank,
+                                             int group, int64_t *t) {
+  for (int32_t i = rank; i < len; i += group) {
+    const uint32_t s = slot_of[i];
+    const uint32_t c = count_take(cnt, s);
+    if (c) atomicAdd((unsigned long long *)&t[tab[s] & 0x7fffffff], (unsigned long long)c);
   }
 }
 
-// Membership of x in the hash set; the slot holding x goes to *slot.
-__device__ __forceinline__ bool member(int32_t x, const int32_t *tab, int log_slots,
-                                       uint32_t *slot) {
-  uint32_t h = hash_slot((uint32_t)x, log_slots);
-  int32_t y = tab[h];
-  if ((y & 0x7fffffff) == x) {
-    *slot = h;
-    return true;
-  }
-  if (y >= 0) return false;  // home slot not flagged: x was never displaced past it
-  const uint32_t msk = (1u << log_slots) - 1u;
+// Empties the len filled slots again (work in proportion to the list, not
+// to the table).
+__device__ __forceinline__ void empty_table(int32_t *tab, const uint16_t *slot_of, int32_t len,
+                                            int rank, int group) {
+  for (int32_t i = rank; i < len; i += group) tab[slot_of[i]] = kEmpty;
+}
+
+// Slot of x along the probe sequence after its flagged home slot h, or -1.
+__device__ __forceinline__ int32_t probe_past(int32_t x, uint32_t h, const int32_t *tab,
+                                              uint32_t msk) {
   for (;;) {
     h = (h + 1u) & msk;
-    y = tab[h];
-    if ((y & 0x7fffffff) == x) {
-      *slot = h;
-      return true;
-    }
-    if (y == kEmpty) return false;
+    const int32_t y = tab[h];
+    if ((y & 0x7fffffff) == x) return (int32_t)h;
+    if (y == kEmpty) return -1;
   }
+}
+
+// Looks up N entries.  Each lookup reads its home slot; only a miss at a
+// flagged home slot probes on, and one test for all N decides whether any
+// must (the rare, divergent part).  Per-vertex mode bumps the counter beside
+// each matched slot (t(w)).  Returns the number of matches.
+template <bool PV, int N>
+__device__ __forceinline__ uint32_t lookup(const int32_t (&x)[N], const int32_t *tab,
+                                           uint32_t *cnt, int log_slots) {
+  uint32_t h[N];
+  int32_t y[N];
+  bool m[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) h[i] = hash_slot((uint32_t)x[i], log_slots);
+#pragma unroll
+  for (int i = 0; i < N; ++i) y[i] = tab[h[i]];
+  int32_t flagged_miss = 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    m[i] = (y[i] & 0x7fffffff) == x[i];
+    flagged_miss |= m[i] ? 0 : y[i];
+  }
+  if (flagged_miss < 0) {
+    const uint32_t msk = (1u << log_slots) - 1u;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      if (!m[i] && y[i] < 0) {
+        const int32_t s = probe_past(x[i], h[i], tab, msk);
+        m[i] = s >= 0;
+        h[i] = (uint32_t)s;
+      }
+    }
+  }
+  uint32_t hits = 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    if (PV && m[i]) count_add(cnt, h[i]);
+    hits += m[i] ? 1u : 0u;
+  }
+  return hits;
 }
 
 // Inclusive warp scan of one int32 per lane.
@@ -183,31 +252,6 @@ __device__ __forceinline__ int32_t warp_incl_scan(int32_t x) {
     if (lane >= o) x += y;
   }
   return x;
-}
-
-// Counts the matches of one element; per-vertex mode also bumps the counter
-// beside the matched slot (t(w)).
-template <bool PV>
-__device__ __forceinline__ uint32_t probe1(int32_t x, const int32_t *tab, uint32_t *cnt,
-                                           int log_slots) {
-  uint32_t slot = 0;
-  const bool hit = member(x, tab, log_slots, &slot);
-  if (PV && hit) atomicAdd(&cnt[slot], 1u);
-  return hit ? 1u : 0u;
-}
-
-// Adds a lane's matches of list r to the chunk's per-partner counters,
-// flushing the previous list's run when the lane moves on.
-template <bool PV>
-__device__ __forceinline__ void note_run(WarpScratch &ws, int r, uint32_t hits, uint32_t &run,
-                                         int &run_r) {
-  if (!PV || hits == 0) return;
-  if (r != run_r) {
-    if (run) atomicAdd(&ws.lc[run_r], run);
-    run = 0;
-    run_r = r;
-  }
-  run += hits;
 }
 
 // Streams N+(l) for the partners l = part[c0 .. c0+cs) (of np, cs <= 32)
@@ -222,9 +266,8 @@ __device__ __forceinline__ void note_run(WarpScratch &ws, int r, uint32_t hits, 
 //  * elements: a position is one list entry (one 4-byte load), for chunks
 //    of a few short lists, where whole words would be mostly padding.
 // W positions per lane are loaded before any is probed.  Matches are
-// counted in registers; per partner they reach shared memory only when a
-// lane's cursor leaves that partner; per w they go to the counter beside
-// w's slot.
+// counted in registers; per partner they go to a shared counter once per
+// position, per w to the counter beside w's slot.
 template <bool PV, int W>
 __device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__restrict__ part,
                                             int32_t np, int32_t c0, int32_t cs,
@@ -267,8 +310,6 @@ __device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__res
   __syncwarp();
   int r = 0;
   uint32_t found = 0;  // matches of this lane in this chunk
-  uint32_t run = 0;    // matches of this lane for list run_r
-  int run_r = 0;
   if (words) {
     const int4 *__restrict__ col4v = reinterpret_cast<const int4 *>(g.col4);
     int2 bn = ws.bn[0];
@@ -288,12 +329,10 @@ __device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__res
 #pragma unroll
       for (int q = 0; q < W; ++q) {
         if (rq[q] < 0) continue;
-        const uint32_t hits = probe1<PV>(x[q].x, tab, cnt, log_slots) +
-                              probe1<PV>(x[q].y, tab, cnt, log_slots) +
-                              probe1<PV>(x[q].z, tab, cnt, log_slots) +
-                              probe1<PV>(x[q].w, tab, cnt, log_slots);
+        const int32_t e[4] = {x[q].x, x[q].y, x[q].z, x[q].w};
+        const uint32_t hits = lookup<PV, 4>(e, tab, cnt, log_slots);
         found += hits;
-        note_run<PV>(ws, rq[q], hits, run, run_r);
+        if (PV && hits) atomicAdd(&ws.lc[rq[q]], hits);
       }
     }
   } else {
@@ -319,16 +358,16 @@ __device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__res
 #pragma unroll
       for (int q = 0; q < W; ++q) {
         if (rq[q] < 0) continue;
-        const uint32_t hits = probe1<PV>(x[q], tab, cnt, log_slots);
+        const int32_t e[1] = {x[q]};
+        const uint32_t hits = lookup<PV, 1>(e, tab, cnt, log_slots);
         found += hits;
-        note_run<PV>(ws, rq[q], hits, run, run_r);
+        if (PV && hits) atomicAdd(&ws.lc[rq[q]], hits);
       }
     }
   }
   found_total += found;
   found_group += found;
   if (PV) {
-    if (run) atomicAdd(&ws.lc[run_r], run);
     __syncwarp();
     if (lane < k && ws.lc[lane])
       atomicAdd((unsigned long long *)&t[ws.l[lane]], (unsigned long long)ws.lc[lane]);
@@ -346,13 +385,16 @@ struct CtaShared {
 // chunks of partners (32, or fewer when a group has few partners, so that
 // every warp gets about two).  A list too long for the table at load 1/2 is
 // hashed in equal segments, one after another, each probed by all partners:
-// N+(h) & N+(l) is the disjoint union of the segments' intersections.  The
-// table (SLOTS slots) is empty on entry and on exit.
+// N+(h) & N+(l) is the disjoint union of the segments' intersections.  In
+// per-vertex mode the slot counters are handed on to t[] after every batch
+// of kPartnerBatch partners.  The table (SLOTS slots) is empty on entry and
+// on exit.
 template <bool PV, int THREADS, int SLOTS, int W>
 __device__ __forceinline__ void cta_groups(const Lists &g, const int32_t *__restrict__ list,
                                            uint32_t n_list, uint32_t *cursor, int32_t *tab,
-                                           uint32_t *cnt, WarpScratch *s_ws, CtaShared &sh,
-                                           int64_t *t, int64_t *tg, uint64_t &found_total) {
+                                           uint32_t *cnt, uint16_t *slot_of, WarpScratch *s_ws,
+                                           CtaShared &sh, int64_t *t, int64_t *tg,
+                                           uint64_t &found_total) {
   constexpr int WARPS = THREADS / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (;;) {
@@ -377,19 +419,28 @@ __device__ __forceinline__ void cta_groups(const Lists &g, const int32_t *__rest
     for (int32_t s0 = 0; s0 < hd; s0 += seg_len) {
       const int32_t len = min(seg_len, hd - s0);
       if (tid == 0) sh.chunk = 0u;
-      fill_table(hl + s0, len, tab, log_slots, tid, THREADS);
+      fill_table(hl + s0, len, tab, slot_of, log_slots, tid, THREADS);
       __syncthreads();
-      for (;;) {
-        uint32_t c = 0;
-        if (lane == 0) c = atomicAdd(&sh.chunk, 1u);
-        c = __shfl_sync(kFull, c, 0);
-        const int32_t c0 = (int32_t)c * cs;
-        if (c0 >= np) break;
-        probe_chunk<PV, W>(g, g.part + pb, np, c0, cs, tab, cnt, log_slots, s_ws[warp], t,
-                           found_total, found_group);
+      for (int32_t b0 = 0;;) {
+        const int32_t b1 = np - b0 > kPartnerBatch ? b0 + kPartnerBatch : np;
+        for (;;) {
+          uint32_t c = 0;
+          if (lane == 0) c = atomicAdd(&sh.chunk, 1u);
+          c = __shfl_sync(kFull, c, 0);
+          const int32_t c0 = b0 + (int32_t)c * cs;
+          if (c0 >= b1) break;
+          probe_chunk<PV, W>(g, g.part + pb, b1, c0, cs, tab, cnt, log_slots, s_ws[warp], t,
+                             found_total, found_group);
+        }
+        __syncthreads();
+        if (PV) flush_counts(tab, cnt, slot_of, len, tid, THREADS, t);
+        if (b1 >= np) break;
+        if (tid == 0) sh.chunk = 0u;
+        __syncthreads();  // counters handed on, chunk counter reset
+        b0 = b1;
       }
-      __syncthreads();
-      drain_table<PV>(tab, cnt, log_slots, tid, THREADS, t);
+      if (PV) __syncthreads();  // flushes read keys from the slots emptied next
+      empty_table(tab, slot_of, len, tid, THREADS);
       if (s0 + seg_len < hd) __syncthreads();  // next segment refills the table
     }
     if (PV || tg) {
@@ -406,12 +457,13 @@ __device__ __forceinline__ void cta_groups(const Lists &g, const int32_t *__rest
 }
 
 // Groups of `list` counted by one warp each with a private table of
-// kWarpSlots slots (empty on entry and on exit).
+// kWarpSlots slots (empty on entry and on exit).  A warp group has at most
+// kPartnerBatch partners (launch_offsets bins larger ones to CTAs).
 template <bool PV>
 __device__ __forceinline__ void warp_groups(const Lists &g, const int32_t *__restrict__ list,
                                             uint32_t n_list, uint32_t *cursor, int32_t *wtab,
-                                            uint32_t *wcnt, WarpScratch &ws, int64_t *t,
-                                            int64_t *tg, uint64_t &found_total) {
+                                            uint32_t *wcnt, uint16_t *slot_of, WarpScratch &ws,
+                                            int64_t *t, int64_t *tg, uint64_t &found_total) {
   const int lane = threadIdx.x & 31;
   for (;;) {
     uint32_t g0 = 0;
@@ -425,7 +477,7 @@ __device__ __forceinline__ void warp_groups(const Lists &g, const int32_t *__res
       const int32_t *hl = g.col4 + 4 * (size_t)__ldg(g.voff + h);
       const int32_t pb = __ldg(g.goff + h), np = __ldg(g.goff + h + 1) - pb;
       const int log_slots = table_log_slots(hd, kWarpSlots);
-      fill_table(hl, hd, wtab, log_slots, lane, 32);
+      fill_table(hl, hd, wtab, slot_of, log_slots, lane, 32);
       __syncwarp();
       uint64_t found_group = 0;
       for (int32_t c0 = 0; c0 < np; c0 += 32)
@@ -437,30 +489,46 @@ __device__ __forceinline__ void warp_groups(const Lists &g, const int32_t *__res
           atomicAdd((unsigned long long *)(PV ? &t[h] : &tg[h]), (unsigned long long)found_group);
       }
       __syncwarp();
-      drain_table<PV>(wtab, wcnt, log_slots, lane, 32, t);
+      if (PV) {
+        flush_counts(wtab, wcnt, slot_of, hd, lane, 32, t);
+        __syncwarp();
+      }
+      empty_table(wtab, slot_of, hd, lane, 32);
       __syncwarp();
     }
   }
 }
+
+// Dynamic shared memory of the counting kernels: the hash table, the slot
+// counters (per-vertex mode) and the slot of every hashed entry.
+constexpr size_t table_smem(int slots, int max_len, bool pv) {
+  return (size_t)4 * slots + (pv ? (size_t)4 * counter_words(slots) : 0) + (size_t)2 * max_len;
+}
+constexpr size_t main_smem(bool pv) { return table_smem(kMainSlots, kCtaMaxRow, pv); }
+constexpr size_t big_smem(bool pv) { return table_smem(kBigSlots, kBigSlots / 2, pv); }
+static_assert(kMainWarps * kWarpMaxRow <= kCtaMaxRow, "warp slot maps must fit the CTA's");
 
 // Main counting kernel: CTA groups first (the heavy ones), then warp groups.
 template <bool PV>
 __global__ void __launch_bounds__(kMainThreads, kMainMinBlocks)
 k_count(Lists g, const int32_t *__restrict__ warp_list, const int32_t *__restrict__ cta_list,
         Ctrl *ctrl, int64_t *t, int64_t *tg) {
-  __shared__ int32_t s_tab[kMainSlots];
-  __shared__ uint32_t s_cnt[PV ? kMainSlots : 1];
+  extern __shared__ __align__(16) unsigned char smem[];
+  int32_t *s_tab = reinterpret_cast<int32_t *>(smem);
+  uint32_t *s_cnt = reinterpret_cast<uint32_t *>(smem + 4 * kMainSlots);
+  uint16_t *s_slot =
+      reinterpret_cast<uint16_t *>(smem + 4 * kMainSlots + (PV ? 4 * counter_words(kMainSlots) : 0));
   __shared__ WarpScratch s_ws[kMainWarps];
   __shared__ CtaShared s_sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   clear_table<PV>(s_tab, s_cnt, kMainSlots, tid, kMainThreads);
   uint64_t found_total = 0;
   cta_groups<PV, kMainThreads, kMainSlots, kWindows>(g, cta_list, ctrl->n_cta_groups,
-                                                     &ctrl->next_cta_group, s_tab, s_cnt, s_ws,
-                                                     s_sh, t, tg, found_total);
+                                                     &ctrl->next_cta_group, s_tab, s_cnt, s_slot,
+                                                     s_ws, s_sh, t, tg, found_total);
   warp_groups<PV>(g, warp_list, ctrl->n_warp_groups, &ctrl->next_warp_group,
-                  s_tab + warp * kWarpSlots, s_cnt + warp * kWarpSlots, s_ws[warp], t, tg,
-                  found_total);
+                  s_tab + warp * kWarpSlots, s_cnt + warp * counter_words(kWarpSlots),
+                  s_slot + warp * kWarpMaxRow, s_ws[warp], t, tg, found_total);
   found_total = warp_sum_u64(found_total);
   if (lane == 0 && found_total) atomicAdd(&ctrl->total, (unsigned long long)found_total);
 }
@@ -473,14 +541,16 @@ k_count_big(Lists g, const int32_t *__restrict__ big_list, Ctrl *ctrl, int64_t *
   extern __shared__ __align__(16) unsigned char smem[];
   int32_t *tab = reinterpret_cast<int32_t *>(smem);
   uint32_t *cnt = reinterpret_cast<uint32_t *>(smem + 4 * kBigSlots);
+  uint16_t *slot_of =
+      reinterpret_cast<uint16_t *>(smem + 4 * kBigSlots + (PV ? 4 * counter_words(kBigSlots) : 0));
   __shared__ WarpScratch s_ws[kBigWarps];
   __shared__ CtaShared s_sh;
   const int tid = threadIdx.x, lane = tid & 31;
   clear_table<PV>(tab, cnt, kBigSlots, tid, kBigThreads);
   uint64_t found_total = 0;
   cta_groups<PV, kBigThreads, kBigSlots, kBigWindows>(g, big_list, ctrl->n_big_groups,
-                                                      &ctrl->next_big_group, tab, cnt, s_ws,
-                                                      s_sh, t, tg, found_total);
+                                                      &ctrl->next_big_group, tab, cnt, slot_of,
+                                                      s_ws, s_sh, t, tg, found_total);
   found_total = warp_sum_u64(found_total);
   if (lane == 0 && found_total) atomicAdd(&ctrl->total, (unsigned long long)found_total);
 }
@@ -560,6 +630,27 @@ struct CountGrid {
   int main_blocks, big_blocks;
 };
 
+template <bool PV>
+cudaError_t count_grid_t(int dev, CountGrid *out) {
+  cudaError_t e = cudaFuncSetAttribute(k_count<PV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)main_smem(PV));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_count_big<PV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)big_smem(PV));
+  if (e != cudaSuccess) return e;
+  int sms = 0, per_main = 0, per_big = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_main, k_count<PV>, kMainThreads,
+                                                    main_smem(PV));
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_big, k_count_big<PV>, kBigThreads,
+                                                      big_smem(PV));
+  if (e != cudaSuccess) return e;
+  sms = sms > 0 ? sms : 1;
+  *out = CountGrid{sms * (per_main > 0 ? per_main : 1), sms * (per_big > 0 ? per_big : 1)};
+  return cudaSuccess;
+}
+
 cudaError_t count_grid(bool pv, CountGrid *out) {
   static CountGrid cache[kMaxDevices][2];
   int dev = 0;
@@ -569,28 +660,9 @@ cudaError_t count_grid(bool pv, CountGrid *out) {
     *out = cache[dev][pv];
     return cudaSuccess;
   }
-  const size_t big_smem = (size_t)4 * kBigSlots * (pv ? 2 : 1);
-  e = pv ? cudaFuncSetAttribute(k_count_big<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)big_smem)
-         : cudaFuncSetAttribute(k_count_big<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)big_smem);
+  CountGrid g{};
+  e = pv ? count_grid_t<true>(dev, &g) : count_grid_t<false>(dev, &g);
   if (e != cudaSuccess) return e;
-  int sms = 0, per_main = 0, per_big = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (pv) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_main, k_count<true>, kMainThreads, 0);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_big, k_count_big<true>, kBigThreads,
-                                                        big_smem);
-  } else {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_main, k_count<false>, kMainThreads, 0);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_big, k_count_big<false>,
-                                                        kBigThreads, big_smem);
-  }
-  if (e != cudaSuccess) return e;
-  sms = sms > 0 ? sms : 1;
-  CountGrid g{sms * (per_main > 0 ? per_main : 1), sms * (per_big > 0 ? per_big : 1)};
   if (dev >= 0 && dev < kMaxDevices) cache[dev][pv] = g;
   *out = g;
   return cudaSuccess;
@@ -613,19 +685,20 @@ cudaError_t launch_count(const int32_t *off, const int32_t *voff, const int32_t 
   CountGrid cg;
   cudaError_t e = count_grid(pv, &cg);
   if (e != cudaSuccess) return e;
-  const size_t big_smem = (size_t)4 * kBigSlots * (pv ? 2 : 1);
   const Lists g{off, voff, col4, goff, part};
   // the long lists first, on their own wide CTAs
   if (pv) {
-    k_count_big<true><<<cg.big_blocks, kBigThreads, big_smem, st>>>(g, big_groups, ctrl, t,
-                                                                    nullptr);
-    k_count<true><<<cg.main_blocks, kMainThreads, 0, st>>>(g, warp_groups, cta_groups, ctrl, t,
-                                                           nullptr);
+    k_count_big<true><<<cg.big_blocks, kBigThreads, big_smem(true), st>>>(g, big_groups, ctrl, t,
+                                                                          nullptr);
+    k_count<true><<<cg.main_blocks, kMainThreads, main_smem(true), st>>>(g, warp_groups,
+                                                                         cta_groups, ctrl, t,
+                                                                         nullptr);
   } else {
-    k_count_big<false><<<cg.big_blocks, kBigThreads, big_smem, st>>>(g, big_groups, ctrl,
-                                                                     nullptr, tg);
-    k_count<false><<<cg.main_blocks, kMainThreads, 0, st>>>(g, warp_groups, cta_groups, ctrl,
-                                                            nullptr, tg);
+    k_count_big<false><<<cg.big_blocks, kBigThreads, big_smem(false), st>>>(g, big_groups, ctrl,
+                                                                            nullptr, tg);
+    k_count<false><<<cg.main_blocks, kMainThreads, main_smem(false), st>>>(g, warp_groups,
+                                                                           cta_groups, ctrl,
+                                                                           nullptr, tg);
   }
   note_launch();
   note_launch();
