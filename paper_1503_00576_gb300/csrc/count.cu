@@ -8,80 +8,79 @@
 // longer forward list is N+(h); partners l: their other endpoints):
 //
 //  * N+(h) is staged once in shared memory as an open-addressing hash set
-//    (multiplicative hashing, linear probing, load <= 1/4; <= 1/2 past 4096
-//    entries), by one warp when the group is small, else by a whole CTA
-//    whose warps claim chunks of partners from a shared counter;
-//  * the lists N+(l) of a chunk of <= 32 partners are read back to back as
-//    one flat sequence of aligned 16-byte words of the padded column array
-//    (each list padded with -1 to whole words, group.cu): lane p takes words
-//    p, p+32, ... and keeps a cursor on the list that holds its word.  Loads
-//    are coalesced 16-byte loads, every lane works however the lists are
-//    cut, and each lane has kWindows words in flight before it probes;
+//    (multiplicative hashing, linear probing, load <= 1/16 where it fits),
+//    by one warp when the group is small, else by a whole CTA whose warps
+//    claim chunks of partners from a shared counter;
+//  * the lists N+(l) of a chunk of <= 32 partners are read as one flat
+//    sequence of aligned 16-byte words of the padded column array (each
+//    list padded with -1 to whole words, group.cu): lane p takes words p,
+//    p+32, ..., finds each word's list by a warp vote over the list ends,
+//    and loads kWindows words (16-byte loads) before it probes any;
 //  * counts stay in registers and are reduced per warp (shuffles) into one
 //    uint64 atomic per warp at the end (the paper's reduction, fused).
 //
 // Per-vertex counts t(v) (Sec. I: the numerator of the clustering
 // coefficient): a triangle found in group h, partner l, element w adds one
-// to t(h), t(l) and t(w).  t(h) is summed over the group, t(l) over the
-// chunk (shared counters per partner) and t(w) in a counter beside w's hash
-// slot, so global atomics scale with the number of forward edges, not with
-// the number of triangles.
+// to t(h), t(l) and t(w).  t(h) is summed over the group, t(l) per word
+// (shared counters per partner) and t(w) in a counter beside w's hash slot,
+// so global atomics scale with the number of forward edges, not with the
+// number of triangles.
 //
-// A hashed list longer than 4096 entries (never seen in the workloads, but
-// allowed by |N+(v)| <= sqrt(2m)) is hashed in segments.  No step needs the
-// lists in sorted order: membership is by hashing, not by merging.
+// A hashed list longer than half the table (never seen in the workloads,
+// but allowed by |N+(v)| <= sqrt(2m)) is hashed in segments.  No step needs
+// the lists in sorted order: membership is by hashing, not by merging.
 #include "tc_common.cuh"
 
 namespace tc {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kWarpSlots = 8 * kWarpMaxRow;  // per-warp table
-constexpr int kGroupChunk = 8;               // warp groups per atomic
-constexpr int kWindows = 4;                  // positions per lane loaded before probing
-constexpr int kBigWindows = 2;               // ... in the long-list kernel (40 registers)
+constexpr int kGroupChunk = 8;  // warp groups per atomic
+constexpr int kWindows = 4;     // words per lane loaded before probing
+constexpr int kBigWindows = 2;  // ... in the long-list kernel (40 registers)
 
-// Main kernel: 256-thread CTAs; CTA tables of 8192 slots serve hashed lists
-// of up to kCtaMaxRow entries (load <= 1/16 up to 512, <= 1/8 up to 1024).
+// Main kernel: 256-thread CTAs; one table per CTA for CTA groups (lists of
+// up to kCtaMaxRow entries), carved into one table per warp for warp
+// groups.  Per-vertex mode adds a 32-bit counter per slot, and 6144 slots
+// keep four CTAs on an SM.
 constexpr int kMainThreads = 256;
 constexpr int kMainWarps = kMainThreads / 32;
-constexpr int kMainSlots = 8192;
 constexpr int kMainMinBlocks = 4;  // 64 registers per thread
+template <bool PV> __host__ __device__ constexpr int main_slots() { return PV ? 6144 : 8192; }
 // Long-list kernel: 512-thread CTAs, 8192 slots (lists up to 4096 entries
 // at once; longer lists in segments).
 constexpr int kBigThreads = 512;
 constexpr int kBigWarps = kBigThreads / 32;
 constexpr int kBigSlots = 8192;
-constexpr int kBigMinBlocks = 3;
-static_assert(kWarpSlots * kMainWarps <= kMainSlots, "warp tables must fit the CTA table");
-static_assert(8 * kCtaMaxRow <= kMainSlots, "CTA lists must fit at load <= 1/8");
+constexpr int kBigMinBlocks = 2;
+static_assert(main_slots<true>() >= 4 * kCtaMaxRow, "CTA lists must fit at load <= 1/4");
+static_assert(main_slots<true>() / kMainWarps >= 4 * kWarpMaxRow,
+              "warp lists must fit at load <= 1/4");
 
 // Hash-set slots.  Ids are < 2^31 - 1, so 0x7fffffff marks an empty slot and
 // bit 31 of an occupied slot records that some key whose home is this slot
 // was displaced further along (linear probing).  A lookup whose home slot is
-// neither the key nor flagged is a miss after one read: with the table at
-// most 1/4 full, almost every unsuccessful lookup stops there, which keeps
-// the lanes of a warp in step.  The padding id -1 never matches: a slot's
+// neither the key nor flagged is a miss after one read: at load 1/16 only
+// ~0.2% of the slots are flagged.  The padding id -1 never matches: a slot's
 // low 31 bits are non-negative.
 constexpr int32_t kEmpty = 0x7fffffff;
 constexpr uint32_t kDisplaced = 0x80000000u;
+constexpr uint32_t kHashMul = 0x9E3779B1u;
 
-__device__ __forceinline__ uint32_t hash_slot(uint32_t x, int log_slots) {
-  return (x * 0x9E3779B1u) >> (32 - log_slots);
+// Home slot of x in a table of `slots` slots (any size): the high word of
+// the multiplicative hash scaled to the table.
+__device__ __forceinline__ uint32_t hash_slot(uint32_t x, uint32_t slots) {
+  return __umulhi(x * kHashMul, slots);
 }
 
-__device__ __forceinline__ int ceil_log2(uint32_t x) {
-  return x <= 1 ? 0 : 32 - __clz(x - 1);
+__device__ __forceinline__ uint32_t next_slot(uint32_t h, uint32_t slots) {
+  return h + 1u == slots ? 0u : h + 1u;
 }
 
-// Table size for a list of len entries: load <= 1/16 when it fits, else as
-// large as the capacity allows; -1 if even load 1/2 does not fit.  A miss
-// costs one shared-memory read unless its home slot is flagged, and at load
-// 1/16 only ~0.2% of the slots are.
-__device__ __forceinline__ int table_log_slots(int32_t len, int capacity) {
-  int lg = ceil_log2(16u * (uint32_t)len);
-  while ((1 << lg) > capacity && (1 << lg) >= 4 * len) --lg;
-  return (1 << lg) <= capacity ? lg : -1;
+// Table size for a list of len entries: load 1/16 where it fits, else the
+// whole capacity (callers keep len <= capacity / 2).
+__device__ __forceinline__ uint32_t table_slots(int32_t len, uint32_t capacity) {
+  return min(16u * (uint32_t)max(len, 1), capacity);
 }
 
 // Read-only view of the forward lists and partner groups.
@@ -93,10 +92,29 @@ struct Lists {
   const int32_t *__restrict__ part;  // partners
 };
 
+// One hash set in shared memory.
+struct Table {
+  int32_t *tab;      // slots
+  uint32_t *cnt;     // per-vertex mode: match counter of each slot
+  uint32_t cnt_sa;   // shared-window address of cnt
+  uint32_t slots;    // size in use
+};
+
 __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
   return x;
+}
+
+__device__ __forceinline__ uint32_t shared_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Adds v to the shared word at saddr when c holds (predicated, no branch).
+__device__ __forceinline__ void red_add_if(uint32_t saddr, uint32_t v, bool c) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t@p red.shared.add.u32 [%0], %1;\n\t}"
+      ::"r"(saddr), "r"(v), "r"((uint32_t)c));
 }
 
 // Per-warp description of the chunk being probed: the non-empty partner
@@ -113,61 +131,31 @@ struct WarpScratch {
   uint32_t lc[32];  // triangles found through that partner
 };
 
-// Per-slot match counters of per-vertex mode: how many partners (of one
-// batch) hold the slot's key w in their lists, i.e. the triangles the group
-// adds to t(w).  With 16-bit counters two share a word; a batch has at most
-// kPartnerBatch partners and a list holds w at most once, so a counter never
-// carries into its neighbour.
-constexpr int kCounterBits = 16;
-static_assert(kCounterBits == 32 || kPartnerBatch <= 65535, "16-bit slot counters");
-
-__host__ __device__ constexpr int counter_words(int slots) {
-  return kCounterBits == 16 ? slots / 2 : slots;
-}
-
-__device__ __forceinline__ void count_add(uint32_t *cnt, uint32_t slot) {
-  if (kCounterBits == 16)
-    atomicAdd(&cnt[slot >> 1], 1u << ((slot & 1u) << 4));
-  else
-    atomicAdd(&cnt[slot], 1u);
-}
-
-// Reads and zeroes the counter of a slot (atomically: two share a word).
-__device__ __forceinline__ uint32_t count_take(uint32_t *cnt, uint32_t slot) {
-  if (kCounterBits == 16) {
-    const uint32_t hi = slot & 1u;
-    const uint32_t old = atomicAnd(&cnt[slot >> 1], hi ? 0x0000ffffu : 0xffff0000u);
-    return hi ? old >> 16 : old & 0xffffu;
-  }
-  const uint32_t c = cnt[slot];
-  cnt[slot] = 0u;
-  return c;
-}
-
 // Empties tab[0..slots) and the counters.
 template <bool PV>
 __device__ __forceinline__ void clear_table(int32_t *tab, uint32_t *cnt, int slots, int rank,
                                             int group) {
-  for (int i = rank; i < slots; i += group) tab[i] = kEmpty;
-  if (PV)
-    for (int i = rank; i < counter_words(slots); i += group) cnt[i] = 0u;
+  for (int i = rank; i < slots; i += group) {
+    tab[i] = kEmpty;
+    if (PV) cnt[i] = 0u;
+  }
 }
 
 // Inserts list[0..len) (distinct ids) into the empty hash set; the slot of
 // list[i] goes to slot_of[i].
 __device__ __forceinline__ void fill_table(const int32_t *__restrict__ list, int32_t len,
-                                           int32_t *tab, uint16_t *slot_of, int log_slots,
-                                           int rank, int group) {
-  const uint32_t msk = (1u << log_slots) - 1u;
+                                           const Table &tb, uint16_t *slot_of, int rank,
+                                           int group) {
   for (int32_t i = rank; i < len; i += group) {
     const int32_t x = __ldg(list + i);
-    const uint32_t home = hash_slot((uint32_t)x, log_slots);
+    const uint32_t home = hash_slot((uint32_t)x, tb.slots);
     uint32_t h = home;
     for (;;) {
-      const int32_t old = atomicCAS(&tab[h], kEmpty, x);
+      const int32_t old = atomicCAS(&tb.tab[h], kEmpty, x);
       if (old == kEmpty) break;
-      if (h == home && !((uint32_t)old & kDisplaced)) atomicOr((unsigned *)&tab[h], kDisplaced);
-      h = (h + 1u) & msk;
+      if (h == home && !((uint32_t)old & kDisplaced))
+        atomicOr((unsigned *)&tb.tab[h], kDisplaced);
+      h = next_slot(h, tb.slots);
     }
     slot_of[i] = (uint16_t)h;
   }
@@ -175,60 +163,59 @@ __device__ __forceinline__ void fill_table(const int32_t *__restrict__ list, int
 
 // Per-vertex mode: adds the counter of each of the len filled slots to t(w)
 // of its key and zeroes it.
-__device__ __forceinline__ void flush_counts(const int32_t *tab, uint32_t *cnt,
-                                             const uint16_t *slot_of, int32_t len, int rank,
-                                             int group, int64_t *t) {
+__device__ __forceinline__ void flush_counts(const Table &tb, const uint16_t *slot_of,
+                                             int32_t len, int rank, int group, int64_t *t) {
   for (int32_t i = rank; i < len; i += group) {
     const uint32_t s = slot_of[i];
-    const uint32_t c = count_take(cnt, s);
-    if (c) atomicAdd((unsigned long long *)&t[tab[s] & 0x7fffffff], (unsigned long long)c);
+    const uint32_t c = tb.cnt[s];
+    if (c) {
+      atomicAdd((unsigned long long *)&t[tb.tab[s] & 0x7fffffff], (unsigned long long)c);
+      tb.cnt[s] = 0u;
+    }
   }
 }
 
 // Empties the len filled slots again (work in proportion to the list, not
 // to the table).
-__device__ __forceinline__ void empty_table(int32_t *tab, const uint16_t *slot_of, int32_t len,
-                                            int rank, int group) {
-  for (int32_t i = rank; i < len; i += group) tab[slot_of[i]] = kEmpty;
+__device__ __forceinline__ void empty_table(const Table &tb, const uint16_t *slot_of,
+                                            int32_t len, int rank, int group) {
+  for (int32_t i = rank; i < len; i += group) tb.tab[slot_of[i]] = kEmpty;
 }
 
 // Slot of x along the probe sequence after its flagged home slot h, or -1.
-__device__ __forceinline__ int32_t probe_past(int32_t x, uint32_t h, const int32_t *tab,
-                                              uint32_t msk) {
+__device__ __forceinline__ int32_t probe_past(int32_t x, uint32_t h, const Table &tb) {
   for (;;) {
-    h = (h + 1u) & msk;
-    const int32_t y = tab[h];
+    h = next_slot(h, tb.slots);
+    const int32_t y = tb.tab[h];
     if ((y & 0x7fffffff) == x) return (int32_t)h;
     if (y == kEmpty) return -1;
   }
 }
 
 // Looks up N entries.  Each lookup reads its home slot; only a miss at a
-// flagged home slot probes on, and one test for all N decides whether any
-// must (the rare, divergent part).  Per-vertex mode bumps the counter beside
+// flagged home slot probes on, and one test of the N home slots' flags
+// decides whether any must (the rare, divergent part).  Per-vertex mode bumps the counter beside
 // each matched slot (t(w)).  Returns the number of matches.
 template <bool PV, int N>
-__device__ __forceinline__ uint32_t lookup(const int32_t (&x)[N], const int32_t *tab,
-                                           uint32_t *cnt, int log_slots) {
+__device__ __forceinline__ uint32_t lookup(const int32_t (&x)[N], const Table &tb) {
   uint32_t h[N];
   int32_t y[N];
   bool m[N];
 #pragma unroll
-  for (int i = 0; i < N; ++i) h[i] = hash_slot((uint32_t)x[i], log_slots);
+  for (int i = 0; i < N; ++i) h[i] = hash_slot((uint32_t)x[i], tb.slots);
 #pragma unroll
-  for (int i = 0; i < N; ++i) y[i] = tab[h[i]];
-  int32_t flagged_miss = 0;
+  for (int i = 0; i < N; ++i) y[i] = tb.tab[h[i]];
+  int32_t flagged = 0;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     m[i] = (y[i] & 0x7fffffff) == x[i];
-    flagged_miss |= m[i] ? 0 : y[i];
+    flagged |= y[i];
   }
-  if (flagged_miss < 0) {
-    const uint32_t msk = (1u << log_slots) - 1u;
+  if (flagged < 0) {  // some home slot is flagged: misses there probe on
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       if (!m[i] && y[i] < 0) {
-        const int32_t s = probe_past(x[i], h[i], tab, msk);
+        const int32_t s = probe_past(x[i], h[i], tb);
         m[i] = s >= 0;
         h[i] = (uint32_t)s;
       }
@@ -237,7 +224,7 @@ __device__ __forceinline__ uint32_t lookup(const int32_t (&x)[N], const int32_t 
   uint32_t hits = 0;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    if (PV && m[i]) count_add(cnt, h[i]);
+    if (PV) red_add_if(tb.cnt_sa + 4u * h[i], 1u, m[i]);
     hits += m[i] ? 1u : 0u;
   }
   return hits;
@@ -254,26 +241,69 @@ __device__ __forceinline__ int32_t warp_incl_scan(int32_t x) {
   return x;
 }
 
+// Word mode of probe_chunk: windows w .. w+NQ-1 of 32 words of the chunk's
+// flat sequence, lane p taking word 32 w + p of each.  The list of a word is
+// the number of lists ending at or before it: those ending at or before the
+// window's start (one vote) plus those whose last word lies in the window
+// before this lane (a bit mask OR-reduced over the lanes).  Lane r holds
+// list r's {base, end} in bn_r.  TAIL: the window reaches past total_v, and
+// the words beyond it are -1.
+template <bool PV, int NQ, bool TAIL>
+__device__ __forceinline__ void probe_windows(const Lists &g, int32_t w, int32_t total_v,
+                                              int2 bn_r, const Table &tb, uint32_t lc_sa,
+                                              uint32_t &found) {
+  const int lane = threadIdx.x & 31;
+  const int4 *__restrict__ col4v = reinterpret_cast<const int4 *>(g.col4);
+  const uint32_t lt = (1u << lane) - 1u;
+  int4 x[NQ];
+  int rq[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int32_t P = 32 * (w + q);
+    const int c0 = __popc(__ballot_sync(kFull, bn_r.y <= P));
+    const uint32_t b = (uint32_t)(bn_r.y - P - 1);
+    const uint32_t ends = __reduce_or_sync(kFull, b < 31u ? 1u << b : 0u);
+    const int r = c0 + __popc(ends & lt);
+    const int32_t base = __shfl_sync(kFull, bn_r.x, r & 31);
+    const int32_t p = P + lane;
+    if (TAIL) {
+      x[q] = make_int4(-1, -1, -1, -1);
+      if (p < total_v) x[q] = __ldg(col4v + (base + p));
+    } else {
+      x[q] = __ldg(col4v + (base + p));
+    }
+    rq[q] = r;
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int32_t e[4] = {x[q].x, x[q].y, x[q].z, x[q].w};
+    const uint32_t hits = lookup<PV, 4>(e, tb);
+    found += hits;
+    if (PV) red_add_if(lc_sa + 4u * (uint32_t)rq[q], hits, hits != 0u);
+  }
+}
+
 // Streams N+(l) for the partners l = part[c0 .. c0+cs) (of np, cs <= 32)
-// through the hash set of the group's list.  The chunk's non-empty lists are
-// concatenated into one flat sequence; lane p takes flat positions p, p+32,
-// ... and keeps a cursor on the list that holds its position (the cursor
-// only moves forward).  Two granularities, chosen per chunk by which needs
-// fewer warp steps:
+// through the hash set of the group's list.  The chunk's non-empty lists
+// are concatenated into one flat sequence.  Two granularities, chosen per
+// chunk by which needs fewer warp steps:
 //  * words: a position is one aligned 16-byte word of the padded column
 //    array (int4), four entries probed per load; padding entries are -1 and
-//    never match;
-//  * elements: a position is one list entry (one 4-byte load), for chunks
-//    of a few short lists, where whole words would be mostly padding.
-// W positions per lane are loaded before any is probed.  Matches are
-// counted in registers; per partner they go to a shared counter once per
-// position, per w to the counter beside w's slot.
+//    never match.  Lane p takes positions p, p+32, ... (coalesced loads);
+//    the list of each position comes from a warp vote over the list ends,
+//    with no per-lane cursor and no branch;
+//  * elements: a position is one list entry (one 4-byte load); lane p takes
+//    positions p, p+32, ... with a cursor on the list holding its position.
+//    For chunks of a few short lists, where whole words would be mostly
+//    padding.
+// Matches are counted in registers; per partner they go to a shared counter
+// (per word, or when an element-mode lane leaves the partner's list), per w
+// to the counter beside w's slot.
 template <bool PV, int W>
 __device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__restrict__ part,
                                             int32_t np, int32_t c0, int32_t cs,
-                                            const int32_t *tab, uint32_t *cnt, int log_slots,
-                                            WarpScratch &ws, int64_t *t, uint64_t &found_total,
-                                            uint64_t &found_group) {
+                                            const Table &tb, WarpScratch &ws, int64_t *t,
+                                            uint64_t &found_total, uint64_t &found_group) {
   const int lane = threadIdx.x & 31;
   const int32_t j = c0 + lane;
   int32_t l = 0, dl = 0, vb = 0;
@@ -308,34 +338,21 @@ __device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__res
     }
   }
   __syncwarp();
-  int r = 0;
   uint32_t found = 0;  // matches of this lane in this chunk
+  uint32_t run = 0;    // matches of this lane in list run_r not yet in ws.lc
+  int run_r = 0;
+  const uint32_t lc_sa = shared_addr(ws.lc);
   if (words) {
-    const int4 *__restrict__ col4v = reinterpret_cast<const int4 *>(g.col4);
-    int2 bn = ws.bn[0];
-    for (int32_t p0 = lane; p0 < total_v; p0 += 32 * W) {
-      int4 x[W];
-      int rq[W];
-#pragma unroll
-      for (int q = 0; q < W; ++q) {
-        const int32_t p = p0 + 32 * q;
-        rq[q] = -1;
-        if (p < total_v) {
-          while (p >= bn.y) bn = ws.bn[++r];
-          x[q] = __ldg(col4v + (bn.x + p));
-          rq[q] = r;
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < W; ++q) {
-        if (rq[q] < 0) continue;
-        const int32_t e[4] = {x[q].x, x[q].y, x[q].z, x[q].w};
-        const uint32_t hits = lookup<PV, 4>(e, tab, cnt, log_slots);
-        found += hits;
-        if (PV && hits) atomicAdd(&ws.lc[rq[q]], hits);
-      }
-    }
+    // lane r holds list r's base and end (flat start of list r+1)
+    const int2 bn_r = lane < k ? ws.bn[lane] : make_int2(0, INT32_MAX);
+    const int32_t full = total_v >> 5;  // windows of 32 words inside the sequence
+    int32_t w = 0;
+    for (; w + W <= full; w += W)
+      probe_windows<PV, W, false>(g, w, total_v, bn_r, tb, lc_sa, found);
+    for (; w < full; ++w) probe_windows<PV, 1, false>(g, w, total_v, bn_r, tb, lc_sa, found);
+    if (total_v & 31) probe_windows<PV, 1, true>(g, w, total_v, bn_r, tb, lc_sa, found);
   } else {
+    int r = 0;
     long long eb = ws.eb[0];
     int32_t next = ws.enext[0];
     for (int32_t p0 = lane; p0 < total_e; p0 += 32 * W) {
@@ -344,7 +361,7 @@ __device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__res
 #pragma unroll
       for (int q = 0; q < W; ++q) {
         const int32_t p = p0 + 32 * q;
-        rq[q] = -1;
+        x[q] = -1;
         if (p < total_e) {
           while (p >= next) {
             ++r;
@@ -352,22 +369,29 @@ __device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__res
             next = ws.enext[r];
           }
           x[q] = __ldg(g.col4 + (eb + p));
-          rq[q] = r;
         }
+        rq[q] = r;
       }
 #pragma unroll
       for (int q = 0; q < W; ++q) {
-        if (rq[q] < 0) continue;
         const int32_t e[1] = {x[q]};
-        const uint32_t hits = lookup<PV, 1>(e, tab, cnt, log_slots);
+        const uint32_t hits = lookup<PV, 1>(e, tb);
         found += hits;
-        if (PV && hits) atomicAdd(&ws.lc[rq[q]], hits);
+        if (PV) {
+          if (rq[q] != run_r) {
+            red_add_if(lc_sa + 4u * run_r, run, run != 0);
+            run = 0;
+            run_r = rq[q];
+          }
+          run += hits;
+        }
       }
     }
   }
   found_total += found;
   found_group += found;
   if (PV) {
+    red_add_if(lc_sa + 4u * run_r, run, run != 0);
     __syncwarp();
     if (lane < k && ws.lc[lane])
       atomicAdd((unsigned long long *)&t[ws.l[lane]], (unsigned long long)ws.lc[lane]);
@@ -383,18 +407,15 @@ struct CtaShared {
 
 // Groups of `list` counted by the whole CTA: N+(h) hashed once, warps claim
 // chunks of partners (32, or fewer when a group has few partners, so that
-// every warp gets about two).  A list too long for the table at load 1/2 is
-// hashed in equal segments, one after another, each probed by all partners:
-// N+(h) & N+(l) is the disjoint union of the segments' intersections.  In
-// per-vertex mode the slot counters are handed on to t[] after every batch
-// of kPartnerBatch partners.  The table (SLOTS slots) is empty on entry and
-// on exit.
+// every warp gets about two).  A list longer than half the table is hashed
+// in equal segments, one after another, each probed by all partners:
+// N+(h) & N+(l) is the disjoint union of the segments' intersections.  The
+// table (SLOTS slots) is empty on entry and on exit.
 template <bool PV, int THREADS, int SLOTS, int W>
 __device__ __forceinline__ void cta_groups(const Lists &g, const int32_t *__restrict__ list,
-                                           uint32_t n_list, uint32_t *cursor, int32_t *tab,
-                                           uint32_t *cnt, uint16_t *slot_of, WarpScratch *s_ws,
-                                           CtaShared &sh, int64_t *t, int64_t *tg,
-                                           uint64_t &found_total) {
+                                           uint32_t n_list, uint32_t *cursor, Table tb,
+                                           uint16_t *slot_of, WarpScratch *s_ws, CtaShared &sh,
+                                           int64_t *t, int64_t *tg, uint64_t &found_total) {
   constexpr int WARPS = THREADS / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (;;) {
@@ -413,34 +434,29 @@ __device__ __forceinline__ void cta_groups(const Lists &g, const int32_t *__rest
     const int32_t pb = __ldg(g.goff + h), np = __ldg(g.goff + h + 1) - pb;
     const int32_t nseg = (hd + SLOTS / 2 - 1) / (SLOTS / 2);
     const int32_t seg_len = (hd + nseg - 1) / nseg;
-    const int log_slots = table_log_slots(seg_len, SLOTS);
+    tb.slots = table_slots(seg_len, SLOTS);
     const int32_t cs = max(8, min(32, (np + 2 * WARPS - 1) / (2 * WARPS)));
     uint64_t found_group = 0;
     for (int32_t s0 = 0; s0 < hd; s0 += seg_len) {
       const int32_t len = min(seg_len, hd - s0);
       if (tid == 0) sh.chunk = 0u;
-      fill_table(hl + s0, len, tab, slot_of, log_slots, tid, THREADS);
+      fill_table(hl + s0, len, tb, slot_of, tid, THREADS);
       __syncthreads();
-      for (int32_t b0 = 0;;) {
-        const int32_t b1 = np - b0 > kPartnerBatch ? b0 + kPartnerBatch : np;
-        for (;;) {
-          uint32_t c = 0;
-          if (lane == 0) c = atomicAdd(&sh.chunk, 1u);
-          c = __shfl_sync(kFull, c, 0);
-          const int32_t c0 = b0 + (int32_t)c * cs;
-          if (c0 >= b1) break;
-          probe_chunk<PV, W>(g, g.part + pb, b1, c0, cs, tab, cnt, log_slots, s_ws[warp], t,
-                             found_total, found_group);
-        }
-        __syncthreads();
-        if (PV) flush_counts(tab, cnt, slot_of, len, tid, THREADS, t);
-        if (b1 >= np) break;
-        if (tid == 0) sh.chunk = 0u;
-        __syncthreads();  // counters handed on, chunk counter reset
-        b0 = b1;
+      for (;;) {
+        uint32_t c = 0;
+        if (lane == 0) c = atomicAdd(&sh.chunk, 1u);
+        c = __shfl_sync(kFull, c, 0);
+        const int32_t c0 = (int32_t)c * cs;
+        if (c0 >= np) break;
+        probe_chunk<PV, W>(g, g.part + pb, np, c0, cs, tb, s_ws[warp], t, found_total,
+                           found_group);
       }
-      if (PV) __syncthreads();  // flushes read keys from the slots emptied next
-      empty_table(tab, slot_of, len, tid, THREADS);
+      __syncthreads();
+      if (PV) {
+        flush_counts(tb, slot_of, len, tid, THREADS, t);
+        __syncthreads();  // flushes read keys from the slots emptied next
+      }
+      empty_table(tb, slot_of, len, tid, THREADS);
       if (s0 + seg_len < hd) __syncthreads();  // next segment refills the table
     }
     if (PV || tg) {
@@ -457,13 +473,12 @@ __device__ __forceinline__ void cta_groups(const Lists &g, const int32_t *__rest
 }
 
 // Groups of `list` counted by one warp each with a private table of
-// kWarpSlots slots (empty on entry and on exit).  A warp group has at most
-// kPartnerBatch partners (launch_offsets bins larger ones to CTAs).
-template <bool PV>
+// WSLOTS slots (empty on entry and on exit).
+template <bool PV, int WSLOTS>
 __device__ __forceinline__ void warp_groups(const Lists &g, const int32_t *__restrict__ list,
-                                            uint32_t n_list, uint32_t *cursor, int32_t *wtab,
-                                            uint32_t *wcnt, uint16_t *slot_of, WarpScratch &ws,
-                                            int64_t *t, int64_t *tg, uint64_t &found_total) {
+                                            uint32_t n_list, uint32_t *cursor, Table tb,
+                                            uint16_t *slot_of, WarpScratch &ws, int64_t *t,
+                                            int64_t *tg, uint64_t &found_total) {
   const int lane = threadIdx.x & 31;
   for (;;) {
     uint32_t g0 = 0;
@@ -476,13 +491,13 @@ __device__ __forceinline__ void warp_groups(const Lists &g, const int32_t *__res
       const int32_t hd = __ldg(g.off + h + 1) - __ldg(g.off + h);
       const int32_t *hl = g.col4 + 4 * (size_t)__ldg(g.voff + h);
       const int32_t pb = __ldg(g.goff + h), np = __ldg(g.goff + h + 1) - pb;
-      const int log_slots = table_log_slots(hd, kWarpSlots);
-      fill_table(hl, hd, wtab, slot_of, log_slots, lane, 32);
+      tb.slots = table_slots(hd, WSLOTS);
+      fill_table(hl, hd, tb, slot_of, lane, 32);
       __syncwarp();
       uint64_t found_group = 0;
       for (int32_t c0 = 0; c0 < np; c0 += 32)
-        probe_chunk<PV, kWindows>(g, g.part + pb, np, c0, 32, wtab, wcnt, log_slots, ws, t,
-                                  found_total, found_group);
+        probe_chunk<PV, kWindows>(g, g.part + pb, np, c0, 32, tb, ws, t, found_total,
+                                  found_group);
       if (PV || tg) {
         found_group = warp_sum_u64(found_group);
         if (lane == 0 && found_group)
@@ -490,10 +505,10 @@ __device__ __forceinline__ void warp_groups(const Lists &g, const int32_t *__res
       }
       __syncwarp();
       if (PV) {
-        flush_counts(wtab, wcnt, slot_of, hd, lane, 32, t);
+        flush_counts(tb, slot_of, hd, lane, 32, t);
         __syncwarp();
       }
-      empty_table(wtab, slot_of, hd, lane, 32);
+      empty_table(tb, slot_of, hd, lane, 32);
       __syncwarp();
     }
   }
@@ -502,10 +517,12 @@ __device__ __forceinline__ void warp_groups(const Lists &g, const int32_t *__res
 // Dynamic shared memory of the counting kernels: the hash table, the slot
 // counters (per-vertex mode) and the slot of every hashed entry.
 constexpr size_t table_smem(int slots, int max_len, bool pv) {
-  return (size_t)4 * slots + (pv ? (size_t)4 * counter_words(slots) : 0) + (size_t)2 * max_len;
+  return (size_t)4 * slots * (pv ? 2 : 1) + (size_t)2 * max_len;
 }
-constexpr size_t main_smem(bool pv) { return table_smem(kMainSlots, kCtaMaxRow, pv); }
-constexpr size_t big_smem(bool pv) { return table_smem(kBigSlots, kBigSlots / 2, pv); }
+template <bool PV> constexpr size_t main_smem() {
+  return table_smem(main_slots<PV>(), kCtaMaxRow, PV);
+}
+template <bool PV> constexpr size_t big_smem() { return table_smem(kBigSlots, kBigSlots / 2, PV); }
 static_assert(kMainWarps * kWarpMaxRow <= kCtaMaxRow, "warp slot maps must fit the CTA's");
 
 // Main counting kernel: CTA groups first (the heavy ones), then warp groups.
@@ -513,22 +530,25 @@ template <bool PV>
 __global__ void __launch_bounds__(kMainThreads, kMainMinBlocks)
 k_count(Lists g, const int32_t *__restrict__ warp_list, const int32_t *__restrict__ cta_list,
         Ctrl *ctrl, int64_t *t, int64_t *tg) {
+  constexpr int SLOTS = main_slots<PV>();
+  constexpr int WSLOTS = SLOTS / kMainWarps;
   extern __shared__ __align__(16) unsigned char smem[];
   int32_t *s_tab = reinterpret_cast<int32_t *>(smem);
-  uint32_t *s_cnt = reinterpret_cast<uint32_t *>(smem + 4 * kMainSlots);
-  uint16_t *s_slot =
-      reinterpret_cast<uint16_t *>(smem + 4 * kMainSlots + (PV ? 4 * counter_words(kMainSlots) : 0));
+  uint32_t *s_cnt = reinterpret_cast<uint32_t *>(smem + 4 * SLOTS);
+  uint16_t *s_slot = reinterpret_cast<uint16_t *>(smem + 4 * SLOTS * (PV ? 2 : 1));
   __shared__ WarpScratch s_ws[kMainWarps];
   __shared__ CtaShared s_sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  clear_table<PV>(s_tab, s_cnt, kMainSlots, tid, kMainThreads);
+  clear_table<PV>(s_tab, s_cnt, SLOTS, tid, kMainThreads);
   uint64_t found_total = 0;
-  cta_groups<PV, kMainThreads, kMainSlots, kWindows>(g, cta_list, ctrl->n_cta_groups,
-                                                     &ctrl->next_cta_group, s_tab, s_cnt, s_slot,
-                                                     s_ws, s_sh, t, tg, found_total);
-  warp_groups<PV>(g, warp_list, ctrl->n_warp_groups, &ctrl->next_warp_group,
-                  s_tab + warp * kWarpSlots, s_cnt + warp * counter_words(kWarpSlots),
-                  s_slot + warp * kWarpMaxRow, s_ws[warp], t, tg, found_total);
+  Table tb{s_tab, s_cnt, shared_addr(s_cnt), SLOTS};
+  cta_groups<PV, kMainThreads, SLOTS, kWindows>(g, cta_list, ctrl->n_cta_groups,
+                                                &ctrl->next_cta_group, tb, s_slot, s_ws, s_sh,
+                                                t, tg, found_total);
+  Table wtb{s_tab + warp * WSLOTS, s_cnt + warp * WSLOTS, shared_addr(s_cnt + warp * WSLOTS),
+            WSLOTS};
+  warp_groups<PV, WSLOTS>(g, warp_list, ctrl->n_warp_groups, &ctrl->next_warp_group, wtb,
+                          s_slot + warp * kWarpMaxRow, s_ws[warp], t, tg, found_total);
   found_total = warp_sum_u64(found_total);
   if (lane == 0 && found_total) atomicAdd(&ctrl->total, (unsigned long long)found_total);
 }
@@ -541,16 +561,16 @@ k_count_big(Lists g, const int32_t *__restrict__ big_list, Ctrl *ctrl, int64_t *
   extern __shared__ __align__(16) unsigned char smem[];
   int32_t *tab = reinterpret_cast<int32_t *>(smem);
   uint32_t *cnt = reinterpret_cast<uint32_t *>(smem + 4 * kBigSlots);
-  uint16_t *slot_of =
-      reinterpret_cast<uint16_t *>(smem + 4 * kBigSlots + (PV ? 4 * counter_words(kBigSlots) : 0));
+  uint16_t *slot_of = reinterpret_cast<uint16_t *>(smem + 4 * kBigSlots * (PV ? 2 : 1));
   __shared__ WarpScratch s_ws[kBigWarps];
   __shared__ CtaShared s_sh;
   const int tid = threadIdx.x, lane = tid & 31;
   clear_table<PV>(tab, cnt, kBigSlots, tid, kBigThreads);
   uint64_t found_total = 0;
+  Table tb{tab, cnt, shared_addr(cnt), kBigSlots};
   cta_groups<PV, kBigThreads, kBigSlots, kBigWindows>(g, big_list, ctrl->n_big_groups,
-                                                      &ctrl->next_big_group, tab, cnt, slot_of,
-                                                      s_ws, s_sh, t, tg, found_total);
+                                                      &ctrl->next_big_group, tb, slot_of, s_ws,
+                                                      s_sh, t, tg, found_total);
   found_total = warp_sum_u64(found_total);
   if (lane == 0 && found_total) atomicAdd(&ctrl->total, (unsigned long long)found_total);
 }
@@ -633,18 +653,18 @@ struct CountGrid {
 template <bool PV>
 cudaError_t count_grid_t(int dev, CountGrid *out) {
   cudaError_t e = cudaFuncSetAttribute(k_count<PV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)main_smem(PV));
+                                       (int)main_smem<PV>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_count_big<PV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)big_smem(PV));
+                             (int)big_smem<PV>());
   if (e != cudaSuccess) return e;
   int sms = 0, per_main = 0, per_big = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_main, k_count<PV>, kMainThreads,
-                                                    main_smem(PV));
+                                                    main_smem<PV>());
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_big, k_count_big<PV>, kBigThreads,
-                                                      big_smem(PV));
+                                                      big_smem<PV>());
   if (e != cudaSuccess) return e;
   sms = sms > 0 ? sms : 1;
   *out = CountGrid{sms * (per_main > 0 ? per_main : 1), sms * (per_big > 0 ? per_big : 1)};
@@ -688,15 +708,15 @@ cudaError_t launch_count(const int32_t *off, const int32_t *voff, const int32_t 
   const Lists g{off, voff, col4, goff, part};
   // the long lists first, on their own wide CTAs
   if (pv) {
-    k_count_big<true><<<cg.big_blocks, kBigThreads, big_smem(true), st>>>(g, big_groups, ctrl, t,
+    k_count_big<true><<<cg.big_blocks, kBigThreads, big_smem<true>(), st>>>(g, big_groups, ctrl, t,
                                                                           nullptr);
-    k_count<true><<<cg.main_blocks, kMainThreads, main_smem(true), st>>>(g, warp_groups,
+    k_count<true><<<cg.main_blocks, kMainThreads, main_smem<true>(), st>>>(g, warp_groups,
                                                                          cta_groups, ctrl, t,
                                                                          nullptr);
   } else {
-    k_count_big<false><<<cg.big_blocks, kBigThreads, big_smem(false), st>>>(g, big_groups, ctrl,
+    k_count_big<false><<<cg.big_blocks, kBigThreads, big_smem<false>(), st>>>(g, big_groups, ctrl,
                                                                             nullptr, tg);
-    k_count<false><<<cg.main_blocks, kMainThreads, main_smem(false), st>>>(g, warp_groups,
+    k_count<false><<<cg.main_blocks, kMainThreads, main_smem<false>(), st>>>(g, warp_groups,
                                                                            cta_groups, ctrl,
                                                                            nullptr, tg);
   }

@@ -607,7 +607,6 @@ void launch_offsets(const int32_t *counts, int32_t n, int32_t *off, const int32_
   const uint32_t items = (uint32_t)n + 1;
   const uint32_t grid = max(1u, (items + kScanTile - 1) / kScanTile);
   tune.warp_max_list = min(max(tune.warp_max_list, 0), kWarpMaxRow);  // warp table capacity
-  tune.warp_max_partners = min(max(tune.warp_max_partners, 0), kPartnerBatch);
   if (row_off)
     k_offsets<kScanGroups><<<grid, kScanThreads, 0, st>>>(counts, n, off, row_off, warp_list,
                                                           cta_list, big_list, tune, status,

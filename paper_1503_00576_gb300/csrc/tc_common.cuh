@@ -66,9 +66,6 @@ constexpr unsigned long long kValueMask = (1ull << 62) - 1;
 constexpr int kWarpMaxRow = 128;
 constexpr int kWarpMaxPartners = 64;
 constexpr int kCtaMaxRow = 1024;
-// Partners per batch of the counting kernels' 16-bit slot counters; a
-// group counted by one warp has at most this many partners.
-constexpr int32_t kPartnerBatch = 65535;
 
 // Runtime tuning of the counting layout (what an autotuner varies).
 struct Tuning {
