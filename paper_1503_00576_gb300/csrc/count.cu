@@ -13,9 +13,10 @@
 //    claim chunks of partners from a shared counter;
 //  * the lists N+(l) of a chunk of <= 32 partners are read as one flat
 //    sequence of aligned 16-byte words of the padded column array (each
-//    list padded with -1 to whole words, group.cu): lane p takes words p,
-//    p+32, ..., finds each word's list by a warp vote over the list ends,
-//    and loads kWindows words (16-byte loads) before it probes any;
+//    list padded with -1 to whole words, group.cu): lane p takes words 2p
+//    and 2p+1 of each 64-word window, finds each word's list by a warp vote
+//    over the list ends, and loads kWindows words (16-byte loads) before it
+//    probes any;
 //  * counts stay in registers and are reduced per warp (shuffles) into one
 //    uint64 atomic per warp at the end (the paper's reduction, fused).
 //
@@ -241,45 +242,58 @@ __device__ __forceinline__ int32_t warp_incl_scan(int32_t x) {
   return x;
 }
 
-// Word mode of probe_chunk: windows w .. w+NQ-1 of 32 words of the chunk's
-// flat sequence, lane p taking word 32 w + p of each.  The list of a word is
-// the number of lists ending at or before it: those ending at or before the
-// window's start (one vote) plus those whose last word lies in the window
-// before this lane (a bit mask OR-reduced over the lanes).  Lane r holds
-// list r's {base, end} in bn_r.  TAIL: the window reaches past total_v, and
-// the words beyond it are -1.
+// Word mode of probe_chunk: windows w .. w+NQ-1 of 64 words of the chunk's
+// flat sequence, lane p taking words 2p and 2p+1 of each (32 contiguous
+// bytes: the warp reads 1 KB per window).  The list of a word is the number
+// of lists ending at or before it: those ending at or before the window's
+// start (one vote) plus those whose last word lies in the window before
+// this one (a 64-bit mask of last words, OR-reduced over the lanes).  Lane
+// r holds list r's {base, end} in bn_r.  TAIL: the window reaches past
+// total_v, and the words beyond it are -1.
 template <bool PV, int NQ, bool TAIL>
 __device__ __forceinline__ void probe_windows(const Lists &g, int32_t w, int32_t total_v,
                                               int2 bn_r, const Table &tb, uint32_t lc_sa,
                                               uint32_t &found) {
   const int lane = threadIdx.x & 31;
   const int4 *__restrict__ col4v = reinterpret_cast<const int4 *>(g.col4);
-  const uint32_t lt = (1u << lane) - 1u;
-  int4 x[NQ];
-  int rq[NQ];
+  const uint32_t two = 2u * (uint32_t)lane;  // offset of the lane's first word
+  const uint64_t before = (1ull << two) - 1ull;
+  int4 x[NQ][2];
+  int r0[NQ], r1[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    const int32_t P = 32 * (w + q);
+    const int32_t P = 64 * (w + q);
     const int c0 = __popc(__ballot_sync(kFull, bn_r.y <= P));
-    const uint32_t b = (uint32_t)(bn_r.y - P - 1);
-    const uint32_t ends = __reduce_or_sync(kFull, b < 31u ? 1u << b : 0u);
-    const int r = c0 + __popc(ends & lt);
-    const int32_t base = __shfl_sync(kFull, bn_r.x, r & 31);
-    const int32_t p = P + lane;
+    const uint32_t o = (uint32_t)(bn_r.y - P - 1);  // offset of list r's last word
+    const uint32_t lo = __reduce_or_sync(kFull, o < 32u ? 1u << o : 0u);
+    const uint32_t hi = __reduce_or_sync(kFull, o - 32u < 31u ? 1u << (o - 32u) : 0u);
+    const uint64_t ends = ((uint64_t)hi << 32) | lo;
+    r0[q] = c0 + __popcll(ends & before);
+    r1[q] = r0[q] + (int)((ends >> two) & 1u);
+    const int32_t a0 = __shfl_sync(kFull, bn_r.x, r0[q] & 31) + P + (int32_t)two;
+    const int32_t a1 = __shfl_sync(kFull, bn_r.x, r1[q] & 31) + P + (int32_t)two + 1;
     if (TAIL) {
-      x[q] = make_int4(-1, -1, -1, -1);
-      if (p < total_v) x[q] = __ldg(col4v + (base + p));
+      x[q][0] = x[q][1] = make_int4(-1, -1, -1, -1);
+      if (P + (int32_t)two < total_v) x[q][0] = __ldg(col4v + a0);
+      if (P + (int32_t)two + 1 < total_v) x[q][1] = __ldg(col4v + a1);
     } else {
-      x[q] = __ldg(col4v + (base + p));
+      x[q][0] = __ldg(col4v + a0);
+      x[q][1] = __ldg(col4v + a1);
     }
-    rq[q] = r;
   }
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    const int32_t e[4] = {x[q].x, x[q].y, x[q].z, x[q].w};
-    const uint32_t hits = lookup<PV, 4>(e, tb);
-    found += hits;
-    if (PV) red_add_if(lc_sa + 4u * (uint32_t)rq[q], hits, hits != 0u);
+    const int32_t e0[4] = {x[q][0].x, x[q][0].y, x[q][0].z, x[q][0].w};
+    const int32_t e1[4] = {x[q][1].x, x[q][1].y, x[q][1].z, x[q][1].w};
+    const uint32_t h0 = lookup<PV, 4>(e0, tb);
+    const uint32_t h1 = lookup<PV, 4>(e1, tb);
+    found += h0 + h1;
+    if (PV) {
+      const bool same = r0[q] == r1[q];
+      const uint32_t first = same ? h0 + h1 : h0;
+      red_add_if(lc_sa + 4u * (uint32_t)r0[q], first, first != 0u);
+      red_add_if(lc_sa + 4u * (uint32_t)r1[q], h1, !same && h1 != 0u);
+    }
   }
 }
 
@@ -289,9 +303,9 @@ __device__ __forceinline__ void probe_windows(const Lists &g, int32_t w, int32_t
 // chunk by which needs fewer warp steps:
 //  * words: a position is one aligned 16-byte word of the padded column
 //    array (int4), four entries probed per load; padding entries are -1 and
-//    never match.  Lane p takes positions p, p+32, ... (coalesced loads);
-//    the list of each position comes from a warp vote over the list ends,
-//    with no per-lane cursor and no branch;
+//    never match.  Lane p takes words 2p, 2p+1 of each 64-word window
+//    (coalesced loads); the list of each word comes from a warp vote over
+//    the list ends, with no per-lane cursor and no branch;
 //  * elements: a position is one list entry (one 4-byte load); lane p takes
 //    positions p, p+32, ... with a cursor on the list holding its position.
 //    For chunks of a few short lists, where whole words would be mostly
@@ -345,12 +359,13 @@ __device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__res
   if (words) {
     // lane r holds list r's base and end (flat start of list r+1)
     const int2 bn_r = lane < k ? ws.bn[lane] : make_int2(0, INT32_MAX);
-    const int32_t full = total_v >> 5;  // windows of 32 words inside the sequence
+    const int32_t full = total_v >> 6;  // windows of 64 words inside the sequence
+    constexpr int NQ = W / 2;           // windows per step: W words per lane in flight
     int32_t w = 0;
-    for (; w + W <= full; w += W)
-      probe_windows<PV, W, false>(g, w, total_v, bn_r, tb, lc_sa, found);
+    for (; w + NQ <= full; w += NQ)
+      probe_windows<PV, NQ, false>(g, w, total_v, bn_r, tb, lc_sa, found);
     for (; w < full; ++w) probe_windows<PV, 1, false>(g, w, total_v, bn_r, tb, lc_sa, found);
-    if (total_v & 31) probe_windows<PV, 1, true>(g, w, total_v, bn_r, tb, lc_sa, found);
+    if (total_v & 63) probe_windows<PV, 1, true>(g, w, total_v, bn_r, tb, lc_sa, found);
   } else {
     int r = 0;
     long long eb = ws.eb[0];
@@ -529,7 +544,7 @@ static_assert(kMainWarps * kWarpMaxRow <= kCtaMaxRow, "warp slot maps must fit t
 template <bool PV>
 __global__ void __launch_bounds__(kMainThreads, kMainMinBlocks)
 k_count(Lists g, const int32_t *__restrict__ warp_list, const int32_t *__restrict__ cta_list,
-        Ctrl *ctrl, int64_t *t, int64_t *tg) {
+        int32_t n, Ctrl *ctrl, int64_t *t, int64_t *tg) {
   constexpr int SLOTS = main_slots<PV>();
   constexpr int WSLOTS = SLOTS / kMainWarps;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -556,7 +571,7 @@ k_count(Lists g, const int32_t *__restrict__ warp_list, const int32_t *__restric
 // Groups whose hashed list is longer than kCtaMaxRow (rare).
 template <bool PV>
 __global__ void __launch_bounds__(kBigThreads, kBigMinBlocks)
-k_count_big(Lists g, const int32_t *__restrict__ big_list, Ctrl *ctrl, int64_t *t,
+k_count_big(Lists g, const int32_t *__restrict__ big_list, int32_t n, Ctrl *ctrl, int64_t *t,
             int64_t *tg) {
   extern __shared__ __align__(16) unsigned char smem[];
   int32_t *tab = reinterpret_cast<int32_t *>(smem);
@@ -699,8 +714,8 @@ cudaError_t prepare_count_kernels() {
 
 cudaError_t launch_count(const int32_t *off, const int32_t *voff, const int32_t *col4,
                          const int32_t *goff, const int32_t *part, const int32_t *warp_groups,
-                         const int32_t *cta_groups, const int32_t *big_groups, Ctrl *ctrl,
-                         int64_t *t, int64_t *tg, cudaStream_t st) {
+                         const int32_t *cta_groups, const int32_t *big_groups, int32_t n,
+                         Ctrl *ctrl, int64_t *t, int64_t *tg, cudaStream_t st) {
   const bool pv = t != nullptr;
   CountGrid cg;
   cudaError_t e = count_grid(pv, &cg);
@@ -708,16 +723,16 @@ cudaError_t launch_count(const int32_t *off, const int32_t *voff, const int32_t 
   const Lists g{off, voff, col4, goff, part};
   // the long lists first, on their own wide CTAs
   if (pv) {
-    k_count_big<true><<<cg.big_blocks, kBigThreads, big_smem<true>(), st>>>(g, big_groups, ctrl, t,
-                                                                          nullptr);
+    k_count_big<true><<<cg.big_blocks, kBigThreads, big_smem<true>(), st>>>(g, big_groups, n, ctrl,
+                                                                          t, nullptr);
     k_count<true><<<cg.main_blocks, kMainThreads, main_smem<true>(), st>>>(g, warp_groups,
-                                                                         cta_groups, ctrl, t,
+                                                                         cta_groups, n, ctrl, t,
                                                                          nullptr);
   } else {
-    k_count_big<false><<<cg.big_blocks, kBigThreads, big_smem<false>(), st>>>(g, big_groups, ctrl,
-                                                                            nullptr, tg);
+    k_count_big<false><<<cg.big_blocks, kBigThreads, big_smem<false>(), st>>>(g, big_groups, n,
+                                                                            ctrl, nullptr, tg);
     k_count<false><<<cg.main_blocks, kMainThreads, main_smem<false>(), st>>>(g, warp_groups,
-                                                                           cta_groups, ctrl,
+                                                                           cta_groups, n, ctrl,
                                                                            nullptr, tg);
   }
   note_launch();

@@ -300,7 +300,7 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
 
   pt.start(TC_PHASE_COUNT);
   cudaError_t e = launch_count(off, voff, col4, goff, part, warp_groups, cta_groups, big_groups,
-                               ctrl, t_out ? t_rank : nullptr, t_out ? nullptr : t_rank, st);
+                               n, ctrl, t_out ? t_rank : nullptr, t_out ? nullptr : t_rank, st);
   if (e == cudaSuccess && t_out) launch_gather_counts(t_rank, rank, n, t_out, st);
   if (e == cudaSuccess && batch) {
     if (t_out) {  // per graph: (sum of t) / 3

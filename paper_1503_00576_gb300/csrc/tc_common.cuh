@@ -232,8 +232,8 @@ void launch_work(const int32_t *row, const int32_t *col, const int32_t *off, con
 // graph's count).
 cudaError_t launch_count(const int32_t *off, const int32_t *voff, const int32_t *col4,
                          const int32_t *goff, const int32_t *part, const int32_t *warp_groups,
-                         const int32_t *cta_groups, const int32_t *big_groups, Ctrl *ctrl,
-                         int64_t *t, int64_t *tg, cudaStream_t st);
+                         const int32_t *cta_groups, const int32_t *big_groups, int32_t n,
+                         Ctrl *ctrl, int64_t *t, int64_t *tg, cudaStream_t st);
 // Sets the counting kernels' attributes and occupancy for the current
 // device (done lazily otherwise; needed before capturing a CUDA graph).
 cudaError_t prepare_count_kernels();
