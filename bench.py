@@ -42,7 +42,7 @@ REF_SAMPLE_PAIRS = 6_000_000       # reference arm: per step
 KERNEL_OF_PHASE = {"canon": "k_canon", "sort1": "k_radix_pass", "degree": "k_unique_degree",
                    "rank": "k_rank_keys+k_radix_pass",
                    "orient": "k_orient", "sort2": "k_radix_pass", "offsets": "k_offsets",
-                   "groups": "k_group_count+k_offsets+k_group_fill", "count": "k_count"}
+                   "groups": "k_group_keys+k_radix_pass+k_offsets", "count": "k_count"}
 
 
 def parse_args():

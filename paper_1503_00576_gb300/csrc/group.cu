@@ -9,13 +9,13 @@
 //
 //   h = v if |N+(v)| > |N+(u)| else u,     l = the other endpoint,
 //
-// and the edges are grouped by h with a counting sort (count per h,
-// exclusive scan, scatter).  A group then hashes N+(h) once and streams
-// N+(l) for each of its partners l.  On the R-MAT graphs of the benchmarks
-// this cuts the probes by a factor of 2.7 against always streaming N+(v).
-//
-// Both kernels are edge-parallel over the unzipped edge array (row[], col[])
-// written by the last radix pass; equal h within a warp share one atomic.
+// and the edges are grouped by h: k_group_keys writes the key h << b | l of
+// every edge, and a stable LSD radix sort over the h bits (the passes of
+// preprocess.cu) leaves the partners l of each group together, its last
+// pass counting the group sizes.  A group then hashes N+(h) once and
+// streams N+(l) for each of its partners l.  On the R-MAT graphs of the
+// benchmarks this cuts the probes by a factor of 2.7 against always
+// streaming N+(v).
 #include "tc_common.cuh"
 
 namespace tc {
@@ -25,10 +25,8 @@ constexpr int kGroupThreads = 256;
 
 // heavy_ratio_pct = 100: the longer list is always the one hashed; larger
 // values keep an edge at its owner unless v's list is that much longer.
-__device__ __forceinline__ void split_edge(const int32_t *__restrict__ off, int32_t u, int32_t v,
+__device__ __forceinline__ void split_edge(int32_t u, int32_t v, int64_t du, int64_t dv,
                                            int32_t heavy_ratio_pct, int32_t &h, int32_t &l) {
-  const int64_t du = __ldg(off + u + 1) - __ldg(off + u);
-  const int64_t dv = __ldg(off + v + 1) - __ldg(off + v);
   if (dv * 100 > du * heavy_ratio_pct) {
     h = v;
     l = u;
@@ -38,80 +36,67 @@ __device__ __forceinline__ void split_edge(const int32_t *__restrict__ off, int3
   }
 }
 
-// Group sizes, and the copy of every forward list into the padded column
-// array: list u occupies words [voff[u], voff[u+1]) of col4, its entries in
-// the order of col, and the rest of its last word holds -1 (an id no hash
-// slot ever matches), so the counting kernel can stream lists as whole
-// aligned 16-byte words.
+// One pass over the unzipped edge array (row[], col[]) in owner order:
+// the group key of every edge with the digit histograms of its h field, and
+// the copy of every forward list into the padded column array: list u
+// occupies words [voff[u], voff[u+1]) of col4, its entries in the order of
+// col, and the rest of its last word holds -1 (an id no hash slot ever
+// matches), so the counting kernel can stream lists as whole aligned
+// 16-byte words.
 __global__ void __launch_bounds__(kGroupThreads)
-k_group_count(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
-              const int32_t *__restrict__ off, const int32_t *__restrict__ voff,
-              int32_t heavy_ratio_pct, const Ctrl *__restrict__ ctrl, int32_t *gcnt,
-              int32_t *__restrict__ col4) {
+k_group_keys(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
+             const int32_t *__restrict__ off, const int32_t *__restrict__ voff, int b,
+             int passes, int32_t heavy_ratio_pct, const Ctrl *__restrict__ ctrl,
+             uint64_t *__restrict__ gkeys, uint32_t *__restrict__ hist,
+             int32_t *__restrict__ col4) {
+  __shared__ uint32_t s_hist[kMaxGroupPasses * 256];
+  for (int i = threadIdx.x; i < passes * 256; i += kGroupThreads) s_hist[i] = 0;
+  __syncthreads();
   const uint32_t m = ctrl->m;
   const uint32_t stride = gridDim.x * kGroupThreads;
   for (uint32_t e = blockIdx.x * kGroupThreads + threadIdx.x; e < m; e += stride) {
     const int32_t u = __ldg(row + e), v = __ldg(col + e);
-    int32_t h, l;
-    split_edge(off, u, v, heavy_ratio_pct, h, l);
     const int32_t ub = __ldg(off + u), ue = __ldg(off + u + 1);
+    const int32_t vd = __ldg(off + v + 1) - __ldg(off + v);
+    int32_t h, l;
+    split_edge(u, v, ue - ub, vd, heavy_ratio_pct, h, l);
+    gkeys[e] = ((uint64_t)(uint32_t)h << b) | (uint32_t)l;
+    for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p * 256 + ((h >> (8 * p)) & 255)], 1u);
     int32_t *dst = col4 + 4 * (size_t)__ldg(voff + u);
     dst[(int32_t)e - ub] = v;
     if ((int32_t)e == ue - 1)  // the list's last entry pads its word
       for (int32_t j = ue - ub; j & 3; ++j) dst[j] = -1;
-    const uint32_t active = __activemask();
-    const uint32_t peers = __match_any_sync(active, h);
-    const int lane = threadIdx.x & 31;
-    if (lane == __ffs(peers) - 1) atomicAdd(&gcnt[h], __popc(peers));
   }
-}
-
-// gcnt[h] holds the group sizes on entry and is counted down to 0.
-__global__ void __launch_bounds__(kGroupThreads)
-k_group_fill(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
-             const int32_t *__restrict__ off, int32_t heavy_ratio_pct,
-             const Ctrl *__restrict__ ctrl, const int32_t *__restrict__ goff, int32_t *gcnt,
-             int32_t *__restrict__ part) {
-  const uint32_t m = ctrl->m;
-  const uint32_t stride = gridDim.x * kGroupThreads;
-  for (uint32_t e = blockIdx.x * kGroupThreads + threadIdx.x; e < m; e += stride) {
-    int32_t h, l;
-    split_edge(off, __ldg(row + e), __ldg(col + e), heavy_ratio_pct, h, l);
-    const uint32_t active = __activemask();
-    const uint32_t peers = __match_any_sync(active, h);
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
-    int32_t top = 0;
-    if (lane == leader) top = atomicSub(&gcnt[h], __popc(peers));
-    top = __shfl_sync(peers, top, leader);
-    const int rank = __popc(peers & ((1u << lane) - 1u));
-    part[__ldg(goff + h) + top - 1 - rank] = l;
-  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * 256; i += kGroupThreads)
+    if (s_hist[i]) atomicAdd(&hist[i], s_hist[i]);
 }
 
 // Work of the counting phase, for instrumentation only (never on the path
-// of a count): per forward edge, the list streamed through the hash set,
-// d+(l) lookups, and the merge work d+(u) + d+(v) of Sec. II-B; per partner
-// group, the list hashed once, d+(h) inserts; the largest d+.
+// of a count): per forward edge (h, l) of group h, the list streamed
+// through the hash set, d+(l) lookups, and the merge work d+(h) + d+(l) of
+// Sec. II-B; per non-empty group, the list hashed once, d+(h) inserts; the
+// largest d+.  One warp per vertex h.
 __global__ void __launch_bounds__(kGroupThreads)
-k_work(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
-       const int32_t *__restrict__ off, const int32_t *__restrict__ goff, int32_t n,
-       int32_t heavy_ratio_pct, Ctrl *ctrl) {
-  const uint32_t m = ctrl->m;
-  const uint32_t stride = gridDim.x * kGroupThreads;
+k_work(const int32_t *__restrict__ off, const int32_t *__restrict__ goff,
+       const int32_t *__restrict__ part, int32_t n, Ctrl *ctrl) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * (kGroupThreads / 32);
   unsigned long long lookups = 0, inserts = 0, merge = 0, dmax = 0;
-  for (uint32_t e = blockIdx.x * kGroupThreads + threadIdx.x; e < m; e += stride) {
-    const int32_t u = __ldg(row + e), v = __ldg(col + e);
-    int32_t h, l;
-    split_edge(off, u, v, heavy_ratio_pct, h, l);
-    lookups += (unsigned long long)(__ldg(off + l + 1) - __ldg(off + l));
-    merge += (unsigned long long)(__ldg(off + u + 1) - __ldg(off + u)) +
-             (unsigned long long)(__ldg(off + v + 1) - __ldg(off + v));
-  }
-  for (uint32_t v = blockIdx.x * kGroupThreads + threadIdx.x; v < (uint32_t)n; v += stride) {
-    const unsigned long long d = (unsigned long long)(__ldg(off + v + 1) - __ldg(off + v));
-    if (__ldg(goff + v + 1) > __ldg(goff + v)) inserts += d;
-    dmax = d > dmax ? d : dmax;
+  for (uint32_t h = (blockIdx.x * kGroupThreads + threadIdx.x) >> 5; h < (uint32_t)n;
+       h += warps) {
+    const unsigned long long dh = (unsigned long long)(__ldg(off + h + 1) - __ldg(off + h));
+    const int32_t pb = __ldg(goff + h), pe = __ldg(goff + h + 1);
+    if (lane == 0) {
+      if (pe > pb) inserts += dh;
+      dmax = dh > dmax ? dh : dmax;
+    }
+    for (int32_t i = pb + lane; i < pe; i += 32) {
+      const int32_t l = __ldg(part + i);
+      const unsigned long long dl = (unsigned long long)(__ldg(off + l + 1) - __ldg(off + l));
+      lookups += dl;
+      merge += dh + dl;
+    }
   }
   for (int o = 16; o; o >>= 1) {
     lookups += __shfl_xor_sync(0xffffffffu, lookups, o);
@@ -120,7 +105,7 @@ k_work(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
     const unsigned long long x = __shfl_xor_sync(0xffffffffu, dmax, o);
     dmax = x > dmax ? x : dmax;
   }
-  if ((threadIdx.x & 31) == 0) {
+  if (lane == 0) {
     atomicAdd(&ctrl->work[0], lookups);
     atomicAdd(&ctrl->work[1], inserts);
     atomicAdd(&ctrl->work[2], merge);
@@ -138,28 +123,20 @@ uint32_t group_grid(uint32_t m_bound) {
 
 }  // namespace
 
-void launch_group_count(const int32_t *row, const int32_t *col, const int32_t *off,
-                        const int32_t *voff, uint32_t m_bound, int32_t heavy_ratio_pct,
-                        Ctrl *ctrl, int32_t *gcnt, int32_t *col4, cudaStream_t st) {
-  k_group_count<<<group_grid(m_bound), kGroupThreads, 0, st>>>(row, col, off, voff,
-                                                               heavy_ratio_pct, ctrl, gcnt,
-                                                               col4);
+void launch_group_keys(const int32_t *row, const int32_t *col, const int32_t *off,
+                       const int32_t *voff, uint32_t m_bound, int b, int passes,
+                       int32_t heavy_ratio_pct, Ctrl *ctrl, uint64_t *gkeys, uint32_t *hist,
+                       int32_t *col4, cudaStream_t st) {
+  k_group_keys<<<group_grid(m_bound), kGroupThreads, 0, st>>>(row, col, off, voff, b, passes,
+                                                              heavy_ratio_pct, ctrl, gkeys, hist,
+                                                              col4);
   note_launch();
 }
 
-void launch_group_fill(const int32_t *row, const int32_t *col, const int32_t *off,
-                       uint32_t m_bound, int32_t heavy_ratio_pct, Ctrl *ctrl,
-                       const int32_t *goff, int32_t *gcnt, int32_t *part, cudaStream_t st) {
-  k_group_fill<<<group_grid(m_bound), kGroupThreads, 0, st>>>(row, col, off, heavy_ratio_pct,
-                                                              ctrl, goff, gcnt, part);
-  note_launch();
-}
-
-void launch_work(const int32_t *row, const int32_t *col, const int32_t *off, const int32_t *goff,
-                 uint32_t m_bound, int32_t n, int32_t heavy_ratio_pct, Ctrl *ctrl,
-                 cudaStream_t st) {
-  k_work<<<group_grid(max(m_bound, (uint32_t)n)), kGroupThreads, 0, st>>>(row, col, off, goff, n,
-                                                                          heavy_ratio_pct, ctrl);
+void launch_work(const int32_t *off, const int32_t *goff, const int32_t *part, int32_t n,
+                 Ctrl *ctrl, cudaStream_t st) {
+  const uint32_t lanes = n > (1 << 28) ? (1u << 30) : (uint32_t)n * 4u;  // grid is capped anyway
+  k_work<<<group_grid(lanes), kGroupThreads, 0, st>>>(off, goff, part, n, ctrl);
   note_launch();
 }
 

@@ -328,7 +328,7 @@ k_radix_pass(const uint64_t *__restrict__ in, void *__restrict__ out, uint32_t n
     if (MODE == kOutColRow) {
       const uint32_t owner = (uint32_t)(key >> owner_shift);
       ((uint32_t *)out)[pos] = (uint32_t)key & col_mask;
-      row_out[pos] = owner;
+      if (row_out) row_out[pos] = owner;
       // the staged tile is in owner order: consecutive lanes share owners,
       // and one atomic per run gives the out-degrees (the node array's counts)
       const uint32_t peers = __match_any_sync(__activemask(), owner);

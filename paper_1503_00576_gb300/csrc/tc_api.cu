@@ -160,6 +160,7 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   // radix passes: undirected keys (2b bits), rank keys (degree bits < 2^b),
   // oriented keys (owner bits)
   const int passes1 = (2 * b + 7) / 8, passes_r = (b + 7) / 8, passes2 = (b + 7) / 8;
+  const int passes3 = (b + 7) / 8;  // group keys: the h field
   Ctrl *ctrl = reinterpret_cast<Ctrl *>(ws + L.ctrl);
   uint32_t *hist = reinterpret_cast<uint32_t *>(ws + L.hist);
   auto *st_sort = reinterpret_cast<unsigned long long *>(ws + L.st_sort);
@@ -197,7 +198,7 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
 
   // zero the control block, histograms and the look-back status words in use
   TC_CUDA(cudaMemsetAsync(ws, 0, L.st_sort + sizeof(unsigned long long) * words *
-                                                  (size_t)(passes1 + passes_r + passes2), st),
+                                                  (size_t)radix_passes(b), st),
           "memset control");
   TC_CUDA(cudaMemsetAsync(ws + L.st_orient, 0, L.keys_a - L.st_orient, st), "memset status");
   TC_CUDA(cudaMemsetAsync(deg, 0, sizeof(int32_t) * (size_t)n, st), "memset deg");
@@ -276,7 +277,6 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   }
   const int32_t *col = reinterpret_cast<const int32_t *>(out);
   const int32_t *row = reinterpret_cast<const int32_t *>(out) + m;
-  int32_t *part = reinterpret_cast<int32_t *>(in);  // the last pass's input is free now
   pt.stop(TC_PHASE_SORT2);
 
   pt.start(TC_PHASE_OFFSETS);
@@ -286,17 +286,35 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   pt.stop(TC_PHASE_OFFSETS);
 
   // partner groups: each forward edge goes to the endpoint with the longer
-  // forward list; gcnt reuses the out-degree array.  The same pass copies
-  // the lists into the padded column array col4.
+  // forward list.  Group keys go to `in` (sort 2's input, free now) and the
+  // same pass copies the lists into the padded column array col4; a radix
+  // sort over the group bits then gathers every group's partners, its last
+  // pass counting the group sizes into gcnt (the out-degree array's space).
   pt.start(TC_PHASE_GROUPS);
+  launch_group_keys(row, col, off, voff, m, b, passes3, tune.heavy_ratio_pct, ctrl, in,
+                    hist + 256 * kGroupSlot, col4, st);
   int32_t *gcnt = outdeg;
   TC_CUDA(cudaMemsetAsync(gcnt, 0, sizeof(int32_t) * (size_t)n, st), "memset groups");
-  launch_group_count(row, col, off, voff, m, tune.heavy_ratio_pct, ctrl, gcnt, col4, st);
+  uint64_t *gin = in, *gout = out;  // row and col are dead after the group keys
+  for (int p = 0; p < passes3; ++p) {
+    unsigned long long *status;
+    uint32_t *ticket;
+    next_pass(&status, &ticket);
+    const bool last = p == passes3 - 1;
+    launch_radix_pass(gin, gout, last ? kOutColRow : kOutKeys, nullptr, last ? gcnt : nullptr, m,
+                      &ctrl->m, b + 8 * p, id_mask, b, hist + 256 * (kGroupSlot + p), status,
+                      ticket, ctrl, st);
+    if (!last) {
+      uint64_t *x = gin;
+      gin = gout;
+      gout = x;
+    }
+  }
+  const int32_t *part = reinterpret_cast<const int32_t *>(gout);
   launch_offsets(gcnt, n, goff, off, warp_groups, cta_groups, big_groups, tune, st_scan2,
                  &ctrl->tile_ticket[kTicketGroupScan], ctrl, st);
-  launch_group_fill(row, col, off, m, tune.heavy_ratio_pct, ctrl, goff, gcnt, part, st);
   pt.stop(TC_PHASE_GROUPS);
-  if (work_stats) launch_work(row, col, off, goff, m, n, tune.heavy_ratio_pct, ctrl, st);
+  if (work_stats) launch_work(off, goff, part, n, ctrl, st);
 
   pt.start(TC_PHASE_COUNT);
   cudaError_t e = launch_count(off, voff, col4, goff, part, warp_groups, cta_groups, big_groups,

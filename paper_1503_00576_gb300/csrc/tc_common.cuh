@@ -20,10 +20,12 @@ constexpr uint32_t kSpinLimit = 1u << 24;
 constexpr int kMaxSort1Passes = 8;  // 2 * 31 id bits / 8-bit digits
 constexpr int kMaxSort2Passes = 4;  // 31 owner bits / 8-bit digits
 constexpr int kMaxRankPasses = 4;   // 31 degree bits / 8-bit digits
-constexpr int kMaxPasses = kMaxSort1Passes + kMaxSort2Passes + kMaxRankPasses;
-// First histogram / status slot of each sort.
+constexpr int kMaxGroupPasses = 4;  // 31 group bits / 8-bit digits
+constexpr int kMaxPasses = kMaxSort1Passes + kMaxSort2Passes + kMaxRankPasses + kMaxGroupPasses;
+// First histogram slot of each sort.
 constexpr int kSort2Slot = kMaxSort1Passes;
 constexpr int kRankSlot = kMaxSort1Passes + kMaxSort2Passes;
+constexpr int kGroupSlot = kMaxSort1Passes + kMaxSort2Passes + kMaxRankPasses;
 
 // Control block: zeroed at the start of every call.
 struct Ctrl {
@@ -123,8 +125,9 @@ inline int id_bits(int32_t n) {
 }
 
 // Radix passes of one run over ids of b bits: the undirected keys (2b
-// bits), the rank keys (degree < 2^b) and the oriented keys (owner bits).
-inline int radix_passes(int b) { return (2 * b + 7) / 8 + 2 * ((b + 7) / 8); }
+// bits), the rank keys (degree < 2^b), the oriented keys (owner bits) and
+// the group keys (group bits).
+inline int radix_passes(int b) { return (2 * b + 7) / 8 + 3 * ((b + 7) / 8); }
 
 inline Layout make_layout(int64_t m_in, int32_t n) {
   Layout L{};
@@ -214,18 +217,19 @@ void launch_word_offsets(const int32_t *counts, int32_t n, int32_t *voff,
                          unsigned long long *status, uint32_t *ticket, Ctrl *ctrl,
                          cudaStream_t st);
 // ---- launchers (group.cu) ----
-// Also copies every forward list into the padded column array col4 (list v
-// starts at word voff[v]; the rest of its last word is -1).
-void launch_group_count(const int32_t *row, const int32_t *col, const int32_t *off,
-                        const int32_t *voff, uint32_t m_bound, int32_t heavy_ratio_pct,
-                        Ctrl *ctrl, int32_t *gcnt, int32_t *col4, cudaStream_t st);
-void launch_group_fill(const int32_t *row, const int32_t *col, const int32_t *off,
-                       uint32_t m_bound, int32_t heavy_ratio_pct, Ctrl *ctrl,
-                       const int32_t *goff, int32_t *gcnt, int32_t *part, cudaStream_t st);
-// Instrumentation: adds the counting phase's work into ctrl->work.
-void launch_work(const int32_t *row, const int32_t *col, const int32_t *off, const int32_t *goff,
-                 uint32_t m_bound, int32_t n, int32_t heavy_ratio_pct, Ctrl *ctrl,
-                 cudaStream_t st);
+// Group keys h << b | l of every forward edge (h: the endpoint with the
+// longer forward list, l: the other one), with the digit histograms of the
+// h field for the group sort; also copies every forward list into the
+// padded column array col4 (list v starts at word voff[v]; the rest of its
+// last word is -1).
+void launch_group_keys(const int32_t *row, const int32_t *col, const int32_t *off,
+                       const int32_t *voff, uint32_t m_bound, int b, int passes,
+                       int32_t heavy_ratio_pct, Ctrl *ctrl, uint64_t *gkeys, uint32_t *hist,
+                       int32_t *col4, cudaStream_t st);
+// Instrumentation: adds the counting phase's work into ctrl->work (from the
+// partner groups and the node array).
+void launch_work(const int32_t *off, const int32_t *goff, const int32_t *part, int32_t n,
+                 Ctrl *ctrl, cudaStream_t st);
 // ---- launchers (count.cu) ----
 // t != nullptr: per-vertex counts (rank space).  Otherwise, if tg is not
 // nullptr, tg[h] += triangles found in group h (their sum per graph is the
