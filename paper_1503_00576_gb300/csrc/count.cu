@@ -38,7 +38,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kGroupChunk = 8;  // warp groups per atomic
 constexpr int kWindows = 4;     // words per lane loaded before probing
-constexpr int kBigWindows = 2;  // ... in the long-list kernel (40 registers)
+constexpr int kBigWindows = 4;  // ... in the long-list kernel
 
 // Main kernel: 256-thread CTAs; one table per CTA for CTA groups (lists of
 // up to kCtaMaxRow entries), carved into one table per warp for warp
