@@ -257,7 +257,7 @@ tc_status tc_count_work(const int32_t *src, const int32_t *dst, int64_t m, int32
  *   total_out  HOST uint64, receives T
  * Returns TC_ERR_OVERFLOW, with a message stating the bytes needed, when
  * tc_workspace_bytes(m, n) exceeds TC_NOALLOC_SCRATCH_BYTES (about
- * 25 m + 60 n bytes: up to about 1.2 million pairs with n = 2^16).
+ * 27 m + 88 n bytes: up to about 1.1 million pairs with n = 2^16).
  * Synchronises.
  *
  * The first call on a device looks up the array's device address on that

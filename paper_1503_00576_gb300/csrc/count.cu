@@ -12,11 +12,11 @@
 //    by one warp when the group is small, else by a whole CTA whose warps
 //    claim chunks of partners from a shared counter;
 //  * the lists N+(l) of a chunk of <= 32 partners are read as one flat
-//    sequence of aligned 16-byte words of the padded column array (each
-//    list padded with -1 to whole words, group.cu): lane p takes words 2p
-//    and 2p+1 of each 64-word window, finds each word's list by a warp vote
-//    over the list ends, and loads kWindows words (16-byte loads) before it
-//    probes any;
+//    sequence of aligned 32-byte blocks of the padded column array (each
+//    list padded with -1 to whole blocks, group.cu): lane p takes block p of
+//    each window of 32 blocks (one 32-byte load; the warp reads 1 KB),
+//    finds the block's list by a warp vote over the list ends, and loads
+//    kWindows / 2 blocks before it probes any;
 //  * counts stay in registers and are reduced per warp (shuffles) into one
 //    uint64 atomic per warp at the end (the paper's reduction, fused).
 //
@@ -87,8 +87,8 @@ __device__ __forceinline__ uint32_t table_slots(int32_t len, uint32_t capacity) 
 // Read-only view of the forward lists and partner groups.
 struct Lists {
   const int32_t *__restrict__ off;   // node array (rank space): list lengths
-  const int32_t *__restrict__ voff;  // node array of col4, in 16-byte words
-  const int32_t *__restrict__ col4;  // forward lists, each padded with -1 to whole words
+  const int32_t *__restrict__ voff;  // node array of col4, in 16-byte words (even)
+  const int32_t *__restrict__ col4;  // forward lists, each padded with -1 to whole 32-byte blocks
   const int32_t *__restrict__ goff;  // partner-group offsets
   const int32_t *__restrict__ part;  // partners
 };
@@ -242,58 +242,51 @@ __device__ __forceinline__ int32_t warp_incl_scan(int32_t x) {
   return x;
 }
 
-// Word mode of probe_chunk: windows w .. w+NQ-1 of 64 words of the chunk's
-// flat sequence, lane p taking words 2p and 2p+1 of each (32 contiguous
-// bytes: the warp reads 1 KB per window).  The list of a word is the number
-// of lists ending at or before it: those ending at or before the window's
-// start (one vote) plus those whose last word lies in the window before
-// this one (a 64-bit mask of last words, OR-reduced over the lanes).  Lane
-// r holds list r's {base, end} in bn_r.  TAIL: the window reaches past
-// total_v, and the words beyond it are -1.
+// One 32-byte block (two words) of col4 at 16-byte word a (even).
+__device__ __forceinline__ void ld_block(const int32_t *col4, int32_t a, int32_t (&x)[8]) {
+  asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]), "=r"(x[4]), "=r"(x[5]), "=r"(x[6]),
+        "=r"(x[7])
+      : "l"(col4 + 4 * (size_t)a));
+}
+
+// Word mode of probe_chunk: windows w .. w+NQ-1 of 32 blocks (64 words) of
+// the chunk's flat sequence, lane p taking block p of each.  Lists occupy
+// whole blocks, so a block lies in one list: the number of lists ending at
+// or before it, i.e. those ending at or before the window (one vote) plus
+// those whose last block lies in the window before this lane's (a bit mask
+// OR-reduced over the lanes).  Lane r holds list r's {base, end} in bn_r.
+// TAIL: the window reaches past total_v, and the blocks beyond it are -1.
 template <bool PV, int NQ, bool TAIL>
 __device__ __forceinline__ void probe_windows(const Lists &g, int32_t w, int32_t total_v,
                                               int2 bn_r, const Table &tb, uint32_t lc_sa,
                                               uint32_t &found) {
   const int lane = threadIdx.x & 31;
-  const int4 *__restrict__ col4v = reinterpret_cast<const int4 *>(g.col4);
-  const uint32_t two = 2u * (uint32_t)lane;  // offset of the lane's first word
-  const uint64_t before = (1ull << two) - 1ull;
-  int4 x[NQ][2];
-  int r0[NQ], r1[NQ];
+  const uint32_t lt = (1u << lane) - 1u;
+  int32_t x[NQ][8];
+  int rq[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
     const int32_t P = 64 * (w + q);
     const int c0 = __popc(__ballot_sync(kFull, bn_r.y <= P));
-    const uint32_t o = (uint32_t)(bn_r.y - P - 1);  // offset of list r's last word
-    const uint32_t lo = __reduce_or_sync(kFull, o < 32u ? 1u << o : 0u);
-    const uint32_t hi = __reduce_or_sync(kFull, o - 32u < 31u ? 1u << (o - 32u) : 0u);
-    const uint64_t ends = ((uint64_t)hi << 32) | lo;
-    r0[q] = c0 + __popcll(ends & before);
-    r1[q] = r0[q] + (int)((ends >> two) & 1u);
-    const int32_t a0 = __shfl_sync(kFull, bn_r.x, r0[q] & 31) + P + (int32_t)two;
-    const int32_t a1 = __shfl_sync(kFull, bn_r.x, r1[q] & 31) + P + (int32_t)two + 1;
+    const uint32_t o = (uint32_t)(bn_r.y - P - 2) >> 1;  // list r's last block in the window
+    const uint32_t ends = __reduce_or_sync(kFull, o < 31u ? 1u << o : 0u);
+    const int r = c0 + __popc(ends & lt);
+    const int32_t a = __shfl_sync(kFull, bn_r.x, r & 31) + P + 2 * lane;
     if (TAIL) {
-      x[q][0] = x[q][1] = make_int4(-1, -1, -1, -1);
-      if (P + (int32_t)two < total_v) x[q][0] = __ldg(col4v + a0);
-      if (P + (int32_t)two + 1 < total_v) x[q][1] = __ldg(col4v + a1);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) x[q][i] = -1;
+      if (P + 2 * lane < total_v) ld_block(g.col4, a, x[q]);
     } else {
-      x[q][0] = __ldg(col4v + a0);
-      x[q][1] = __ldg(col4v + a1);
+      ld_block(g.col4, a, x[q]);
     }
+    rq[q] = r;
   }
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    const int32_t e0[4] = {x[q][0].x, x[q][0].y, x[q][0].z, x[q][0].w};
-    const int32_t e1[4] = {x[q][1].x, x[q][1].y, x[q][1].z, x[q][1].w};
-    const uint32_t h0 = lookup<PV, 4>(e0, tb);
-    const uint32_t h1 = lookup<PV, 4>(e1, tb);
-    found += h0 + h1;
-    if (PV) {
-      const bool same = r0[q] == r1[q];
-      const uint32_t first = same ? h0 + h1 : h0;
-      red_add_if(lc_sa + 4u * (uint32_t)r0[q], first, first != 0u);
-      red_add_if(lc_sa + 4u * (uint32_t)r1[q], h1, !same && h1 != 0u);
-    }
+    const uint32_t hits = lookup<PV, 8>(x[q], tb);
+    found += hits;
+    if (PV) red_add_if(lc_sa + 4u * (uint32_t)rq[q], hits, hits != 0u);
   }
 }
 
@@ -301,11 +294,11 @@ __device__ __forceinline__ void probe_windows(const Lists &g, int32_t w, int32_t
 // through the hash set of the group's list.  The chunk's non-empty lists
 // are concatenated into one flat sequence.  Two granularities, chosen per
 // chunk by which needs fewer warp steps:
-//  * words: a position is one aligned 16-byte word of the padded column
-//    array (int4), four entries probed per load; padding entries are -1 and
-//    never match.  Lane p takes words 2p, 2p+1 of each 64-word window
-//    (coalesced loads); the list of each word comes from a warp vote over
-//    the list ends, with no per-lane cursor and no branch;
+//  * blocks: a position is one aligned 32-byte block of the padded column
+//    array, eight entries probed per load; padding entries are -1 and never
+//    match.  Lane p takes block p of each 32-block window (coalesced
+//    loads); the list of each block comes from a warp vote over the list
+//    ends, with no per-lane cursor and no branch;
 //  * elements: a position is one list entry (one 4-byte load); lane p takes
 //    positions p, p+32, ... with a cursor on the list holding its position.
 //    For chunks of a few short lists, where whole words would be mostly
@@ -330,13 +323,13 @@ __device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__res
   if (nonempty == 0) return;
   const int k = __popc(nonempty);
   const int rank = __popc(nonempty & ((1u << lane) - 1u));
-  const int32_t nv = (dl + 3) >> 2;
+  const int32_t nv = ((dl + 7) >> 3) << 1;  // 16-byte words: whole 32-byte blocks
   const int32_t incl_e = warp_incl_scan(dl);
   const int32_t incl_v = warp_incl_scan(nv);
   const int32_t total_e = __shfl_sync(kFull, incl_e, 31);
   const int32_t total_v = __shfl_sync(kFull, incl_v, 31);
-  // a word step probes four entries, an element step one: cost ~3:1
-  const bool words = 3 * ((total_v + 31) >> 5) < ((total_e + 31) >> 5);
+  // a block step probes eight entries, an element step one: cost ~5:1
+  const bool words = 5 * ((total_v + 63) >> 6) < ((total_e + 31) >> 5);
   // list r+1 starts where list r ends (empty lists add nothing to the scans)
   const bool last = rank == k - 1;
   if (dl > 0) {

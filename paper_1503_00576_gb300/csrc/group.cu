@@ -39,10 +39,10 @@ __device__ __forceinline__ void split_edge(int32_t u, int32_t v, int64_t du, int
 // One pass over the unzipped edge array (row[], col[]) in owner order:
 // the group key of every edge with the digit histograms of its h field, and
 // the copy of every forward list into the padded column array: list u
-// occupies words [voff[u], voff[u+1]) of col4, its entries in the order of
-// col, and the rest of its last word holds -1 (an id no hash slot ever
-// matches), so the counting kernel can stream lists as whole aligned
-// 16-byte words.
+// occupies 16-byte words [voff[u], voff[u+1]) of col4 (an even number: whole
+// 32-byte blocks), its entries in the order of col, and the rest of its last
+// block holds -1 (an id no hash slot ever matches), so the counting kernel
+// can stream lists as whole aligned 32-byte blocks.
 __global__ void __launch_bounds__(kGroupThreads)
 k_group_keys(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
              const int32_t *__restrict__ off, const int32_t *__restrict__ voff, int b,
@@ -65,7 +65,7 @@ k_group_keys(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
     int32_t *dst = col4 + 4 * (size_t)__ldg(voff + u);
     dst[(int32_t)e - ub] = v;
     if ((int32_t)e == ue - 1)  // the list's last entry pads its word
-      for (int32_t j = ue - ub; j & 3; ++j) dst[j] = -1;
+      for (int32_t j = ue - ub; j & 7; ++j) dst[j] = -1;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < passes * 256; i += kGroupThreads)

@@ -456,7 +456,7 @@ k_orient(const uint64_t *__restrict__ keys, int b,
 // ---------------------------------------------------------------------------
 // offsets: exclusive scan of per-vertex counts.  Used for the node array
 // (counts = out-degrees), for the node array of the padded column array
-// (counts = out-degrees rounded up to whole 16-byte words, in words) and for
+// (counts = out-degrees rounded up to whole 32-byte blocks, in 16-byte words) and for
 // the partner groups of the counting phase (counts = partners per group),
 // where it also bins the groups that can hold a triangle (>= 1 partner,
 // >= 2 entries in the hashed list) by the length of the hashed list: one
@@ -487,7 +487,7 @@ k_offsets(const int32_t *__restrict__ counts, int32_t n, int32_t *__restrict__ o
   for (int i = 0; i < IPT; ++i) {
     const uint32_t v = first + i;
     d[i] = v < (uint32_t)n ? __ldg(counts + v) : 0;
-    if (KIND == kScanWords) d[i] = (d[i] + 3) >> 2;
+    if (KIND == kScanWords) d[i] = ((d[i] + 7) >> 3) << 1;
     sum += (uint32_t)d[i];
   }
   uint32_t tile_sum;

@@ -130,10 +130,19 @@ Ctrl *host_ctrl() {
   return h;
 }
 
+// The padded column array holds at most m + 7 min(n, m) entries, indexed
+// by int32 16-byte words.
+bool padded_fits(int64_t m, int64_t n) {
+  return m + 7 * (n < m ? n : m) < ((int64_t)1 << 33);
+}
+
 tc_status check_args(const int32_t *src, const int32_t *dst, int64_t m, int32_t n) {
   if (m < 0 || n < 0) return set_status(TC_ERR_INVALID_ARG, "m=%lld n=%d", (long long)m, n);
   if (m > (int64_t)INT32_MAX)
     return set_status(TC_ERR_OVERFLOW, "m=%lld exceeds 2^31-1 pairs", (long long)m);
+  if (!padded_fits(m, n))
+    return set_status(TC_ERR_OVERFLOW, "m=%lld, n=%d: padded lists exceed 2^31 16-byte words",
+                      (long long)m, n);
   if (m > 0 && (!src || !dst)) return set_status(TC_ERR_INVALID_ARG, "src/dst is NULL");
   return TC_OK;
 }
@@ -813,6 +822,8 @@ tc_status tc_engine_create(int64_t max_pairs, int32_t max_vertices, int32_t max_
   if (max_pairs < 1 || max_vertices < 1 || max_graphs < 1)
     return set_status(TC_ERR_INVALID_ARG, "capacities must be positive");
   if (max_pairs > (int64_t)INT32_MAX) return set_status(TC_ERR_OVERFLOW, "max_pairs > 2^31-1");
+  if (!padded_fits(max_pairs, max_vertices))
+    return set_status(TC_ERR_OVERFLOW, "padded lists of the capacities exceed 2^31 words");
   tc_engine *e = new tc_engine;
   e->max_pairs = max_pairs;
   e->max_vertices = max_vertices;

@@ -168,9 +168,9 @@ inline Layout make_layout(int64_t m_in, int32_t n) {
   L.vkeys_a = take(sizeof(uint64_t) * nv);
   L.vkeys_b = take(sizeof(uint64_t) * nv);
   L.t_rank = take(sizeof(int64_t) * nv);
-  // forward lists padded to whole 16-byte words: at most m + 3 min(n, m)
-  // elements, since each non-empty list adds at most 3
-  L.col4 = take(sizeof(int32_t) * (m + 3 * (nv < m ? nv : m)));
+  // forward lists padded to whole 32-byte blocks: at most m + 7 min(n, m)
+  // elements, since each non-empty list adds at most 7
+  L.col4 = take(sizeof(int32_t) * (m + 7 * (nv < m ? nv : m)));
   L.total = p;
   return L;
 }
@@ -211,8 +211,8 @@ void launch_orient(const uint64_t *keys, uint32_t m_in, int b, const int32_t *ra
 void launch_offsets(const int32_t *counts, int32_t n, int32_t *off, const int32_t *row_off,
                     int32_t *warp_list, int32_t *cta_list, int32_t *big_list, Tuning tune,
                     unsigned long long *status, uint32_t *ticket, Ctrl *ctrl, cudaStream_t st);
-// Exclusive scan of ceil(counts / 4) -> voff[0..n]: the node array of the
-// padded column array, in 16-byte words.
+// Exclusive scan of 2 ceil(counts / 8) -> voff[0..n]: the node array of the
+// padded column array (lists in whole 32-byte blocks), in 16-byte words.
 void launch_word_offsets(const int32_t *counts, int32_t n, int32_t *voff,
                          unsigned long long *status, uint32_t *ticket, Ctrl *ctrl,
                          cudaStream_t st);
@@ -220,8 +220,8 @@ void launch_word_offsets(const int32_t *counts, int32_t n, int32_t *voff,
 // Group keys h << b | l of every forward edge (h: the endpoint with the
 // longer forward list, l: the other one), with the digit histograms of the
 // h field for the group sort; also copies every forward list into the
-// padded column array col4 (list v starts at word voff[v]; the rest of its
-// last word is -1).
+// padded column array col4 (list v starts at 16-byte word voff[v], always
+// even; the rest of its last 32-byte block is -1).
 void launch_group_keys(const int32_t *row, const int32_t *col, const int32_t *off,
                        const int32_t *voff, uint32_t m_bound, int b, int passes,
                        int32_t heavy_ratio_pct, Ctrl *ctrl, uint64_t *gkeys, uint32_t *hist,
