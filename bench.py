@@ -62,6 +62,11 @@ def parse_args():
     p.add_argument("--batch-graphs", type=int, default=4096)
     p.add_argument("--serve-graphs", type=int, default=2048,
                    help="requests per arrival rate in the serving run (0: skip it)")
+    p.add_argument("--shard", action="store_true",
+                   help="with several GPUs, count ONE graph: each rank counts its share of "
+                        "the partner groups and one sum all-reduce joins the shares "
+                        "(Sec. III-E; strong scaling).  Default: each rank counts its own "
+                        "replica (weak scaling)")
     return p.parse_args()
 
 
@@ -429,7 +434,17 @@ def run_ours(args, world, rank, local, pg):
     deg_out = torch.empty(n, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    if args.total_only:
+    sharded = args.shard and world > 1
+    if sharded:
+        from paper_1503_00576_gb300.shard import count_sharded
+
+        if args.total_only:
+            def step():
+                return count_sharded(s, d, n, stream=stream)
+        else:
+            def step():
+                return count_sharded(s, d, n, per_vertex=True, stream=stream)[0]
+    elif args.total_only:
         def step():
             return tc.tc_count(s, d, n, stream=stream)
     else:
@@ -470,11 +485,12 @@ def run_ours(args, world, rank, local, pg):
     elapsed = ev0.elapsed_time(ev1) / 1e3
     elapsed = max_over_ranks(pg, elapsed, dev)
     ms_per_step = elapsed / args.steps * 1e3
-    value = world * m_in * args.steps / elapsed
+    # replicas: every rank counted its own copy; shards: all ranks one graph
+    value = (1 if sharded else world) * m_in * args.steps / elapsed
 
     # end to end through the host-buffer entry point, pinned buffers
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not sharded:  # the host-buffer call counts whole graphs
         hs = torch.from_numpy(src).pin_memory()
         hd = torch.from_numpy(dst).pin_memory()
         ht = torch.empty(n, dtype=torch.int64).pin_memory()
@@ -519,14 +535,16 @@ def run_ours(args, world, rank, local, pg):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
         "config": {"workload": graphgen.WORKLOADS[args.workload][0], "n": n, "m_in": m_in,
                    "m_distinct": m, "triangles": T,
                    "outputs": "T (uint64)" if args.total_only
                               else "T (uint64), t[n] (int64), deg[n] (int32)",
                    "l2": "no flush: inputs %.2f GB and key buffers %.2f GB exceed L2"
                          % (8 * m_in / 1e9, 16 * m_in / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": ("shards%d" % world if sharded else "replicas")
+                                  if world > 1 else "single"},
         "roofline": roofline(prof, args.steps, m_in, m, n, args.workload, work,
                              args.total_only),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,

@@ -84,6 +84,28 @@ tc_status tc_count_per_vertex(const int32_t *src, const int32_t *dst, int64_t m,
                               uint64_t *total_out);
 
 /*
+ * One share of the counting work, for counting one graph on several GPUs
+ * (Sec. III-E: every device holds the edge and node arrays and counts its
+ * allotted subset of the edges; the shares add up to the whole).  Here
+ * every device runs the preprocessing itself (it is deterministic, so the
+ * arrays agree without a copy) and counts the partner groups dealt to share
+ * `part` of `parts` (each group list dealt round-robin, heaviest first, so
+ * the shares carry like work).  Summing total_out over the parts gives T,
+ * and summing t_out element-wise gives the per-vertex counts; deg_out is
+ * complete in every part.  parts = 1 is tc_count / tc_count_per_vertex.
+ *   part, parts  0 <= part < parts, else TC_ERR_INVALID_ARG
+ *   t_out        device int64[n], this part's share of t (required when n > 0)
+ *   deg_out      device int32[n], written if not NULL
+ *   total_out    HOST uint64, this part's share of T (required for tc_count_part)
+ * Both synchronise.
+ */
+tc_status tc_count_part(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
+                        int32_t part, int32_t parts, tc_stream_t stream, uint64_t *total_out);
+tc_status tc_count_per_vertex_part(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
+                                   int32_t part, int32_t parts, tc_stream_t stream,
+                                   int64_t *t_out, int32_t *deg_out, uint64_t *total_out);
+
+/*
  * Local clustering coefficients and the transitivity ratio from per-vertex
  * counts and degrees (Sec. I names both as the reason to count triangles):
  *   cc(v) = 2 t(v) / (deg(v) (deg(v) - 1)) in float64, 0 where deg(v) < 2

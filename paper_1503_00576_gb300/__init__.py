@@ -46,7 +46,8 @@ TC_COUNT_ERROR = (1 << 64) - 1
 PHASES = ("canon", "sort1", "degree", "rank", "orient", "sort2", "offsets", "groups", "count")
 
 # Every symbol include/tc.h declares.
-EXPORTS = ("tc_count", "tc_count_per_vertex", "tc_clustering", "tc_count_host",
+EXPORTS = ("tc_count", "tc_count_per_vertex", "tc_count_part", "tc_count_per_vertex_part",
+           "tc_clustering", "tc_count_host",
            "tc_count_per_vertex_host", "tc_workspace_bytes", "tc_count_ws", "tc_set_tuning",
            "tc_get_tuning", "tc_count_batch", "tc_engine_create", "tc_engine_submit",
            "tc_engine_wait", "tc_engine_submit_parts", "tc_engine_poll", "tc_engine_count",
@@ -95,6 +96,9 @@ def _bind(lib):
     sig = {
         "tc_count": ([vp, vp, i64, i32, vp], u64),
         "tc_count_per_vertex": ([vp, vp, i64, i32, vp, vp, vp, c.POINTER(u64)], c.c_int),
+        "tc_count_part": ([vp, vp, i64, i32, i32, i32, vp, c.POINTER(u64)], c.c_int),
+        "tc_count_per_vertex_part": ([vp, vp, i64, i32, i32, i32, vp, vp, vp, c.POINTER(u64)],
+                                     c.c_int),
         "tc_clustering": ([vp, vp, i32, vp, vp, c.POINTER(c.c_double)], c.c_int),
         "tc_count_host": ([vp, vp, i64, i32, c.POINTER(u64)], c.c_int),
         "tc_count_per_vertex_host": ([vp, vp, i64, i32, vp, vp, c.POINTER(u64)], c.c_int),
@@ -218,6 +222,40 @@ def tc_count_per_vertex(src, dst, n: int, stream=None, t_out=None, deg_out=None)
         rc = lib.tc_count_per_vertex(src.data_ptr(), dst.data_ptr(), src.numel(), n,
                                      _stream_of(stream, dev), t.data_ptr(), deg.data_ptr(),
                                      ctypes.byref(total))
+    _check(rc)
+    return int(total.value), t, deg
+
+
+def tc_count_part(src, dst, n: int, part: int, parts: int, stream=None) -> int:
+    """This part's share of T when the counting is split into `parts`
+    shares (the shares of parts 0 .. parts-1 add up to T)."""
+    torch = _torch()
+    dev = _edges(src, dst)
+    total = ctypes.c_uint64(0)
+    lib = load_library()
+    with torch.cuda.device(dev):
+        rc = lib.tc_count_part(src.data_ptr(), dst.data_ptr(), src.numel(), n, part, parts,
+                               _stream_of(stream, dev), ctypes.byref(total))
+    _check(rc)
+    return int(total.value)
+
+
+def tc_count_per_vertex_part(src, dst, n: int, part: int, parts: int, stream=None,
+                             t_out=None, deg_out=None):
+    """(T_part, t_part, deg): this part's shares of T and of t (they add up
+    over the parts to T and t) and the complete degrees."""
+    torch = _torch()
+    dev = _edges(src, dst)
+    t = t_out if t_out is not None else torch.empty(n, dtype=torch.int64, device=dev)
+    deg = deg_out if deg_out is not None else torch.empty(n, dtype=torch.int32, device=dev)
+    if t.dtype != torch.int64 or t.numel() != n or deg.dtype != torch.int32 or deg.numel() != n:
+        raise TypeError("t_out must be int64[n] and deg_out int32[n]")
+    total = ctypes.c_uint64(0)
+    lib = load_library()
+    with torch.cuda.device(dev):
+        rc = lib.tc_count_per_vertex_part(src.data_ptr(), dst.data_ptr(), src.numel(), n, part,
+                                          parts, _stream_of(stream, dev), t.data_ptr(),
+                                          deg.data_ptr(), ctypes.byref(total))
     _check(rc)
     return int(total.value), t, deg
 

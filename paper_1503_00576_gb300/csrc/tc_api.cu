@@ -163,7 +163,8 @@ struct BatchRun {
 tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t n,
                        cudaStream_t st, unsigned char *ws, const Layout &L, int64_t *t_out,
                        int32_t *deg_out, const BatchRun *batch, const Tuning &tune,
-                       PhaseTimer &pt, Ctrl *staging, bool work_stats = false) {
+                       PhaseTimer &pt, Ctrl *staging, bool work_stats = false,
+                       int32_t shard = 0, int32_t shards = 1) {
   const uint32_t m = (uint32_t)m_in;
   const int b = id_bits(n);
   // radix passes: undirected keys (2b bits), rank keys (degree bits < 2^b),
@@ -327,7 +328,8 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
 
   pt.start(TC_PHASE_COUNT);
   cudaError_t e = launch_count(off, voff, col4, goff, part, warp_groups, cta_groups, big_groups,
-                               n, ctrl, t_out ? t_rank : nullptr, t_out ? nullptr : t_rank, st);
+                               n, shard, shards, ctrl, t_out ? t_rank : nullptr,
+                               t_out ? nullptr : t_rank, st);
   if (e == cudaSuccess && t_out) launch_gather_counts(t_rank, rank, n, t_out, st);
   if (e == cudaSuccess && batch) {
     if (t_out) {  // per graph: (sum of t) / 3
@@ -366,12 +368,12 @@ Tuning current_tuning() {
 tc_status run_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t n,
                    cudaStream_t st, unsigned char *ws, const Layout &L, int64_t *t_out,
                    int32_t *deg_out, uint64_t *total, Ctrl *staging = nullptr,
-                   bool profile = true) {
+                   bool profile = true, int32_t shard = 0, int32_t shards = 1) {
   PhaseTimer pt(st, profile);
   Ctrl *h = staging ? staging : host_ctrl();
   if (!h) return set_status(TC_ERR_OOM, "pinned staging buffer");
   tc_status s = enqueue_core(src, dst, m_in, n, st, ws, L, t_out, deg_out, nullptr,
-                             current_tuning(), pt, h);
+                             current_tuning(), pt, h, false, shard, shards);
   if (s != TC_OK) return s;
   TC_CUDA(cudaStreamSynchronize(st), "synchronize");
   pt.fold();
@@ -380,9 +382,12 @@ tc_status run_core(const int32_t *src, const int32_t *dst, int64_t m_in, int32_t
 
 tc_status count_impl(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
                      cudaStream_t st, void *ws_user, size_t ws_bytes, int64_t *t_out,
-                     int32_t *deg_out, uint64_t *total) {
+                     int32_t *deg_out, uint64_t *total, int32_t shard = 0,
+                     int32_t shards = 1) {
   tc_status s = check_args(src, dst, m, n);
   if (s != TC_OK) return s;
+  if (shards < 1 || shard < 0 || shard >= shards)
+    return set_status(TC_ERR_INVALID_ARG, "shard %d of %d", shard, shards);
   if (m > 0 && n == 0) return set_status(TC_ERR_ID_RANGE, "n = 0 but m > 0");
   if (m == 0) {
     if (n > 0 && t_out)
@@ -400,12 +405,14 @@ tc_status count_impl(const int32_t *src, const int32_t *dst, int64_t m, int32_t 
                         L.total);
     if ((uintptr_t)ws_user & 255)
       return set_status(TC_ERR_INVALID_ARG, "workspace is not 256-byte aligned");
-    return run_core(src, dst, m, n, st, (unsigned char *)ws_user, L, t_out, deg_out, total);
+    return run_core(src, dst, m, n, st, (unsigned char *)ws_user, L, t_out, deg_out, total,
+                    nullptr, true, shard, shards);
   }
   keep_pool_memory();
   void *ws = nullptr;
   TC_CUDA(cudaMallocAsync(&ws, L.total, st), "workspace allocation");
-  s = run_core(src, dst, m, n, st, (unsigned char *)ws, L, t_out, deg_out, total);
+  s = run_core(src, dst, m, n, st, (unsigned char *)ws, L, t_out, deg_out, total, nullptr, true,
+               shard, shards);
   const tc_status keep = s;
   char detail[256];
   memcpy(detail, t_detail, sizeof(detail));
@@ -730,6 +737,24 @@ tc_status tc_count_per_vertex(const int32_t *src, const int32_t *dst, int64_t m,
   uint64_t T = 0;
   tc_status s =
       count_impl(src, dst, m, n, (cudaStream_t)stream, nullptr, 0, t_out, deg_out, &T);
+  if (s == TC_OK && total_out) *total_out = T;
+  return s;
+}
+
+tc_status tc_count_part(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
+                        int32_t part, int32_t parts, tc_stream_t stream, uint64_t *total_out) {
+  if (!total_out) return set_status(TC_ERR_INVALID_ARG, "total_out is NULL");
+  return count_impl(src, dst, m, n, (cudaStream_t)stream, nullptr, 0, nullptr, nullptr,
+                    total_out, part, parts);
+}
+
+tc_status tc_count_per_vertex_part(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
+                                   int32_t part, int32_t parts, tc_stream_t stream,
+                                   int64_t *t_out, int32_t *deg_out, uint64_t *total_out) {
+  if (n > 0 && !t_out) return set_status(TC_ERR_INVALID_ARG, "t_out is NULL");
+  uint64_t T = 0;
+  tc_status s = count_impl(src, dst, m, n, (cudaStream_t)stream, nullptr, 0, t_out, deg_out, &T,
+                           part, parts);
   if (s == TC_OK && total_out) *total_out = T;
   return s;
 }

@@ -233,11 +233,14 @@ void launch_work(const int32_t *off, const int32_t *goff, const int32_t *part, i
 // ---- launchers (count.cu) ----
 // t != nullptr: per-vertex counts (rank space).  Otherwise, if tg is not
 // nullptr, tg[h] += triangles found in group h (their sum per graph is the
-// graph's count).
+// graph's count).  Only the groups of shard `shard` of `shards` are counted
+// (every group list dealt round-robin in heavy-first order); shards = 1
+// counts them all.
 cudaError_t launch_count(const int32_t *off, const int32_t *voff, const int32_t *col4,
                          const int32_t *goff, const int32_t *part, const int32_t *warp_groups,
                          const int32_t *cta_groups, const int32_t *big_groups, int32_t n,
-                         Ctrl *ctrl, int64_t *t, int64_t *tg, cudaStream_t st);
+                         int32_t shard, int32_t shards, Ctrl *ctrl, int64_t *t, int64_t *tg,
+                         cudaStream_t st);
 // Sets the counting kernels' attributes and occupancy for the current
 // device (done lazily otherwise; needed before capturing a CUDA graph).
 cudaError_t prepare_count_kernels();

@@ -1,0 +1,77 @@
+"""Shares of the counting work (the multi-GPU setup of Sec. III-E), run one
+after another on one GPU: the shares of parts 0 .. P-1 must add up exactly
+to the whole count (T and every t(v)), every share must carry a like part
+of the work, and the degrees must be complete in every share.  Counts are
+integers: the tolerance is zero."""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tc():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1503_00576_gb300 as lib
+
+    lib.load_library()
+    return lib
+
+
+def dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a, np.int32)).cuda()
+
+
+@pytest.fixture(scope="module")
+def rmat16():
+    src, dst = graphgen.rmat(16, 16 << 16, 21)
+    return dev(src), dev(dst), 1 << 16
+
+
+@pytest.mark.parametrize("parts", [1, 2, 3, 8])
+def test_total_shares_add_up(tc, rmat16, parts):
+    s, d, n = rmat16
+    whole = tc.tc_count(s, d, n)
+    shares = [tc.tc_count_part(s, d, n, p, parts) for p in range(parts)]
+    assert sum(shares) == whole
+    if parts > 1:  # round-robin dealing of heavy-first lists: like shares
+        assert min(shares) > 0.5 * whole / parts
+        assert max(shares) < 1.5 * whole / parts
+
+
+def test_per_vertex_shares_add_up_to_the_oracle(tc):
+    src, dst = graphgen.rmat(12, 16 << 12, 22)
+    n = 1 << 12
+    want = oracle.forward(src, dst, n)
+    s, d = dev(src), dev(dst)
+    acc = np.zeros(n, np.int64)
+    total = 0
+    for p in range(3):
+        T, t, deg = tc.tc_count_per_vertex_part(s, d, n, p, 3)
+        total += T
+        acc += t.cpu().numpy()
+        assert np.array_equal(deg.cpu().numpy(), want["deg"])
+    assert total == want["T"]
+    assert np.array_equal(acc, want["t"])
+
+
+def test_shares_of_a_batchless_empty_graph(tc):
+    import torch
+
+    e = torch.empty(0, dtype=torch.int32, device="cuda")
+    assert [tc.tc_count_part(e, e, 10, p, 2) for p in range(2)] == [0, 0]
+
+
+@pytest.mark.parametrize("part,parts", [(0, 0), (-1, 2), (2, 2), (5, 3)])
+def test_bad_shares_are_rejected(tc, rmat16, part, parts):
+    s, d, n = rmat16
+    with pytest.raises(tc.TCError) as err:
+        tc.tc_count_part(s, d, n, part, parts)
+    assert err.value.code == tc.TC_ERR_INVALID_ARG
