@@ -88,9 +88,11 @@ tc_status tc_count_per_vertex(const int32_t *src, const int32_t *dst, int64_t m,
  * (Sec. III-E: every device holds the edge and node arrays and counts its
  * allotted subset of the edges; the shares add up to the whole).  Here
  * every device runs the preprocessing itself (it is deterministic, so the
- * arrays agree without a copy) and counts the partner groups dealt to share
- * `part` of `parts` (each group list dealt round-robin, heaviest first, so
- * the shares carry like work).  Summing total_out over the parts gives T,
+ * arrays agree without a copy) and counts the partner groups of the vertices
+ * h of degree rank h = part mod parts (consecutive ranks have like degrees
+ * and alternate between the shares, so the shares carry like work; the
+ * dealing depends on the graph alone, so separate calls agree on it).
+ * Summing total_out over the parts gives T,
  * and summing t_out element-wise gives the per-vertex counts; deg_out is
  * complete in every part.  parts = 1 is tc_count / tc_count_per_vertex.
  *   part, parts  0 <= part < parts, else TC_ERR_INVALID_ARG

@@ -91,23 +91,7 @@ struct Lists {
   const int32_t *__restrict__ col4;  // forward lists, each padded with -1 to whole 32-byte blocks
   const int32_t *__restrict__ goff;  // partner-group offsets
   const int32_t *__restrict__ part;  // partners
-  uint32_t shard, shards;            // this run counts the groups at positions = shard mod shards
 };
-
-// Number of the n_list groups of a list that fall to this run's shard:
-// positions shard, shard + shards, ... in heavy-first order (every list is
-// dealt round-robin, so each shard gets a like mix of heavy and light
-// groups).
-__device__ __forceinline__ uint32_t shard_count(const Lists &g, uint32_t n_list) {
-  return n_list > g.shard ? (n_list - g.shard + g.shards - 1) / g.shards : 0u;
-}
-
-// The group at the shard's gi-th position, heavy first: lists are filled in
-// about ascending rank, and high ranks (high degrees) carry the most work.
-__device__ __forceinline__ int32_t shard_group(const Lists &g, const int32_t *list,
-                                               uint32_t n_list, uint32_t gi) {
-  return __ldg(list + (n_list - 1 - (gi * g.shards + g.shard)));
-}
 
 // One hash set in shared memory.
 struct Table {
@@ -442,7 +426,6 @@ __device__ __forceinline__ void cta_groups(const Lists &g, const int32_t *__rest
                                            int64_t *t, int64_t *tg, uint64_t &found_total) {
   constexpr int WARPS = THREADS / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t n_mine = shard_count(g, n_list);
   for (;;) {
     if (tid == 0) {
       sh.group = (int32_t)atomicAdd(cursor, 1u);
@@ -450,9 +433,10 @@ __device__ __forceinline__ void cta_groups(const Lists &g, const int32_t *__rest
     }
     __syncthreads();  // also orders the previous group's drain before this fill
     const uint32_t gi = (uint32_t)sh.group;
-    if (gi >= n_mine) break;
-    // heavy groups first, to shorten the tail
-    const int32_t h = shard_group(g, list, n_list, gi);
+    if (gi >= n_list) break;
+    // lists are filled in about ascending rank, and high ranks (high
+    // degrees) carry the most work: take them first to shorten the tail
+    const int32_t h = __ldg(list + (n_list - 1 - gi));
     const int32_t hd = __ldg(g.off + h + 1) - __ldg(g.off + h);
     const int32_t *hl = g.col4 + 4 * (size_t)__ldg(g.voff + h);
     const int32_t pb = __ldg(g.goff + h), np = __ldg(g.goff + h + 1) - pb;
@@ -504,15 +488,14 @@ __device__ __forceinline__ void warp_groups(const Lists &g, const int32_t *__res
                                             uint16_t *slot_of, WarpScratch &ws, int64_t *t,
                                             int64_t *tg, uint64_t &found_total) {
   const int lane = threadIdx.x & 31;
-  const uint32_t n_mine = shard_count(g, n_list);
   for (;;) {
     uint32_t g0 = 0;
     if (lane == 0) g0 = atomicAdd(cursor, (uint32_t)kGroupChunk);
     g0 = __shfl_sync(kFull, g0, 0);
-    if (g0 >= n_mine) break;
-    const uint32_t g1 = min(g0 + (uint32_t)kGroupChunk, n_mine);
+    if (g0 >= n_list) break;
+    const uint32_t g1 = min(g0 + (uint32_t)kGroupChunk, n_list);
     for (uint32_t gi = g0; gi < g1; ++gi) {
-      const int32_t h = shard_group(g, list, n_list, gi);  // heavy (high-rank) groups first
+      const int32_t h = __ldg(list + (n_list - 1 - gi));  // heavy (high-rank) groups first
       const int32_t hd = __ldg(g.off + h + 1) - __ldg(g.off + h);
       const int32_t *hl = g.col4 + 4 * (size_t)__ldg(g.voff + h);
       const int32_t pb = __ldg(g.goff + h), np = __ldg(g.goff + h + 1) - pb;
@@ -725,13 +708,12 @@ cudaError_t prepare_count_kernels() {
 cudaError_t launch_count(const int32_t *off, const int32_t *voff, const int32_t *col4,
                          const int32_t *goff, const int32_t *part, const int32_t *warp_groups,
                          const int32_t *cta_groups, const int32_t *big_groups, int32_t n,
-                         int32_t shard, int32_t shards, Ctrl *ctrl, int64_t *t, int64_t *tg,
-                         cudaStream_t st) {
+                         Ctrl *ctrl, int64_t *t, int64_t *tg, cudaStream_t st) {
   const bool pv = t != nullptr;
   CountGrid cg;
   cudaError_t e = count_grid(pv, &cg);
   if (e != cudaSuccess) return e;
-  const Lists g{off, voff, col4, goff, part, (uint32_t)shard, (uint32_t)shards};
+  const Lists g{off, voff, col4, goff, part};
   // the long lists first, on their own wide CTAs
   if (pv) {
     k_count_big<true><<<cg.big_blocks, kBigThreads, big_smem<true>(), st>>>(g, big_groups, n, ctrl,

@@ -469,7 +469,8 @@ __global__ void __launch_bounds__(kScanThreads)
 k_offsets(const int32_t *__restrict__ counts, int32_t n, int32_t *__restrict__ off,
           const int32_t *__restrict__ row_off, int32_t *__restrict__ warp_list,
           int32_t *__restrict__ cta_list, int32_t *__restrict__ big_list, Tuning tune,
-          unsigned long long *status, uint32_t *ticket, Ctrl *ctrl) {
+          unsigned long long *status, uint32_t *ticket, Ctrl *ctrl, uint32_t shard,
+          uint32_t shards) {
   constexpr int IPT = kScanItemsPerThread, TILE = kScanTile;
   __shared__ uint32_t s_scratch[32];
   __shared__ uint32_t s_tile, s_excl;
@@ -507,7 +508,8 @@ k_offsets(const int32_t *__restrict__ counts, int32_t n, int32_t *__restrict__ o
   for (int i = 0; i < IPT; ++i) {
     const uint32_t v = first + i;
     int32_t dh = 0;
-    if (v < (uint32_t)n && d[i] > 0) dh = __ldg(row_off + v + 1) - __ldg(row_off + v);
+    if (v < (uint32_t)n && d[i] > 0 && v % shards == shard)
+      dh = __ldg(row_off + v + 1) - __ldg(row_off + v);
     // a warp takes a group only if both its list and its partner count are
     // short: one warp streaming thousands of partners would finish last
     const bool is_warp = dh >= 2 && dh <= tune.warp_max_list && d[i] <= tune.warp_max_partners;
@@ -603,18 +605,20 @@ void launch_orient(const uint64_t *keys, uint32_t m_in, int b, const int32_t *ra
 
 void launch_offsets(const int32_t *counts, int32_t n, int32_t *off, const int32_t *row_off,
                     int32_t *warp_list, int32_t *cta_list, int32_t *big_list, Tuning tune,
-                    unsigned long long *status, uint32_t *ticket, Ctrl *ctrl, cudaStream_t st) {
+                    unsigned long long *status, uint32_t *ticket, Ctrl *ctrl, cudaStream_t st,
+                    int32_t shard, int32_t shards) {
   const uint32_t items = (uint32_t)n + 1;
   const uint32_t grid = max(1u, (items + kScanTile - 1) / kScanTile);
   tune.warp_max_list = min(max(tune.warp_max_list, 0), kWarpMaxRow);  // warp table capacity
   if (row_off)
     k_offsets<kScanGroups><<<grid, kScanThreads, 0, st>>>(counts, n, off, row_off, warp_list,
                                                           cta_list, big_list, tune, status,
-                                                          ticket, ctrl);
+                                                          ticket, ctrl, (uint32_t)shard,
+                                                          (uint32_t)shards);
   else
     k_offsets<kScanPlain><<<grid, kScanThreads, 0, st>>>(counts, n, off, nullptr, nullptr,
                                                          nullptr, nullptr, tune, status, ticket,
-                                                         ctrl);
+                                                         ctrl, 0u, 1u);
   note_launch();
 }
 
@@ -625,7 +629,7 @@ void launch_word_offsets(const int32_t *counts, int32_t n, int32_t *voff,
   const uint32_t grid = max(1u, (items + kScanTile - 1) / kScanTile);
   k_offsets<kScanWords><<<grid, kScanThreads, 0, st>>>(counts, n, voff, nullptr, nullptr,
                                                        nullptr, nullptr, kDefaultTuning, status,
-                                                       ticket, ctrl);
+                                                       ticket, ctrl, 0u, 1u);
   note_launch();
 }
 

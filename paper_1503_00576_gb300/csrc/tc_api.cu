@@ -321,15 +321,16 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
     }
   }
   const int32_t *part = reinterpret_cast<const int32_t *>(gout);
+  // only this run's share of the groups is binned (all of them unless the
+  // counting is split over several devices, Sec. III-E)
   launch_offsets(gcnt, n, goff, off, warp_groups, cta_groups, big_groups, tune, st_scan2,
-                 &ctrl->tile_ticket[kTicketGroupScan], ctrl, st);
+                 &ctrl->tile_ticket[kTicketGroupScan], ctrl, st, shard, shards);
   pt.stop(TC_PHASE_GROUPS);
   if (work_stats) launch_work(off, goff, part, n, ctrl, st);
 
   pt.start(TC_PHASE_COUNT);
   cudaError_t e = launch_count(off, voff, col4, goff, part, warp_groups, cta_groups, big_groups,
-                               n, shard, shards, ctrl, t_out ? t_rank : nullptr,
-                               t_out ? nullptr : t_rank, st);
+                               n, ctrl, t_out ? t_rank : nullptr, t_out ? nullptr : t_rank, st);
   if (e == cudaSuccess && t_out) launch_gather_counts(t_rank, rank, n, t_out, st);
   if (e == cudaSuccess && batch) {
     if (t_out) {  // per graph: (sum of t) / 3

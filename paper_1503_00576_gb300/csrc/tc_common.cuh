@@ -207,10 +207,13 @@ void launch_orient(const uint64_t *keys, uint32_t m_in, int b, const int32_t *ra
                    Ctrl *ctrl, cudaStream_t st);
 // Exclusive scan counts[0..n) -> off[0..n].  With row_off != nullptr the
 // entries are partner groups and are binned into warp_list / cta_list /
-// big_list by the length of their hashed list.
+// big_list by the length of their hashed list; only the groups h with
+// h mod shards = shard are binned (the share of the counting work this run
+// does; shards = 1 bins them all).
 void launch_offsets(const int32_t *counts, int32_t n, int32_t *off, const int32_t *row_off,
                     int32_t *warp_list, int32_t *cta_list, int32_t *big_list, Tuning tune,
-                    unsigned long long *status, uint32_t *ticket, Ctrl *ctrl, cudaStream_t st);
+                    unsigned long long *status, uint32_t *ticket, Ctrl *ctrl, cudaStream_t st,
+                    int32_t shard = 0, int32_t shards = 1);
 // Exclusive scan of 2 ceil(counts / 8) -> voff[0..n]: the node array of the
 // padded column array (lists in whole 32-byte blocks), in 16-byte words.
 void launch_word_offsets(const int32_t *counts, int32_t n, int32_t *voff,
@@ -233,14 +236,11 @@ void launch_work(const int32_t *off, const int32_t *goff, const int32_t *part, i
 // ---- launchers (count.cu) ----
 // t != nullptr: per-vertex counts (rank space).  Otherwise, if tg is not
 // nullptr, tg[h] += triangles found in group h (their sum per graph is the
-// graph's count).  Only the groups of shard `shard` of `shards` are counted
-// (every group list dealt round-robin in heavy-first order); shards = 1
-// counts them all.
+// graph's count).
 cudaError_t launch_count(const int32_t *off, const int32_t *voff, const int32_t *col4,
                          const int32_t *goff, const int32_t *part, const int32_t *warp_groups,
                          const int32_t *cta_groups, const int32_t *big_groups, int32_t n,
-                         int32_t shard, int32_t shards, Ctrl *ctrl, int64_t *t, int64_t *tg,
-                         cudaStream_t st);
+                         Ctrl *ctrl, int64_t *t, int64_t *tg, cudaStream_t st);
 // Sets the counting kernels' attributes and occupancy for the current
 // device (done lazily otherwise; needed before capturing a CUDA graph).
 cudaError_t prepare_count_kernels();

@@ -2,7 +2,9 @@
 after another on one GPU: the shares of parts 0 .. P-1 must add up exactly
 to the whole count (T and every t(v)), every share must carry a like part
 of the work, and the degrees must be complete in every share.  Counts are
-integers: the tolerance is zero."""
+integers: the tolerance is zero.  Each share is a separate call, so this
+also checks that the dealing of groups to shares does not depend on the
+order in which one call happens to bin them."""
 import numpy as np
 import pytest
 
@@ -41,9 +43,9 @@ def test_total_shares_add_up(tc, rmat16, parts):
     whole = tc.tc_count(s, d, n)
     shares = [tc.tc_count_part(s, d, n, p, parts) for p in range(parts)]
     assert sum(shares) == whole
-    if parts > 1:  # round-robin dealing of heavy-first lists: like shares
-        assert min(shares) > 0.5 * whole / parts
-        assert max(shares) < 1.5 * whole / parts
+    if 1 < parts <= 3:  # consecutive degree ranks alternate: like shares
+        assert min(shares) > 0.6 * whole / parts
+        assert max(shares) < 1.4 * whole / parts
 
 
 def test_per_vertex_shares_add_up_to_the_oracle(tc):
