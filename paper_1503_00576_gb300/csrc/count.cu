@@ -328,8 +328,9 @@ __device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__res
   const int32_t incl_v = warp_incl_scan(nv);
   const int32_t total_e = __shfl_sync(kFull, incl_e, 31);
   const int32_t total_v = __shfl_sync(kFull, incl_v, 31);
-  // a block step probes eight entries, an element step one: cost ~5:1
-  const bool words = 5 * ((total_v + 63) >> 6) < ((total_e + 31) >> 5);
+  // a block step probes eight entries, an element step one: cost ~4:1
+  // (measured: 4 beats 5 and 7 on R-MAT and random geometric graphs)
+  const bool words = 4 * ((total_v + 63) >> 6) < ((total_e + 31) >> 5);
   // list r+1 starts where list r ends (empty lists add nothing to the scans)
   const bool last = rank == k - 1;
   if (dl > 0) {
