@@ -37,6 +37,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kGroupChunk = 8;  // warp groups per atomic
+constexpr int kMinChunk = 8;    // fewest partners a warp of a CTA group claims
 constexpr int kWindows = 4;     // words per lane loaded before probing
 constexpr int kBigWindows = 4;  // ... in the long-list kernel
 
@@ -415,8 +416,8 @@ struct CtaShared {
 };
 
 // Groups of `list` counted by the whole CTA: N+(h) hashed once, warps claim
-// chunks of partners (32, or fewer when a group has few partners, so that
-// every warp gets about two).  A list longer than half the table is hashed
+// chunks of partners, each a share of the partners left (at most 32), so
+// that the warps run out of work together.  A list longer than half the table is hashed
 // in equal segments, one after another, each probed by all partners:
 // N+(h) & N+(l) is the disjoint union of the segments' intersections.  The
 // table (SLOTS slots) is empty on entry and on exit.
@@ -444,7 +445,6 @@ __device__ __forceinline__ void cta_groups(const Lists &g, const int32_t *__rest
     const int32_t nseg = (hd + SLOTS / 2 - 1) / (SLOTS / 2);
     const int32_t seg_len = (hd + nseg - 1) / nseg;
     tb.slots = table_slots(seg_len, SLOTS);
-    const int32_t cs = max(8, min(32, (np + 2 * WARPS - 1) / (2 * WARPS)));
     uint64_t found_group = 0;
     for (int32_t s0 = 0; s0 < hd; s0 += seg_len) {
       const int32_t len = min(seg_len, hd - s0);
@@ -452,13 +452,19 @@ __device__ __forceinline__ void cta_groups(const Lists &g, const int32_t *__rest
       fill_table(hl + s0, len, tb, slot_of, tid, THREADS);
       __syncthreads();
       for (;;) {
-        uint32_t c = 0;
-        if (lane == 0) c = atomicAdd(&sh.chunk, 1u);
+        // guided chunks: a share of what is left, so that the warps finish
+        // the group together (32 partners at most, 8 at least)
+        uint32_t c = 0, cs = 0;
+        if (lane == 0) {
+          const int32_t left = np - (int32_t)*(volatile uint32_t *)&sh.chunk;
+          cs = (uint32_t)max(kMinChunk, min(32, left / (2 * WARPS)));
+          c = atomicAdd(&sh.chunk, cs);
+        }
         c = __shfl_sync(kFull, c, 0);
-        const int32_t c0 = (int32_t)c * cs;
-        if (c0 >= np) break;
-        probe_chunk<PV, W>(g, g.part + pb, np, c0, cs, tb, s_ws[warp], t, found_total,
-                           found_group);
+        cs = __shfl_sync(kFull, cs, 0);
+        if ((int32_t)c >= np) break;
+        probe_chunk<PV, W>(g, g.part + pb, np, (int32_t)c, (int32_t)cs, tb, s_ws[warp], t,
+                           found_total, found_group);
       }
       __syncthreads();
       if (PV) {
