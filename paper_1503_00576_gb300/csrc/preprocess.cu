@@ -106,35 +106,47 @@ __device__ __forceinline__ uint32_t block_scan_exclusive(uint32_t x, uint32_t *s
   return before + incl - x;
 }
 
-// Decoupled look-back for one running sum (one thread).  Publishes the
-// tile's aggregate, walks back to the nearest inclusive prefix, publishes
-// its own inclusive prefix and returns the exclusive prefix.
-__device__ uint64_t lookback_single(unsigned long long *status, uint32_t tile, uint64_t agg,
-                                    Ctrl *ctrl) {
+// Decoupled look-back for one running sum, by one warp.  Publishes the
+// tile's aggregate, then reads the statuses of 32 predecessors at once (lane
+// k reads tile j - k): once all 32 have published something, it adds the
+// values up to the nearest inclusive prefix, or all 32 and moves on; so a
+// walk back over many tiles costs one memory latency per 32 tiles.
+// Publishes the tile's inclusive prefix and returns the exclusive one (in
+// every lane).  All 32 lanes of the warp must call it.
+__device__ uint64_t lookback_warp(unsigned long long *status, uint32_t tile, uint64_t agg,
+                                  Ctrl *ctrl) {
+  const int lane = threadIdx.x & 31;
   if (tile == 0) {
-    st_volatile_u64(&status[0], kFlagInclusive | agg);
+    if (lane == 0) st_volatile_u64(&status[0], kFlagInclusive | agg);
     return 0;
   }
-  st_volatile_u64(&status[tile], kFlagAggregate | agg);
+  if (lane == 0) st_volatile_u64(&status[tile], kFlagAggregate | agg);
   uint64_t excl = 0;
   int64_t j = (int64_t)tile - 1;
   uint32_t spins = 0;
-  while (j >= 0) {
-    unsigned long long s = ld_volatile_u64(&status[j]);
-    unsigned long long flag = s & ~kValueMask;
-    if (flag == 0) {
+  for (;;) {
+    const int64_t idx = j - lane;
+    // before tile 0 nothing is added: an inclusive zero
+    const unsigned long long s = idx >= 0 ? ld_volatile_u64(&status[idx]) : kFlagInclusive;
+    const unsigned long long flag = s & ~kValueMask;
+    if (__any_sync(kFull, flag == 0)) {  // a predecessor in the window has not published
       if (++spins > kSpinLimit) {
-        atomicOr(&ctrl->err, kErrTimeout);
+        if (lane == 0) atomicOr(&ctrl->err, kErrTimeout);
         break;
       }
-      if (spins > 64) __nanosleep(64);
+      if (spins > 8) __nanosleep(32);
       continue;
     }
-    excl += s & kValueMask;
-    if (flag == kFlagInclusive) break;
-    --j;
+    const uint32_t inc = __ballot_sync(kFull, flag == kFlagInclusive);
+    const int last = inc ? __ffs(inc) - 1 : 31;  // lanes 0 .. last contribute
+    uint64_t v = lane <= last ? (s & kValueMask) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    excl += v;
+    if (inc) break;
+    j -= 32;
   }
-  st_volatile_u64(&status[tile], kFlagInclusive | (excl + agg));
+  if (lane == 0) st_volatile_u64(&status[tile], kFlagInclusive | (excl + agg));
   return excl;
 }
 
@@ -396,7 +408,7 @@ k_rank_keys(const int32_t *__restrict__ deg, int32_t n, int b, int passes,
 // ---------------------------------------------------------------------------
 // orient: compact distinct edges, orient by rank (= (degree, id) order)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kOrientThreads)
+__global__ void __launch_bounds__(kOrientThreads, 4)
 k_orient(const uint64_t *__restrict__ keys, int b,
          const int32_t *__restrict__ rank, uint64_t *__restrict__ okeys,
          uint32_t *__restrict__ hist2, int passes2, unsigned long long *status, Ctrl *ctrl) {
@@ -430,24 +442,41 @@ k_orient(const uint64_t *__restrict__ keys, int b,
     flags |= (uint32_t)keep << i;
     cnt += keep;
   }
+  // orient the kept keys now: the rank gathers of eight keys at a time are
+  // issued together, and all of it overlaps the other tiles' look-backs
+  constexpr int HALF = KPT / 2;
+#pragma unroll
+  for (int h0 = 0; h0 < KPT; h0 += HALF) {
+    uint32_t ra[HALF], rc[HALF];
+#pragma unroll
+    for (int i = 0; i < HALF; ++i) {
+      const bool keep = (flags >> (h0 + i)) & 1u;
+      ra[i] = keep ? (uint32_t)__ldg(rank + (uint32_t)(k[h0 + i] >> b)) : 0u;
+      rc[i] = keep ? (uint32_t)__ldg(rank + (uint32_t)(k[h0 + i] & mask)) : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < HALF; ++i) {
+      const uint32_t owner = min(ra[i], rc[i]), nbr = max(ra[i], rc[i]);
+      k[h0 + i] = ((uint64_t)owner << b) | nbr;
+      if ((flags >> (h0 + i)) & 1u)
+        for (int p = 0; p < passes2; ++p)
+          atomicAdd(&s_hist[p * 256 + ((owner >> (8 * p)) & 255u)], 1u);
+    }
+  }
   uint32_t tile_cnt;
   const uint32_t toff = block_scan_exclusive<kOrientThreads>(cnt, s_scratch, &tile_cnt);
-  if (tid == 0) {
-    const uint64_t excl = lookback_single(status, tile, tile_cnt, ctrl);
-    s_excl = (uint32_t)excl;
-    if (tile_base + TILE >= m_in) ctrl->m = (uint32_t)(excl + tile_cnt);  // last tile
+  if (tid < 32) {
+    const uint64_t excl = lookback_warp(status, tile, tile_cnt, ctrl);
+    if (tid == 0) {
+      s_excl = (uint32_t)excl;
+      if (tile_base + TILE >= m_in) ctrl->m = (uint32_t)(excl + tile_cnt);  // last tile
+    }
   }
   __syncthreads();
   uint32_t pos = s_excl + toff;
 #pragma unroll
-  for (int i = 0; i < KPT; ++i) {
-    if (!((flags >> i) & 1u)) continue;
-    const uint32_t a = (uint32_t)(k[i] >> b), c = (uint32_t)(k[i] & mask);
-    const uint32_t ra = (uint32_t)__ldg(rank + a), rc = (uint32_t)__ldg(rank + c);
-    const uint32_t owner = min(ra, rc), nbr = max(ra, rc);
-    okeys[pos++] = ((uint64_t)owner << b) | nbr;
-    for (int p = 0; p < passes2; ++p) atomicAdd(&s_hist[p * 256 + ((owner >> (8 * p)) & 255u)], 1u);
-  }
+  for (int i = 0; i < KPT; ++i)
+    if ((flags >> i) & 1u) okeys[pos++] = k[i];
   __syncthreads();
   for (int i = tid; i < passes2 * 256; i += kOrientThreads)
     if (s_hist[i]) atomicAdd(&hist2[i], s_hist[i]);
@@ -493,7 +522,10 @@ k_offsets(const int32_t *__restrict__ counts, int32_t n, int32_t *__restrict__ o
   }
   uint32_t tile_sum;
   const uint32_t toff = block_scan_exclusive<kScanThreads>(sum, s_scratch, &tile_sum);
-  if (tid == 0) s_excl = (uint32_t)lookback_single(status, tile, tile_sum, ctrl);
+  if (tid < 32) {
+    const uint32_t excl = (uint32_t)lookback_warp(status, tile, tile_sum, ctrl);
+    if (tid == 0) s_excl = excl;
+  }
   __syncthreads();
   uint32_t run = s_excl + toff;
 #pragma unroll
