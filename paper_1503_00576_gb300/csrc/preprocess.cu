@@ -357,6 +357,7 @@ k_radix_pass(const uint64_t *__restrict__ in, void *__restrict__ out, uint32_t n
 // distinct edges after sort 1 and their degree histogram
 // ---------------------------------------------------------------------------
 constexpr int kDegThreads = 256;
+constexpr int kDegUnroll = 8;
 
 __global__ void __launch_bounds__(kDegThreads)
 k_unique_degree(const uint64_t *__restrict__ keys, const Ctrl *__restrict__ ctrl, int b,
@@ -366,17 +367,28 @@ k_unique_degree(const uint64_t *__restrict__ keys, const Ctrl *__restrict__ ctrl
   const uint64_t mask = (1ull << b) - 1;
   const uint32_t stride = gridDim.x * kDegThreads;
   const int lane = threadIdx.x & 31;
-  for (uint32_t i = blockIdx.x * kDegThreads + threadIdx.x; i < m_in; i += stride) {
-    const uint64_t key = __ldg(keys + i);
-    const bool first = key != sentinel && (i == 0 || __ldg(keys + i - 1) != key);
-    const uint32_t firsts = __ballot_sync(__activemask(), first);
-    if (!first) continue;
-    // sorted keys: neighbouring lanes usually share the lower endpoint, so
-    // that side takes one atomic per run
-    const uint32_t a = (uint32_t)(key >> b);
-    const uint32_t peers = __match_any_sync(firsts, a);
-    if (lane == __ffs(peers) - 1) atomicAdd(&deg[a], __popc(peers));
-    atomicAdd(&deg[(uint32_t)(key & mask)], 1);
+  // kDegUnroll keys per thread per round, their loads issued together (the
+  // kernel is latency-bound otherwise); a round is uniform per warp
+  for (uint32_t i0 = blockIdx.x * kDegThreads + (threadIdx.x & ~31u); i0 < m_in;
+       i0 += kDegUnroll * stride) {
+    uint64_t key[kDegUnroll], prev[kDegUnroll];
+#pragma unroll
+    for (int q = 0; q < kDegUnroll; ++q) {
+      const uint32_t i = i0 + q * stride + lane;
+      key[q] = i < m_in ? __ldg(keys + i) : sentinel;
+      prev[q] = (i < m_in && i > 0) ? __ldg(keys + i - 1) : ~0ull;
+    }
+#pragma unroll
+    for (int q = 0; q < kDegUnroll; ++q) {
+      const bool first = key[q] != sentinel && prev[q] != key[q];
+      const uint32_t firsts = __ballot_sync(kFull, first);
+      // sorted keys: neighbouring lanes usually share the lower endpoint,
+      // so that side takes one atomic per run
+      const uint32_t a = (uint32_t)(key[q] >> b);
+      const uint32_t peers = __match_any_sync(kFull, first ? a : 0xffffffffu) & firsts;
+      if (first && lane == __ffs(peers) - 1) atomicAdd(&deg[a], __popc(peers));
+      if (first) atomicAdd(&deg[(uint32_t)(key[q] & mask)], 1);
+    }
   }
 }
 
