@@ -22,7 +22,7 @@
 //
 // Per-vertex counts t(v) (Sec. I: the numerator of the clustering
 // coefficient): a triangle found in group h, partner l, element w adds one
-// to t(h), t(l) and t(w).  t(h) is summed over the group, t(l) per word
+// to t(h), t(l) and t(w).  t(h) is summed over the group, t(l) per block
 // (shared counters per partner) and t(w) in a counter beside w's hash slot,
 // so global atomics scale with the number of forward edges, not with the
 // number of triangles.
@@ -38,7 +38,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kGroupChunk = 8;  // warp groups per atomic
 constexpr int kMinChunk = 8;    // fewest partners a warp of a CTA group claims
-constexpr int kWindows = 4;     // words per lane loaded before probing
+constexpr int kWindows = 4;     // 16-byte words per lane loaded before probing (two blocks)
 constexpr int kBigWindows = 4;  // ... in the long-list kernel
 
 // Main kernel: 256-thread CTAs; one table per CTA for CTA groups (lists of
@@ -123,7 +123,7 @@ __device__ __forceinline__ void red_add_if(uint32_t saddr, uint32_t v, bool c) {
 // lists r = 0 .. k-1 in flat order.
 struct WarpScratch {
   union {
-    int2 bn[32];  // word mode: {col4 word of flat position 0 of list r, flat start of r+1}
+    int2 bn[32];  // block mode: {col4 word of flat position 0 of list r, flat start of r+1}
     struct {
       long long eb[32];   // element mode: col4 element of flat position 0 of list r
       int32_t enext[32];  // element mode: flat start of list r+1
@@ -251,7 +251,7 @@ __device__ __forceinline__ void ld_block(const int32_t *col4, int32_t a, int32_t
       : "l"(col4 + 4 * (size_t)a));
 }
 
-// Word mode of probe_chunk: windows w .. w+NQ-1 of 32 blocks (64 words) of
+// Block mode of probe_chunk: windows w .. w+NQ-1 of 32 blocks (64 words) of
 // the chunk's flat sequence, lane p taking block p of each.  Lists occupy
 // whole blocks, so a block lies in one list: the number of lists ending at
 // or before it, i.e. those ending at or before the window (one vote) plus
@@ -302,10 +302,10 @@ __device__ __forceinline__ void probe_windows(const Lists &g, int32_t w, int32_t
 //    ends, with no per-lane cursor and no branch;
 //  * elements: a position is one list entry (one 4-byte load); lane p takes
 //    positions p, p+32, ... with a cursor on the list holding its position.
-//    For chunks of a few short lists, where whole words would be mostly
+//    For chunks of a few short lists, where whole blocks would be mostly
 //    padding.
 // Matches are counted in registers; per partner they go to a shared counter
-// (per word, or when an element-mode lane leaves the partner's list), per w
+// (per block, or when an element-mode lane leaves the partner's list), per w
 // to the counter beside w's slot.
 template <bool PV, int W>
 __device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__restrict__ part,
@@ -331,11 +331,11 @@ __device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__res
   const int32_t total_v = __shfl_sync(kFull, incl_v, 31);
   // a block step probes eight entries, an element step one: cost ~4:1
   // (measured: 4 beats 5 and 7 on R-MAT and random geometric graphs)
-  const bool words = 4 * ((total_v + 63) >> 6) < ((total_e + 31) >> 5);
+  const bool blocks = 4 * ((total_v + 63) >> 6) < ((total_e + 31) >> 5);
   // list r+1 starts where list r ends (empty lists add nothing to the scans)
   const bool last = rank == k - 1;
   if (dl > 0) {
-    if (words) {
+    if (blocks) {
       ws.bn[rank] = make_int2(vb - (incl_v - nv), last ? INT32_MAX : incl_v);
     } else {
       ws.eb[rank] = 4ll * vb - (incl_e - dl);
@@ -351,7 +351,7 @@ __device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__res
   uint32_t run = 0;    // matches of this lane in list run_r not yet in ws.lc
   int run_r = 0;
   const uint32_t lc_sa = shared_addr(ws.lc);
-  if (words) {
+  if (blocks) {
     // lane r holds list r's base and end (flat start of list r+1)
     const int2 bn_r = lane < k ? ws.bn[lane] : make_int2(0, INT32_MAX);
     const int32_t full = total_v >> 6;  // windows of 64 words inside the sequence
