@@ -171,11 +171,15 @@ def test_invalid_arguments(tc):
     assert lib.tc_last_error() == tc.TC_ERR_INVALID_ARG
 
 
-@pytest.mark.parametrize("row", [0, 1, 2, 31, 32, 33, 64, 255, 256, 257, 1000])
+@pytest.mark.parametrize("row", [0, 1, 2, 7, 8, 9, 15, 16, 17, 31, 32, 33, 64, 127, 128, 129,
+                                 255, 256, 257, 1000, 1024, 1025])
 def test_row_lengths(tc, row):
     """A vertex whose forward list has exactly `row` entries: a clique on
     row+1 vertices (equal degrees, so the lowest id owns the longest list)
-    plus a path and a star that add no triangle."""
+    plus a path and a star that add no triangle.  The lengths straddle the
+    32-byte blocks the lists are padded to (8 entries), the warp-group limit
+    (128) and the CTA-group limit (1024, past which the long-list kernel
+    takes the group)."""
     s, d, n = fam.disjoint_union(fam.complete(row + 1), fam.path(50), fam.star(40))
     r = assert_same(tc, s, d, n, check_total_only=False)
     assert r["max_out_degree"] == max(row, 1)
@@ -183,8 +187,9 @@ def test_row_lengths(tc, row):
 
 @pytest.mark.parametrize("row", [4096, 4097, 5000])
 def test_long_rows_closed_form(tc, row):
-    """Rows past 4096 entries use a half-loaded CTA table; a clique on k
-    vertices has C(k,3) triangles and C(k-1,2) at every vertex."""
+    """Rows of 4096 entries fill half the long-list kernel's table; longer
+    ones are hashed in two segments.  A clique on k vertices has C(k,3)
+    triangles and C(k-1,2) at every vertex."""
     k = row + 1
     s, d, n = fam.disjoint_union(fam.complete(k), fam.path(50), fam.star(40))
     T, t, deg = run_pv(tc, s, d, n)
@@ -194,8 +199,9 @@ def test_long_rows_closed_form(tc, row):
 
 
 def test_long_row_global_fallback(tc):
-    """K_8200: the lowest ids own forward lists longer than 8192, which are
-    probed with a binary search in global memory.  T = C(n,3) exactly."""
+    """K_8200: the lowest ids own forward lists longer than 8192 entries,
+    hashed in three segments, each probed by every partner.  T = C(n,3)
+    exactly."""
     n = 8200
     s, d, n = fam.complete(n)
     T, t, deg = run_pv(tc, s, d, n)
