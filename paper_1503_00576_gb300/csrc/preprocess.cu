@@ -213,33 +213,48 @@ k_canon(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, uint32
 // ---------------------------------------------------------------------------
 // one LSD radix pass (8-bit digit at `shift`), onesweep style
 // ---------------------------------------------------------------------------
+struct RadixShared {
+  uint64_t keys[kSortTile];                 // the tile, staged in digit order
+  uint32_t whist[kSortThreads / 32][256];   // per warp and digit: count, then first position
+  uint32_t gbase[256];                      // per digit: output position of staged index 0
+  uint32_t scratch[32];
+  uint32_t tile;
+};
+
+// Writes one staged key to its output position (and, for the column pass,
+// its row and the out-degree of its owner).
 template <int MODE>
-__global__ void __launch_bounds__(kSortThreads, 4)
-k_radix_pass(const uint64_t *__restrict__ in, void *__restrict__ out, uint32_t n_keys_bound,
-             const uint32_t *__restrict__ n_keys_dev, int shift, uint32_t col_mask,
-             uint32_t *__restrict__ row_out, int owner_shift, int32_t *outdeg,
-             const uint32_t *__restrict__ hist, unsigned long long *__restrict__ status,
-             uint32_t *ticket, Ctrl *ctrl) {
+__device__ __forceinline__ void radix_out(uint64_t key, uint32_t pos, void *__restrict__ out,
+                                          uint32_t col_mask, uint32_t *__restrict__ row_out,
+                                          int owner_shift, int32_t *outdeg, uint32_t active) {
+  if (MODE == kOutColRow) {
+    const uint32_t owner = (uint32_t)(key >> owner_shift);
+    ((uint32_t *)out)[pos] = (uint32_t)key & col_mask;
+    if (row_out) row_out[pos] = owner;
+    // the staged tile is in owner order: consecutive lanes share owners,
+    // and one atomic per run gives the out-degrees (the node array's counts)
+    const uint32_t peers = __match_any_sync(active, owner);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&outdeg[owner], __popc(peers));
+  } else if (MODE == kOutRank) {
+    ((uint32_t *)out)[(uint32_t)key & col_mask] = pos;
+  } else {
+    ((uint64_t *)out)[pos] = key;
+  }
+}
+
+// One tile of a pass.  FULL: all TILE keys of the tile exist (every tile but
+// the last), so no key needs a bounds test.
+template <int MODE, bool FULL>
+__device__ __forceinline__ void radix_tile(RadixShared &S, const uint64_t *__restrict__ in,
+                                           void *__restrict__ out, uint32_t n_keys,
+                                           uint32_t tile, uint32_t gofs, int shift,
+                                           uint32_t col_mask, uint32_t *__restrict__ row_out,
+                                           int owner_shift, int32_t *outdeg,
+                                           unsigned long long *__restrict__ status, Ctrl *ctrl) {
   constexpr int WARPS = kSortThreads / 32, KPT = kSortKeysPerThread, TILE = kSortTile;
-  __shared__ uint64_t s_keys[TILE];
-  __shared__ uint32_t s_whist[WARPS][256];
-  __shared__ uint32_t s_tile_start[256];
-  __shared__ uint32_t s_gbase[256];
-  __shared__ uint32_t s_scratch[32];
-  __shared__ uint32_t s_tile;
-
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t n_keys = n_keys_dev ? *n_keys_dev : n_keys_bound;
-  if (tid == 0) s_tile = atomicAdd(ticket, 1u);
-  for (int i = tid; i < WARPS * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0;
-  __syncthreads();
-  const uint32_t tile = s_tile;
   const uint32_t tile_base = tile * (uint32_t)TILE;
-  if (tile_base >= n_keys) return;  // uniform for the block
-
-  // global start of every digit: exclusive scan of the pass histogram
-  uint32_t dummy;
-  const uint32_t gofs = scan256_exclusive(hist[tid], s_scratch, &dummy);
+  const uint32_t first = tile_base + (uint32_t)(warp * 32 * KPT + lane);  // key i: first + 32 i
 
   // ---- rank keys within the tile (stable: warp-major, round-major, lane) ----
   // All 16 keys of a thread are loaded before ranking starts, and the
@@ -248,54 +263,58 @@ k_radix_pass(const uint64_t *__restrict__ in, void *__restrict__ out, uint32_t n
   // keys spill to L1.
   const uint32_t lt_mask = (1u << lane) - 1u;
   uint64_t k[KPT];
-  uint32_t rk[KPT];
+  uint32_t pk[KPT];  // digit << 16 | rank among the warp's keys of that digit
+#pragma unroll
+  for (int i = 0; i < KPT; ++i)
+    k[i] = (FULL || first + 32u * i < n_keys) ? __ldg(in + first + 32u * i) : 0ull;
 #pragma unroll
   for (int i = 0; i < KPT; ++i) {
-    const uint32_t idx = tile_base + (uint32_t)(warp * 32 * KPT + i * 32 + lane);
-    k[i] = idx < n_keys ? __ldg(in + idx) : 0ull;
-  }
-#pragma unroll
-  for (int i = 0; i < KPT; ++i) {
-    const uint32_t idx = tile_base + (uint32_t)(warp * 32 * KPT + i * 32 + lane);
-    const bool valid = idx < n_keys;
+    const bool valid = FULL || first + 32u * i < n_keys;
     const uint32_t d = (uint32_t)(k[i] >> shift) & 255u;
-    uint32_t peers = __ballot_sync(kFull, valid);
+    uint32_t peers = FULL ? kFull : __ballot_sync(kFull, valid);
 #pragma unroll
     for (int bit = 0; bit < 8; ++bit) {
       const uint32_t bb = __ballot_sync(kFull, (d >> bit) & 1u);
-      peers &= ((d >> bit) & 1u) ? bb : ~bb;
+      peers &= bb ^ (((d >> bit) & 1u) - 1u);  // bb where bit is set, else ~bb
     }
-    const uint32_t before = s_whist[warp][d];
-    rk[i] = before + __popc(peers & lt_mask);
+    const uint32_t below = __popc(peers & lt_mask);  // 0: the first lane of its digit
+    const uint32_t before = S.whist[warp][d];
     __syncwarp();
-    if (valid && lane == __ffs(peers) - 1) s_whist[warp][d] = before + __popc(peers);
+    if (valid && below == 0) S.whist[warp][d] = before + __popc(peers);
     __syncwarp();
+    pk[i] = (d << 16) | (before + below);
   }
   __syncthreads();
 
-  // ---- per digit: warp offsets, tile offsets, global offsets ----
+  // ---- per digit (thread tid): tile count, published at once; tile offset
+  // and warp offsets; then the keys are staged, sorted by digit, before the
+  // look-back waits on the tiles before this one ----
+  unsigned long long *st = status + (size_t)tile * 256 + tid;
   uint32_t tile_cnt = 0;
+#pragma unroll
+  for (int w = 0; w < WARPS; ++w) tile_cnt += S.whist[w][tid];
+  st_volatile_u64(st, (tile == 0 ? kFlagInclusive : kFlagAggregate) | tile_cnt);
+  uint32_t tile_total;
+  const uint32_t tstart = scan256_exclusive(tile_cnt, S.scratch, &tile_total);
   {
-    uint32_t run = 0;
+    // staged position of the first key of warp w with this digit
+    uint32_t run = tstart;
 #pragma unroll
     for (int w = 0; w < WARPS; ++w) {
-      const uint32_t c = s_whist[w][tid];
-      s_whist[w][tid] = run;
+      const uint32_t c = S.whist[w][tid];
+      S.whist[w][tid] = run;
       run += c;
     }
-    tile_cnt = run;
   }
-  uint32_t tile_total;
-  const uint32_t tstart = scan256_exclusive(tile_cnt, s_scratch, &tile_total);
-  s_tile_start[tid] = tstart;
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < KPT; ++i)
+    if (FULL || first + 32u * i < n_keys)
+      S.keys[S.whist[warp][pk[i] >> 16] + (pk[i] & 0xffffu)] = k[i];
   {
     // decoupled look-back for this digit
-    unsigned long long *st = status + (size_t)tile * 256 + tid;
     uint64_t excl = 0;
-    if (tile == 0) {
-      st_volatile_u64(st, kFlagInclusive | tile_cnt);
-    } else {
-      st_volatile_u64(st, kFlagAggregate | tile_cnt);
+    if (tile > 0) {
       int64_t j = (int64_t)tile - 1;
       uint32_t spins = 0;
       while (j >= 0) {
@@ -315,42 +334,58 @@ k_radix_pass(const uint64_t *__restrict__ in, void *__restrict__ out, uint32_t n
       }
       st_volatile_u64(st, kFlagInclusive | (excl + tile_cnt));
     }
-    // output position of the tile-local sorted index i with digit d is
-    // s_gbase[d] + i (mod 2^32 arithmetic; the result is < 2^31)
-    s_gbase[tid] = gofs + (uint32_t)excl - tstart;
-  }
-  __syncthreads();
-
-  // ---- stage in shared memory, sorted by digit ----
-#pragma unroll
-  for (int i = 0; i < KPT; ++i) {
-    const uint32_t idx = tile_base + (uint32_t)(warp * 32 * KPT + i * 32 + lane);
-    if (idx < n_keys) {
-      const uint32_t d = (uint32_t)(k[i] >> shift) & 255u;
-      s_keys[s_tile_start[d] + s_whist[warp][d] + rk[i]] = k[i];
-    }
+    // output position of the staged index i with digit d is s_gbase[d] + i
+    // (mod 2^32 arithmetic; the result is < 2^31)
+    S.gbase[tid] = gofs + (uint32_t)excl - tstart;
   }
   __syncthreads();
 
   // ---- scatter: consecutive threads write consecutive positions of a run ----
-  const uint32_t tile_n = min((uint32_t)TILE, n_keys - tile_base);
-  for (uint32_t i = tid; i < tile_n; i += kSortThreads) {
-    const uint64_t key = s_keys[i];
-    const uint32_t pos = s_gbase[(uint32_t)(key >> shift) & 255u] + i;
-    if (MODE == kOutColRow) {
-      const uint32_t owner = (uint32_t)(key >> owner_shift);
-      ((uint32_t *)out)[pos] = (uint32_t)key & col_mask;
-      if (row_out) row_out[pos] = owner;
-      // the staged tile is in owner order: consecutive lanes share owners,
-      // and one atomic per run gives the out-degrees (the node array's counts)
-      const uint32_t peers = __match_any_sync(__activemask(), owner);
-      if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&outdeg[owner], __popc(peers));
-    } else if (MODE == kOutRank) {
-      ((uint32_t *)out)[(uint32_t)key & col_mask] = pos;
-    } else {
-      ((uint64_t *)out)[pos] = key;
+  if (FULL) {
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+      const uint32_t i = (uint32_t)(tid + j * kSortThreads);
+      const uint64_t key = S.keys[i];
+      radix_out<MODE>(key, S.gbase[(uint32_t)(key >> shift) & 255u] + i, out, col_mask, row_out,
+                      owner_shift, outdeg, kFull);
+    }
+  } else {
+    const uint32_t tile_n = n_keys - tile_base;
+    for (uint32_t i = tid; i < tile_n; i += kSortThreads) {
+      const uint64_t key = S.keys[i];
+      radix_out<MODE>(key, S.gbase[(uint32_t)(key >> shift) & 255u] + i, out, col_mask, row_out,
+                      owner_shift, outdeg, __activemask());
     }
   }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kSortThreads, 4)
+k_radix_pass(const uint64_t *__restrict__ in, void *__restrict__ out, uint32_t n_keys_bound,
+             const uint32_t *__restrict__ n_keys_dev, int shift, uint32_t col_mask,
+             uint32_t *__restrict__ row_out, int owner_shift, int32_t *outdeg,
+             const uint32_t *__restrict__ hist, unsigned long long *__restrict__ status,
+             uint32_t *ticket, Ctrl *ctrl) {
+  constexpr int WARPS = kSortThreads / 32, TILE = kSortTile;
+  __shared__ RadixShared S;
+  const int tid = threadIdx.x;
+  const uint32_t n_keys = n_keys_dev ? *n_keys_dev : n_keys_bound;
+  if (tid == 0) S.tile = atomicAdd(ticket, 1u);
+  for (int i = tid; i < WARPS * 256; i += kSortThreads) (&S.whist[0][0])[i] = 0;
+  __syncthreads();
+  const uint32_t tile = S.tile;
+  const uint32_t tile_base = tile * (uint32_t)TILE;
+  if (tile_base >= n_keys) return;  // uniform for the block
+
+  // global start of every digit: exclusive scan of the pass histogram
+  uint32_t dummy;
+  const uint32_t gofs = scan256_exclusive(hist[tid], S.scratch, &dummy);
+  if (n_keys - tile_base >= (uint32_t)TILE)
+    radix_tile<MODE, true>(S, in, out, n_keys, tile, gofs, shift, col_mask, row_out, owner_shift,
+                           outdeg, status, ctrl);
+  else
+    radix_tile<MODE, false>(S, in, out, n_keys, tile, gofs, shift, col_mask, row_out,
+                            owner_shift, outdeg, status, ctrl);
 }
 
 // ---------------------------------------------------------------------------
