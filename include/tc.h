@@ -124,12 +124,16 @@ tc_status tc_clustering(const int64_t *t, const int32_t *deg, int32_t n, tc_stre
 
 /*
  * Host-buffer variants: the same computations as tc_count /
- * tc_count_per_vertex with inputs and outputs in HOST memory.  The copies
- * are part of the call: the edge array is copied to the device, counted on
- * a stream private to the calling thread, and the results are copied back
- * before return (the paper's end-to-end timing, Sec. IV, covers the same
- * span).  Page-locked host buffers transfer fastest; pageable ones work.
- * Both synchronise.
+ * tc_count_per_vertex with inputs and outputs in HOST memory.  The
+ * transfers are part of the call: the edge array moves to the device, is
+ * counted on a stream private to the calling thread, and the results are
+ * copied back before return (the paper's end-to-end timing, Sec. IV, covers
+ * the same span).  Where the device reads host memory through the host's
+ * page tables (Grace), the first kernel reads src_host and dst_host in
+ * place, once each, instead of a copy to device memory first; elsewhere
+ * they are copied (page-locked buffers transfer fastest; pageable ones
+ * work).  The caller must not modify the inputs during the call.  Both
+ * synchronise.
  *   src_host, dst_host  host int32[m]
  *   t_host              host int64[n] (required when n > 0)
  *   deg_host            host int32[n] or NULL

@@ -22,6 +22,7 @@ namespace tc {
 namespace {
 
 constexpr int kGroupThreads = 256;
+constexpr int kGroupUnroll = 4;
 
 // heavy_ratio_pct = 100: the longer list is always the one hashed; larger
 // values keep an edge at its owner unless v's list is that much longer.
@@ -54,18 +55,38 @@ k_group_keys(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
   __syncthreads();
   const uint32_t m = ctrl->m;
   const uint32_t stride = gridDim.x * kGroupThreads;
-  for (uint32_t e = blockIdx.x * kGroupThreads + threadIdx.x; e < m; e += stride) {
-    const int32_t u = __ldg(row + e), v = __ldg(col + e);
-    const int32_t ub = __ldg(off + u), ue = __ldg(off + u + 1);
-    const int32_t vd = __ldg(off + v + 1) - __ldg(off + v);
-    int32_t h, l;
-    split_edge(u, v, ue - ub, vd, heavy_ratio_pct, h, l);
-    gkeys[e] = ((uint64_t)(uint32_t)h << b) | (uint32_t)l;
-    for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p * 256 + ((h >> (8 * p)) & 255)], 1u);
-    int32_t *dst = col4 + 4 * (size_t)__ldg(voff + u);
-    dst[(int32_t)e - ub] = v;
-    if ((int32_t)e == ue - 1)  // the list's last entry pads its word
-      for (int32_t j = ue - ub; j & 7; ++j) dst[j] = -1;
+  // kGroupUnroll edges per thread per round, each step's loads issued for
+  // all of them together: the offsets are gathers that depend on the edge
+  for (uint32_t e0 = blockIdx.x * kGroupThreads + threadIdx.x; e0 < m;
+       e0 += kGroupUnroll * stride) {
+    int32_t u[kGroupUnroll], v[kGroupUnroll];
+#pragma unroll
+    for (int q = 0; q < kGroupUnroll; ++q) {
+      const uint32_t e = e0 + q * stride;
+      u[q] = e < m ? __ldg(row + e) : 0;
+      v[q] = e < m ? __ldg(col + e) : 0;
+    }
+    int32_t ub[kGroupUnroll], ue[kGroupUnroll], vd[kGroupUnroll], vw[kGroupUnroll];
+#pragma unroll
+    for (int q = 0; q < kGroupUnroll; ++q) {
+      ub[q] = __ldg(off + u[q]);
+      ue[q] = __ldg(off + u[q] + 1);
+      vd[q] = __ldg(off + v[q] + 1) - __ldg(off + v[q]);
+      vw[q] = __ldg(voff + u[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < kGroupUnroll; ++q) {
+      const uint32_t e = e0 + q * stride;
+      if (e >= m) break;
+      int32_t h, l;
+      split_edge(u[q], v[q], ue[q] - ub[q], vd[q], heavy_ratio_pct, h, l);
+      gkeys[e] = ((uint64_t)(uint32_t)h << b) | (uint32_t)l;
+      for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p * 256 + ((h >> (8 * p)) & 255)], 1u);
+      int32_t *dst = col4 + 4 * (size_t)vw[q];
+      dst[(int32_t)e - ub[q]] = v[q];
+      if ((int32_t)e == ue[q] - 1)  // the list's last entry pads its word
+        for (int32_t j = ue[q] - ub[q]; j & 7; ++j) dst[j] = -1;
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < passes * 256; i += kGroupThreads)

@@ -154,6 +154,7 @@ __device__ uint64_t lookback_warp(unsigned long long *status, uint32_t tile, uin
 // canon: validate, drop loops, undirected 64-bit keys, digit histograms
 // ---------------------------------------------------------------------------
 constexpr int kCanonThreads = 256;
+constexpr int kCanonUnroll = 4;
 
 __global__ void __launch_bounds__(kCanonThreads)
 k_canon(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, uint32_t m_in,
@@ -176,34 +177,49 @@ k_canon(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, uint32
   if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->m_in = m_real;
   bool bad = false;
   const uint32_t stride = gridDim.x * kCanonThreads;
-  // pairs past m_real are batch padding: not keyed, not sorted
-  for (uint32_t i = blockIdx.x * kCanonThreads + threadIdx.x; i < m_real; i += stride) {
-    int32_t u = __ldg(src + i), v = __ldg(dst + i);
-    int32_t lim = n, shift = 0, lo_graph = 0;
-    if (batch) {
-      int32_t lo = 0, hi = ng;  // the last graph g with eo[g] <= i
-      while (hi - lo > 1) {
-        const int32_t mid = (lo + hi) >> 1;
-        if ((uint32_t)__ldg(eo + mid) <= i) lo = mid; else hi = mid;
+  // pairs past m_real are batch padding: not keyed, not sorted.  The pairs
+  // of kCanonUnroll rounds are loaded before any is keyed: the inputs may be
+  // host memory read in place, where each load waits a long time.
+  for (uint32_t i0 = blockIdx.x * kCanonThreads + threadIdx.x; i0 < m_real;
+       i0 += kCanonUnroll * stride) {
+    int32_t us[kCanonUnroll], vs[kCanonUnroll];
+#pragma unroll
+    for (int q = 0; q < kCanonUnroll; ++q) {
+      const uint32_t i = i0 + q * stride;
+      us[q] = i < m_real ? __ldg(src + i) : 0;
+      vs[q] = i < m_real ? __ldg(dst + i) : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < kCanonUnroll; ++q) {
+      const uint32_t i = i0 + q * stride;
+      if (i >= m_real) break;
+      const int32_t u = us[q], v = vs[q];
+      int32_t lim = n, shift = 0, lo_graph = 0;
+      if (batch) {
+        int32_t lo = 0, hi = ng;  // the last graph g with eo[g] <= i
+        while (hi - lo > 1) {
+          const int32_t mid = (lo + hi) >> 1;
+          if ((uint32_t)__ldg(eo + mid) <= i) lo = mid; else hi = mid;
+        }
+        lo_graph = lo;
+        shift = __ldg(vo + lo);
+        lim = __ldg(vo + lo + 1) - shift;
       }
-      lo_graph = lo;
-      shift = __ldg(vo + lo);
-      lim = __ldg(vo + lo + 1) - shift;
+      uint64_t key;
+      if ((uint32_t)u >= (uint32_t)lim || (uint32_t)v >= (uint32_t)lim) {
+        // a batch fails only the graph that holds the pair; the pair is dropped
+        // so the other graphs of the union are counted exactly
+        if (batch) batch->gerr[lo_graph] = 1; else bad = true;
+        key = sentinel;
+      } else if (u == v) {
+        key = sentinel;  // self-loop: sorts last, dropped with the sentinels
+      } else {
+        const uint32_t lo = (uint32_t)(min(u, v) + shift), hi = (uint32_t)(max(u, v) + shift);
+        key = ((uint64_t)lo << b) | hi;
+      }
+      keys[i] = key;
+      for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * 256 + ((key >> (8 * p)) & 255)], 1u);
     }
-    uint64_t key;
-    if ((uint32_t)u >= (uint32_t)lim || (uint32_t)v >= (uint32_t)lim) {
-      // a batch fails only the graph that holds the pair; the pair is dropped
-      // so the other graphs of the union are counted exactly
-      if (batch) batch->gerr[lo_graph] = 1; else bad = true;
-      key = sentinel;
-    } else if (u == v) {
-      key = sentinel;  // self-loop: sorts last, dropped with the sentinels
-    } else {
-      const uint32_t lo = (uint32_t)(min(u, v) + shift), hi = (uint32_t)(max(u, v) + shift);
-      key = ((uint64_t)lo << b) | hi;
-    }
-    keys[i] = key;
-    for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * 256 + ((key >> (8 * p)) & 255)], 1u);
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctrl->err, kErrIdRange);
   for (int i = threadIdx.x; i < passes * 256; i += kCanonThreads)

@@ -427,7 +427,25 @@ tc_status count_impl(const int32_t *src, const int32_t *dst, int64_t m, int32_t 
   return keep;
 }
 
-// Host-buffer driver: copy in, count, copy out, on a private stream.
+// Whether a kernel may read any host buffer in place: true where the device
+// reads pageable memory through the host's page tables (address translation
+// services, as on Grace), false elsewhere (then inputs are copied in).
+bool kernels_read_host_memory() {
+  static const bool yes = [] {
+    int dev = 0, pageable = 0, page_tables = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&page_tables, cudaDevAttrPageableMemoryAccessUsesHostPageTables,
+                               dev) != cudaSuccess)
+      return false;
+    return pageable == 1 && page_tables == 1;
+  }();
+  return yes;
+}
+
+// Host-buffer driver: copy in, count, copy out, on a private stream.  Only
+// the first kernel reads the input pairs, once each, so where kernels can
+// read host memory the pairs are read in place instead of copied first.
 tc_status host_impl(const int32_t *src_h, const int32_t *dst_h, int64_t m, int32_t n,
                     int64_t *t_h, int32_t *deg_h, uint64_t *total, bool per_vertex) {
   tc_status s = check_args(src_h, dst_h, m, n);
@@ -439,7 +457,8 @@ tc_status host_impl(const int32_t *src_h, const int32_t *dst_h, int64_t m, int32
   const size_t in_bytes = sizeof(int32_t) * (size_t)m;
   int32_t *d_src = nullptr, *d_dst = nullptr, *d_deg = nullptr;
   int64_t *d_t = nullptr;
-  if (m > 0) {
+  const bool in_place = kernels_read_host_memory();
+  if (m > 0 && !in_place) {
     TC_CUDA(cudaMallocAsync((void **)&d_src, in_bytes, st), "input allocation");
     TC_CUDA(cudaMallocAsync((void **)&d_dst, in_bytes, st), "input allocation");
     TC_CUDA(cudaMemcpyAsync(d_src, src_h, in_bytes, cudaMemcpyHostToDevice, st), "copy in");
@@ -451,7 +470,8 @@ tc_status host_impl(const int32_t *src_h, const int32_t *dst_h, int64_t m, int32
       TC_CUDA(cudaMallocAsync((void **)&d_deg, sizeof(int32_t) * (size_t)n, st), "deg allocation");
   }
   uint64_t T = 0;
-  s = count_impl(d_src, d_dst, m, n, st, nullptr, 0, per_vertex ? d_t : nullptr, d_deg, &T);
+  s = count_impl(in_place ? src_h : d_src, in_place ? dst_h : d_dst, m, n, st, nullptr, 0,
+                 per_vertex ? d_t : nullptr, d_deg, &T);
   if (s == TC_OK && per_vertex && n > 0) {
     cudaError_t e = cudaMemcpyAsync(t_h, d_t, sizeof(int64_t) * (size_t)n,
                                     cudaMemcpyDeviceToHost, st);

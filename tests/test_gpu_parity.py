@@ -247,6 +247,29 @@ def test_host_buffers(tc):
     assert T == r["T"] and np.array_equal(t, r["t"]) and np.array_equal(deg, r["deg"])
 
 
+def test_host_buffers_pinned_and_bad_ids(tc):
+    """Page-locked inputs and outputs (the bench's end-to-end call), a ragged
+    pair count, and an id out of range reported through the host call."""
+    import torch
+    import graphgen
+
+    s, d = graphgen.rmat(16, (16 << 16) + 13, 62)
+    n = 1 << 16
+    r = oracle.forward(s, d, n)
+    hs, hd = torch.from_numpy(s).pin_memory(), torch.from_numpy(d).pin_memory()
+    ht = torch.empty(n, dtype=torch.int64).pin_memory()
+    hdeg = torch.empty(n, dtype=torch.int32).pin_memory()
+    assert tc.tc_count_host(hs, hd, n) == r["T"]
+    T, _, _ = tc.tc_count_per_vertex_host(hs, hd, n, t_out=ht, deg_out=hdeg)
+    assert T == r["T"]
+    assert np.array_equal(ht.numpy(), r["t"]) and np.array_equal(hdeg.numpy(), r["deg"])
+    bad = d.copy()
+    bad[len(bad) // 2] = n
+    with pytest.raises(tc.TCError) as e:
+        tc.tc_count_host(s, bad, n)
+    assert e.value.code == tc.TC_ERR_ID_RANGE
+
+
 def test_caller_workspace(tc):
     import torch
     import graphgen
