@@ -107,20 +107,21 @@ __device__ __forceinline__ uint32_t block_scan_exclusive(uint32_t x, uint32_t *s
 }
 
 // Decoupled look-back for one running sum, by one warp.  Publishes the
-// tile's aggregate, then reads the statuses of 32 predecessors at once (lane
+// tile's aggregate (unless the caller already did: `published`, see
+// publish_aggregate), then reads the statuses of 32 predecessors at once (lane
 // k reads tile j - k): once all 32 have published something, it adds the
 // values up to the nearest inclusive prefix, or all 32 and moves on; so a
 // walk back over many tiles costs one memory latency per 32 tiles.
 // Publishes the tile's inclusive prefix and returns the exclusive one (in
 // every lane).  All 32 lanes of the warp must call it.
 __device__ uint64_t lookback_warp(unsigned long long *status, uint32_t tile, uint64_t agg,
-                                  Ctrl *ctrl) {
+                                  Ctrl *ctrl, bool published = false) {
   const int lane = threadIdx.x & 31;
   if (tile == 0) {
-    if (lane == 0) st_volatile_u64(&status[0], kFlagInclusive | agg);
+    if (lane == 0 && !published) st_volatile_u64(&status[0], kFlagInclusive | agg);
     return 0;
   }
-  if (lane == 0) st_volatile_u64(&status[tile], kFlagAggregate | agg);
+  if (lane == 0 && !published) st_volatile_u64(&status[tile], kFlagAggregate | agg);
   uint64_t excl = 0;
   int64_t j = (int64_t)tile - 1;
   uint32_t spins = 0;
@@ -148,6 +149,14 @@ __device__ uint64_t lookback_warp(unsigned long long *status, uint32_t tile, uin
   }
   if (lane == 0) st_volatile_u64(&status[tile], kFlagInclusive | (excl + agg));
   return excl;
+}
+
+// The first half of lookback_warp, for a tile whose aggregate is known
+// before the rest of its work: successors can sum past it sooner.  Called
+// by one thread.
+__device__ __forceinline__ void publish_aggregate(unsigned long long *status, uint32_t tile,
+                                                  uint64_t agg) {
+  st_volatile_u64(&status[tile], (tile == 0 ? kFlagInclusive : kFlagAggregate) | agg);
 }
 
 // ---------------------------------------------------------------------------
@@ -505,6 +514,11 @@ k_orient(const uint64_t *__restrict__ keys, int b,
     flags |= (uint32_t)keep << i;
     cnt += keep;
   }
+  // the tile's count is published before the gathers below, so that the
+  // tiles after this one need not wait for them
+  uint32_t tile_cnt;
+  const uint32_t toff = block_scan_exclusive<kOrientThreads>(cnt, s_scratch, &tile_cnt);
+  if (tid == 0) publish_aggregate(status, tile, tile_cnt);
   // orient the kept keys now: the rank gathers of eight keys at a time are
   // issued together, and all of it overlaps the other tiles' look-backs
   constexpr int HALF = KPT / 2;
@@ -526,10 +540,8 @@ k_orient(const uint64_t *__restrict__ keys, int b,
           atomicAdd(&s_hist[p * 256 + ((owner >> (8 * p)) & 255u)], 1u);
     }
   }
-  uint32_t tile_cnt;
-  const uint32_t toff = block_scan_exclusive<kOrientThreads>(cnt, s_scratch, &tile_cnt);
   if (tid < 32) {
-    const uint64_t excl = lookback_warp(status, tile, tile_cnt, ctrl);
+    const uint64_t excl = lookback_warp(status, tile, tile_cnt, ctrl, true);
     if (tid == 0) {
       s_excl = (uint32_t)excl;
       if (tile_base + TILE >= m_in) ctrl->m = (uint32_t)(excl + tile_cnt);  // last tile
