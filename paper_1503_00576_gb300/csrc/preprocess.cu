@@ -485,6 +485,12 @@ k_orient(const uint64_t *__restrict__ keys, int b,
          const int32_t *__restrict__ rank, uint64_t *__restrict__ okeys,
          uint32_t *__restrict__ hist2, int passes2, unsigned long long *status, Ctrl *ctrl) {
   constexpr int KPT = kOrientKeysPerThread, TILE = kOrientTile;
+  static_assert(KPT == 16, "the swizzle below assumes rows of 16 keys");
+  // The tile passes through shared memory both ways: loaded and stored with
+  // coalesced accesses, read and written per thread as 16 consecutive keys.
+  // Row r of 16 keys has its columns XOR-ed with r mod 16, so that both
+  // the column-wise and the row-wise accesses of a warp spread over the banks.
+  __shared__ uint64_t s_buf[TILE];
   __shared__ uint32_t s_scratch[32];
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_excl;
@@ -500,15 +506,22 @@ k_orient(const uint64_t *__restrict__ keys, int b,
   const uint64_t sentinel = (1ull << (2 * b)) - 1;
   const uint64_t mask = (1ull << b) - 1;
 
-  const uint32_t first = tile_base + (uint32_t)tid * KPT;
-  uint64_t k[KPT];
-  uint32_t flags = 0, cnt = 0;
-  uint64_t prev = (first > 0 && first <= m_in) ? __ldg(keys + first - 1) : sentinel;
-  if (first == 0) prev = ~0ull;  // differs from every key
+  auto swz = [](uint32_t j) { return (j & ~15u) | ((j ^ (j >> 4)) & 15u); };
 #pragma unroll
   for (int i = 0; i < KPT; ++i) {
-    const uint32_t idx = first + i;
-    k[i] = idx < m_in ? __ldg(keys + idx) : sentinel;
+    const uint32_t j = (uint32_t)(i * kOrientThreads + tid);
+    s_buf[swz(j)] = tile_base + j < m_in ? __ldg(keys + tile_base + j) : sentinel;
+  }
+  __syncthreads();
+  const uint32_t first = (uint32_t)tid * KPT;  // this thread's keys, within the tile
+  uint64_t k[KPT];
+  uint32_t flags = 0, cnt = 0;
+  uint64_t prev;
+  if (first > 0) prev = s_buf[swz(first - 1)];
+  else prev = tile_base > 0 ? __ldg(keys + tile_base - 1) : ~0ull;  // ~0 differs from every key
+#pragma unroll
+  for (int i = 0; i < KPT; ++i) {
+    k[i] = s_buf[swz(first + i)];
     const bool keep = k[i] != sentinel && k[i] != prev;
     prev = k[i];
     flags |= (uint32_t)keep << i;
@@ -540,6 +553,14 @@ k_orient(const uint64_t *__restrict__ keys, int b,
           atomicAdd(&s_hist[p * 256 + ((owner >> (8 * p)) & 255u)], 1u);
     }
   }
+  {
+    // the kept keys in tile order (the scan's barriers ordered all reads
+    // of the loaded tile before these writes)
+    uint32_t pos = toff;
+#pragma unroll
+    for (int i = 0; i < KPT; ++i)
+      if ((flags >> i) & 1u) s_buf[swz(pos++)] = k[i];
+  }
   if (tid < 32) {
     const uint64_t excl = lookback_warp(status, tile, tile_cnt, ctrl, true);
     if (tid == 0) {
@@ -548,10 +569,8 @@ k_orient(const uint64_t *__restrict__ keys, int b,
     }
   }
   __syncthreads();
-  uint32_t pos = s_excl + toff;
-#pragma unroll
-  for (int i = 0; i < KPT; ++i)
-    if ((flags >> i) & 1u) okeys[pos++] = k[i];
+  const uint32_t base = s_excl;
+  for (uint32_t j = tid; j < tile_cnt; j += kOrientThreads) okeys[base + j] = s_buf[swz(j)];
   __syncthreads();
   for (int i = tid; i < passes2 * 256; i += kOrientThreads)
     if (s_hist[i]) atomicAdd(&hist2[i], s_hist[i]);
