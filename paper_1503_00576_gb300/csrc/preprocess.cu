@@ -15,7 +15,10 @@
 //                  global digit offsets, shared-memory staging so that the
 //                  scatter writes runs of equal digits contiguously).
 //   unique+degree  after sort 1, equal keys are adjacent: the first of each
-//                  run is a distinct edge; degree histogram of those.
+//                  run is a distinct edge; degree histogram of those (the
+//                  higher endpoints are counted for every key by the sort-1
+//                  pass after which the keys are in their order, one atomic
+//                  per run, and repeated keys take their count back here).
 //   rank keys      the (degree, id) order of Sec. II-B as a permutation:
 //                  a stable radix sort of deg(v) << b | v whose last pass
 //                  scatters rank[v]; the rest of the pipeline runs on ranks.
@@ -262,6 +265,15 @@ __device__ __forceinline__ void radix_out(uint64_t key, uint32_t pos, void *__re
     if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&outdeg[owner], __popc(peers));
   } else if (MODE == kOutRank) {
     ((uint32_t *)out)[(uint32_t)key & col_mask] = pos;
+  } else if (MODE == kOutKeysDeg) {
+    // the staged tile is in order of the low field: equal higher endpoints
+    // sit in runs, one atomic per run (owner_shift holds b: the sentinel
+    // 2^(2b) - 1 counts nothing)
+    ((uint64_t *)out)[pos] = key;
+    const bool real = key != (1ull << (2 * owner_shift)) - 1;
+    const uint32_t hi = (uint32_t)key & col_mask;
+    const uint32_t peers = __match_any_sync(active, real ? hi : 0xffffffffu);
+    if (real && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&outdeg[hi], __popc(peers));
   } else {
     ((uint64_t *)out)[pos] = key;
   }
@@ -447,7 +459,9 @@ k_unique_degree(const uint64_t *__restrict__ keys, const Ctrl *__restrict__ ctrl
       const uint32_t a = (uint32_t)(key[q] >> b);
       const uint32_t peers = __match_any_sync(kFull, first ? a : 0xffffffffu) & firsts;
       if (first && lane == __ffs(peers) - 1) atomicAdd(&deg[a], __popc(peers));
-      if (first) atomicAdd(&deg[(uint32_t)(key[q] & mask)], 1);
+      // the higher endpoint was counted for every key by the sort pass that
+      // grouped the keys by it; a repeated key takes its count back
+      if (!first && key[q] != sentinel) atomicAdd(&deg[(uint32_t)(key[q] & mask)], -1);
     }
   }
 }
@@ -698,6 +712,10 @@ void launch_radix_pass(const uint64_t *in, void *out, RadixOut mode, uint32_t *r
     k_radix_pass<kOutRank><<<grid, kSortThreads, 0, st>>>(in, out, n_keys_bound, n_keys_dev,
                                                           shift, col_mask, nullptr, 0, nullptr,
                                                           hist, status, ticket, ctrl);
+  else if (mode == kOutKeysDeg)
+    k_radix_pass<kOutKeysDeg><<<grid, kSortThreads, 0, st>>>(
+        in, out, n_keys_bound, n_keys_dev, shift, col_mask, nullptr, owner_shift, outdeg, hist,
+        status, ticket, ctrl);
   else
     k_radix_pass<kOutKeys><<<grid, kSortThreads, 0, st>>>(in, out, n_keys_bound, n_keys_dev,
                                                           shift, col_mask, nullptr, 0, nullptr,

@@ -221,11 +221,16 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
 
   pt.start(TC_PHASE_SORT1);
   uint64_t *in = keys_a, *out = keys_b;
+  const uint32_t id_mask1 = (uint32_t)((1ull << b) - 1);
   for (int p = 0; p < passes1; ++p) {
     unsigned long long *status;
     uint32_t *ticket;
     next_pass(&status, &ticket);
-    launch_radix_pass(in, out, kOutKeys, nullptr, nullptr, m, &ctrl->m_in, 8 * p, 0u, 0,
+    // after pass hi_pass the keys are in order of their higher endpoint
+    // (the low b bits): that pass also counts it into deg
+    const bool hi_pass = p == (b + 7) / 8 - 1;
+    launch_radix_pass(in, out, hi_pass ? kOutKeysDeg : kOutKeys, nullptr, hi_pass ? deg : nullptr,
+                      m, &ctrl->m_in, 8 * p, hi_pass ? id_mask1 : 0u, hi_pass ? b : 0,
                       hist + 256 * p, status, ticket, ctrl, st);
     uint64_t *x = in;
     in = out;

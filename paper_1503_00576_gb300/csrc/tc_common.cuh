@@ -190,7 +190,9 @@ void launch_canon(const int32_t *src, const int32_t *dst, uint32_t m_in, int32_t
 // to `out`) plus the row array (key >> owner_shift, to `row_out`) with the
 // out-degrees added to `outdeg`; or the rank scatter rank[low bits] =
 // sorted position (to `out`).
-enum RadixOut { kOutKeys = 0, kOutColRow = 1, kOutRank = 2 };
+// kOutKeysDeg: keys out, and deg[key & col_mask] += 1 for every key but the
+// sentinel (the pass after which equal low fields are adjacent).
+enum RadixOut { kOutKeys = 0, kOutColRow = 1, kOutRank = 2, kOutKeysDeg = 3 };
 void launch_radix_pass(const uint64_t *in, void *out, RadixOut mode, uint32_t *row_out,
                        int32_t *outdeg, uint32_t n_keys_bound, const uint32_t *n_keys_dev,
                        int shift, uint32_t col_mask, int owner_shift, const uint32_t *hist,
