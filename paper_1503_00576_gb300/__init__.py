@@ -12,7 +12,7 @@ Functions mirror the C ABI names:
     tc_count(src, dst, n)                  -> T
     tc_count_per_vertex(src, dst, n)       -> (T, t int64[n], deg int32[n])
     tc_clustering(t, deg)                  -> (cc float64[n], transitivity)
-    tc_count_host(src, dst, n)             -> T          (numpy in, host copies timed inside)
+    tc_count_host(src, dst, n)             -> T          (host arrays in, transfers inside)
     tc_count_per_vertex_host(src, dst, n)  -> (T, t, deg) (numpy in and out)
     tc_workspace_bytes(m, n), tc_count_ws(src, dst, n, ws)
     tc_count_batch(src, dst, edge_offsets, vertex_counts) -> uint64[G]
@@ -283,8 +283,9 @@ def _host_i32(a):
 
 
 def tc_count_host(src, dst, n: int) -> int:
-    """T from HOST arrays (numpy int32 or pinned CPU tensors); the copies to
-    and from the device are part of the call."""
+    """T from HOST arrays (numpy int32 or pinned CPU tensors); the transfers
+    to and from the device are part of the call (where the device reads host
+    memory through the host's page tables, the inputs are read in place)."""
     s, d = _host_ptrs(src, dst)
     total = ctypes.c_uint64(0)
     _check(load_library().tc_count_host(s[1], d[1], s[2], n, ctypes.byref(total)))
