@@ -164,6 +164,17 @@ def batch_params(count: int, seed: int, log2_n=(8, 18), degree=(4.0, 64.0)):
     return n.astype(np.int32), m, kinds, seeds
 
 
+def batch_graph(count: int, seed: int, g: int, log2_n=(8, 18), degree=(4.0, 64.0)):
+    """Graph g of graph_batch(count, seed, ...) alone, as (src, dst, n):
+    the same sizes, seed and generator, without building the whole batch."""
+    n, m, kinds, seeds = batch_params(count, seed, log2_n, degree)
+    if kinds[g] == "er":
+        src, dst = er(int(n[g]), int(m[g]), seeds[g])
+    else:
+        src, dst = rmat_graph(int(n[g]), int(m[g]), seeds[g])
+    return src, dst, int(n[g])
+
+
 def graph_batch(count: int, seed: int, log2_n=(8, 18), degree=(4.0, 64.0),
                 threads: int = 0) -> GraphBatch:
     """Generate a batch of `count` graphs (in parallel; deterministic)."""

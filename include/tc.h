@@ -278,22 +278,31 @@ tc_status tc_count_work(const int32_t *src, const int32_t *dst, int64_t m, int32
  * It computes exactly what tc_count computes, on the caller's device
  * pointers and stream, but its scratch space is a static device array of
  * TC_NOALLOC_SCRATCH_BYTES bytes that is part of the library image: every
- * GPU that loads the library holds it until the process exits.  The call
- * allocates nothing (no cudaMalloc*, cudaFree*, pinned host buffers or
- * events).
+ * GPU on which it has been loaded holds it until the process exits.  The
+ * call itself allocates nothing (no cudaMalloc*, cudaFree*, pinned host
+ * buffers or events).
  *   src, dst   device int32[m], read-only
  *   total_out  HOST uint64, receives T
  * Returns TC_ERR_OVERFLOW, with a message stating the bytes needed, when
  * tc_workspace_bytes(m, n) exceeds TC_NOALLOC_SCRATCH_BYTES (about
  * 27 m + 88 n bytes: up to about 1.1 million pairs with n = 2^16).
- * Synchronises.
  *
- * The first call on a device looks up the array's device address on that
- * device (cudaGetSymbolAddress); make that first call before capturing any
- * stream.  All calls share the one array and it keeps the previous call's
- * contents (each call clears what must start at zero), so calls that
- * overlap on the GPU -- from two threads or on two streams -- race: order
- * them.
+ * First call on a device: under CUDA's lazy module loading (the default)
+ * the array and the library's kernels are loaded onto a device when they
+ * are first used there, i.e. by the first call on that device, so that
+ * call may take device memory (the 32 MiB array plus kernel code).  A caller
+ * that later reserves all device memory should make one call (on any small
+ * graph) at start-up first; with CUDA_MODULE_LOADING=EAGER they are loaded
+ * with the context instead.  If loading fails for lack of memory the call
+ * returns TC_ERR_OOM.
+ *
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress), synchronises `stream` and reads the result back
+ * with a plain copy, so it cannot be called while a stream is being
+ * captured into a CUDA graph.  All calls share the one array and it keeps
+ * the previous call's contents (each call clears what must start at zero),
+ * so calls that overlap on the GPU -- from two threads or on two streams --
+ * race: order them.
  */
 #define TC_NOALLOC_SCRATCH_BYTES (32u << 20)
 tc_status tc_count_noalloc(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,

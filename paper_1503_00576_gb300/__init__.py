@@ -45,7 +45,7 @@ TC_ERR_OVERFLOW = 6
 TC_COUNT_ERROR = (1 << 64) - 1
 PHASES = ("canon", "sort1", "degree", "rank", "orient", "sort2", "offsets", "groups", "count")
 
-# Every symbol include/tc.h declares.
+# Every symbol include/tc.h and include/tc_debug.h declare.
 EXPORTS = ("tc_count", "tc_count_per_vertex", "tc_count_part", "tc_count_per_vertex_part",
            "tc_clustering", "tc_count_host",
            "tc_count_per_vertex_host", "tc_workspace_bytes", "tc_count_ws", "tc_set_tuning",
@@ -53,7 +53,8 @@ EXPORTS = ("tc_count", "tc_count_per_vertex", "tc_count_part", "tc_count_per_ver
            "tc_engine_wait", "tc_engine_submit_parts", "tc_engine_poll", "tc_engine_count",
            "tc_engine_destroy", "tc_count_work", "tc_count_noalloc",
            "tc_last_error", "tc_status_string", "tc_last_error_detail", "tc_launch_count",
-           "tc_profile_enable", "tc_profile_read", "tc_phase_name")
+           "tc_profile_enable", "tc_profile_read", "tc_phase_name",
+           "tc_debug_set_wait_limit", "tc_debug_fail_allocations", "tc_debug_reset")
 
 
 class Work(ctypes.Structure):
@@ -123,6 +124,9 @@ def _bind(lib):
         "tc_profile_enable": ([c.c_int], None),
         "tc_profile_read": ([c.POINTER(c.c_double), c.POINTER(u64), c.c_int], None),
         "tc_phase_name": ([c.c_int], c.c_char_p),
+        "tc_debug_set_wait_limit": ([c.c_uint32, i32], c.c_int),
+        "tc_debug_fail_allocations": ([i32, i32], c.c_int),
+        "tc_debug_reset": ([], c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -559,6 +563,29 @@ def tc_profile_read(reset: bool = False) -> dict:
     nl = (ctypes.c_uint64 * len(PHASES))()
     load_library().tc_profile_read(ms, nl, 1 if reset else 0)
     return {p: (float(ms[i]), int(nl[i])) for i, p in enumerate(PHASES)}
+
+
+def tc_debug_set_wait_limit(spin_limit: int, unpublished_tile: int = -1, device=None) -> None:
+    """Failure-path test hook (include/tc_debug.h): every device spin-wait on
+    `device` gives up after `spin_limit` iterations, and radix-sort tile
+    `unpublished_tile` (>= 0) never publishes, so the tiles after it wait on
+    a word nothing sets.  Calls then fail with TC_ERR_TIMEOUT."""
+    torch = _torch()
+    with torch.cuda.device(device if device is not None else torch.cuda.current_device()):
+        _check(load_library().tc_debug_set_wait_limit(spin_limit, unpublished_tile))
+
+
+def tc_debug_fail_allocations(skip: int, count: int) -> None:
+    """Failure-path test hook: of the library's next device allocations the
+    first `skip` succeed and the `count` after them fail (TC_ERR_OOM)."""
+    _check(load_library().tc_debug_fail_allocations(skip, count))
+
+
+def tc_debug_reset(device=None) -> None:
+    """Undo both failure-path hooks (wait limit on `device`)."""
+    torch = _torch()
+    with torch.cuda.device(device if device is not None else torch.cuda.current_device()):
+        _check(load_library().tc_debug_reset())
 
 
 # short aliases

@@ -565,6 +565,7 @@ k_count(Lists g, const int32_t *__restrict__ warp_list, const int32_t *__restric
   uint16_t *s_slot = reinterpret_cast<uint16_t *>(smem + 4 * SLOTS * (PV ? 2 : 1));
   __shared__ WarpScratch s_ws[kMainWarps];
   __shared__ CtaShared s_sh;
+  if (aborted(ctrl)) return;  // an earlier wait of this call ran out: the lists are not complete
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   clear_table<PV>(s_tab, s_cnt, SLOTS, tid, kMainThreads);
   uint64_t found_total = 0;
@@ -591,6 +592,7 @@ k_count_big(Lists g, const int32_t *__restrict__ big_list, int32_t n, Ctrl *ctrl
   uint16_t *slot_of = reinterpret_cast<uint16_t *>(smem + 4 * kBigSlots * (PV ? 2 : 1));
   __shared__ WarpScratch s_ws[kBigWarps];
   __shared__ CtaShared s_sh;
+  if (aborted(ctrl)) return;  // an earlier wait of this call ran out: the lists are not complete
   const int tid = threadIdx.x, lane = tid & 31;
   clear_table<PV>(tab, cnt, kBigSlots, tid, kBigThreads);
   uint64_t found_total = 0;
@@ -634,7 +636,8 @@ k_clustering(const int64_t *__restrict__ t, const int32_t *__restrict__ deg, int
 // Per-vertex counts from rank space back to the caller's vertex ids.
 __global__ void __launch_bounds__(kClusterThreads)
 k_gather_counts(const int64_t *__restrict__ t_rank, const int32_t *__restrict__ rank, int32_t n,
-                int64_t *__restrict__ t_out) {
+                int64_t *__restrict__ t_out, const Ctrl *ctrl) {
+  if (aborted(ctrl)) return;  // rank[] may be incomplete
   const uint32_t stride = gridDim.x * kClusterThreads;
   for (uint32_t v = blockIdx.x * kClusterThreads + threadIdx.x; v < (uint32_t)n; v += stride)
     t_out[v] = __ldg(t_rank + __ldg(rank + v));
@@ -764,13 +767,13 @@ void launch_clustering(const int64_t *t, const int32_t *deg, int32_t n, double *
 }
 
 void launch_gather_counts(const int64_t *t_rank, const int32_t *rank, int32_t n, int64_t *t_out,
-                          cudaStream_t st) {
+                          const Ctrl *ctrl, cudaStream_t st) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const uint32_t want = ((uint32_t)n + kClusterThreads * 4 - 1) / (kClusterThreads * 4);
   const uint32_t grid = max(1u, min(want, (uint32_t)(sms > 0 ? sms : 1) * 8));
-  k_gather_counts<<<grid, kClusterThreads, 0, st>>>(t_rank, rank, n, t_out);
+  k_gather_counts<<<grid, kClusterThreads, 0, st>>>(t_rank, rank, n, t_out, ctrl);
   note_launch();
 }
 

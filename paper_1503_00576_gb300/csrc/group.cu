@@ -51,6 +51,7 @@ k_group_keys(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
              uint64_t *__restrict__ gkeys, uint32_t *__restrict__ hist,
              int32_t *__restrict__ col4) {
   __shared__ uint32_t s_hist[kMaxGroupPasses * 256];
+  if (aborted(ctrl)) return;  // an earlier wait of this call ran out
   for (int i = threadIdx.x; i < passes * 256; i += kGroupThreads) s_hist[i] = 0;
   __syncthreads();
   const uint32_t m = ctrl->m;
@@ -101,6 +102,7 @@ k_group_keys(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
 __global__ void __launch_bounds__(kGroupThreads)
 k_work(const int32_t *__restrict__ off, const int32_t *__restrict__ goff,
        const int32_t *__restrict__ part, int32_t n, Ctrl *ctrl) {
+  if (aborted(ctrl)) return;
   const int lane = threadIdx.x & 31;
   const uint32_t warps = gridDim.x * (kGroupThreads / 32);
   unsigned long long lookups = 0, inserts = 0, merge = 0, dmax = 0;

@@ -48,6 +48,11 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Bound of every spin-wait of this file, and the radix-pass tile that never
+// publishes (none by default).  Only the failure-path tests change them.
+__device__ uint32_t g_spin_limit = kSpinLimit;
+__device__ uint32_t g_unpublished_tile = 0xffffffffu;
+
 __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p) {
   return *(const volatile unsigned long long *)p;
 }
@@ -116,10 +121,14 @@ __device__ __forceinline__ uint32_t block_scan_exclusive(uint32_t x, uint32_t *s
 // values up to the nearest inclusive prefix, or all 32 and moves on; so a
 // walk back over many tiles costs one memory latency per 32 tiles.
 // Publishes the tile's inclusive prefix and returns the exclusive one (in
-// every lane).  All 32 lanes of the warp must call it.
+// every lane).  If a wait runs out, or a predecessor is poisoned, the tile's
+// prefix is unknown: it publishes a poisoned status, sets *bad (in every
+// lane) and the caller must write nothing.  All 32 lanes of the warp must
+// call it.
 __device__ uint64_t lookback_warp(unsigned long long *status, uint32_t tile, uint64_t agg,
-                                  Ctrl *ctrl, bool published = false) {
+                                  Ctrl *ctrl, bool *bad, bool published = false) {
   const int lane = threadIdx.x & 31;
+  *bad = false;
   if (tile == 0) {
     if (lane == 0 && !published) st_volatile_u64(&status[0], kFlagInclusive | agg);
     return 0;
@@ -128,14 +137,20 @@ __device__ uint64_t lookback_warp(unsigned long long *status, uint32_t tile, uin
   uint64_t excl = 0;
   int64_t j = (int64_t)tile - 1;
   uint32_t spins = 0;
+  const uint32_t limit = g_spin_limit;
   for (;;) {
     const int64_t idx = j - lane;
     // before tile 0 nothing is added: an inclusive zero
     const unsigned long long s = idx >= 0 ? ld_volatile_u64(&status[idx]) : kFlagInclusive;
     const unsigned long long flag = s & ~kValueMask;
+    if (__any_sync(kFull, flag == kFlagPoison)) {
+      *bad = true;
+      break;
+    }
     if (__any_sync(kFull, flag == 0)) {  // a predecessor in the window has not published
-      if (++spins > kSpinLimit) {
+      if (++spins > limit) {
         if (lane == 0) atomicOr(&ctrl->err, kErrTimeout);
+        *bad = true;
         break;
       }
       if (spins > 8) __nanosleep(32);
@@ -150,8 +165,15 @@ __device__ uint64_t lookback_warp(unsigned long long *status, uint32_t tile, uin
     if (inc) break;
     j -= 32;
   }
-  if (lane == 0) st_volatile_u64(&status[tile], kFlagInclusive | (excl + agg));
+  if (lane == 0) st_volatile_u64(&status[tile], *bad ? kFlagPoison : kFlagInclusive | (excl + agg));
   return excl;
+}
+
+// A tile that starts after the call has failed publishes a poisoned status
+// (so that no successor waits on it) and does nothing else.  One word per
+// tile; called by one thread.
+__device__ __forceinline__ void poison_tile(unsigned long long *status, uint32_t tile) {
+  st_volatile_u64(&status[tile], kFlagPoison);
 }
 
 // The first half of lookback_warp, for a tile whose aggregate is known
@@ -247,6 +269,7 @@ struct RadixShared {
   uint32_t gbase[256];                      // per digit: output position of staged index 0
   uint32_t scratch[32];
   uint32_t tile;
+  uint32_t abort;  // some digit's look-back gave up: the tile writes nothing
 };
 
 // Writes one staged key to its output position (and, for the column pass,
@@ -330,7 +353,8 @@ __device__ __forceinline__ void radix_tile(RadixShared &S, const uint64_t *__res
   uint32_t tile_cnt = 0;
 #pragma unroll
   for (int w = 0; w < WARPS; ++w) tile_cnt += S.whist[w][tid];
-  st_volatile_u64(st, (tile == 0 ? kFlagInclusive : kFlagAggregate) | tile_cnt);
+  const bool publish = tile != g_unpublished_tile;  // always, but in a failure-path test
+  if (publish) st_volatile_u64(st, (tile == 0 ? kFlagInclusive : kFlagAggregate) | tile_cnt);
   uint32_t tile_total;
   const uint32_t tstart = scan256_exclusive(tile_cnt, S.scratch, &tile_total);
   {
@@ -354,28 +378,37 @@ __device__ __forceinline__ void radix_tile(RadixShared &S, const uint64_t *__res
     if (tile > 0) {
       int64_t j = (int64_t)tile - 1;
       uint32_t spins = 0;
+      const uint32_t limit = g_spin_limit;
+      bool bad = false;
       while (j >= 0) {
         const unsigned long long s = ld_volatile_u64(status + (size_t)j * 256 + tid);
         const unsigned long long flag = s & ~kValueMask;
         if (flag == 0) {
-          if (++spins > kSpinLimit) {
+          if (++spins > limit) {
             atomicOr(&ctrl->err, kErrTimeout);
+            bad = true;
             break;
           }
           if (spins > 64) __nanosleep(64);
           continue;
         }
+        if (flag == kFlagPoison) {
+          bad = true;
+          break;
+        }
         excl += s & kValueMask;
         if (flag == kFlagInclusive) break;
         --j;
       }
-      st_volatile_u64(st, kFlagInclusive | (excl + tile_cnt));
+      if (publish) st_volatile_u64(st, bad ? kFlagPoison : kFlagInclusive | (excl + tile_cnt));
+      if (bad) S.abort = 1u;
     }
     // output position of the staged index i with digit d is s_gbase[d] + i
     // (mod 2^32 arithmetic; the result is < 2^31)
     S.gbase[tid] = gofs + (uint32_t)excl - tstart;
   }
   __syncthreads();
+  if (S.abort) return;  // uniform for the block
 
   // ---- scatter: consecutive threads write consecutive positions of a run ----
   if (FULL) {
@@ -406,11 +439,18 @@ k_radix_pass(const uint64_t *__restrict__ in, void *__restrict__ out, uint32_t n
   constexpr int WARPS = kSortThreads / 32, TILE = kSortTile;
   __shared__ RadixShared S;
   const int tid = threadIdx.x;
-  const uint32_t n_keys = n_keys_dev ? *n_keys_dev : n_keys_bound;
-  if (tid == 0) S.tile = atomicAdd(ticket, 1u);
+  if (tid == 0) {
+    S.tile = atomicAdd(ticket, 1u);
+    S.abort = aborted(ctrl) ? 1u : 0u;
+  }
   for (int i = tid; i < WARPS * 256; i += kSortThreads) (&S.whist[0][0])[i] = 0;
   __syncthreads();
   const uint32_t tile = S.tile;
+  if (S.abort) {  // an earlier wait of this call ran out: the input is not complete
+    st_volatile_u64(status + (size_t)tile * 256 + tid, kFlagPoison);
+    return;
+  }
+  const uint32_t n_keys = n_keys_dev ? *n_keys_dev : n_keys_bound;
   const uint32_t tile_base = tile * (uint32_t)TILE;
   if (tile_base >= n_keys) return;  // uniform for the block
 
@@ -434,6 +474,7 @@ constexpr int kDegUnroll = 8;
 __global__ void __launch_bounds__(kDegThreads)
 k_unique_degree(const uint64_t *__restrict__ keys, const Ctrl *__restrict__ ctrl, int b,
                 int32_t *deg) {
+  if (aborted(ctrl)) return;
   const uint32_t m_in = ctrl->m_in;
   const uint64_t sentinel = (1ull << (2 * b)) - 1;
   const uint64_t mask = (1ull << b) - 1;
@@ -508,13 +549,21 @@ k_orient(const uint64_t *__restrict__ keys, int b,
   __shared__ uint32_t s_scratch[32];
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_excl;
+  __shared__ uint32_t s_abort;
   __shared__ uint32_t s_hist[kMaxSort2Passes * 256];
   const int tid = threadIdx.x;
   const uint32_t m_in = ctrl->m_in;
-  if (tid == 0) s_tile = atomicAdd(&ctrl->tile_ticket[kTicketOrient], 1u);
+  if (tid == 0) {
+    s_tile = atomicAdd(&ctrl->tile_ticket[kTicketOrient], 1u);
+    s_abort = aborted(ctrl) ? 1u : 0u;
+  }
   for (int i = tid; i < passes2 * 256; i += kOrientThreads) s_hist[i] = 0;
   __syncthreads();
   const uint32_t tile = s_tile;
+  if (s_abort) {  // an earlier wait of this call ran out
+    if (tid == 0) poison_tile(status, tile);
+    return;
+  }
   const uint32_t tile_base = tile * (uint32_t)TILE;
   if (tile_base >= m_in) return;
   const uint64_t sentinel = (1ull << (2 * b)) - 1;
@@ -576,13 +625,16 @@ k_orient(const uint64_t *__restrict__ keys, int b,
       if ((flags >> i) & 1u) s_buf[swz(pos++)] = k[i];
   }
   if (tid < 32) {
-    const uint64_t excl = lookback_warp(status, tile, tile_cnt, ctrl, true);
+    bool bad;
+    const uint64_t excl = lookback_warp(status, tile, tile_cnt, ctrl, &bad, true);
     if (tid == 0) {
       s_excl = (uint32_t)excl;
-      if (tile_base + TILE >= m_in) ctrl->m = (uint32_t)(excl + tile_cnt);  // last tile
+      s_abort = bad ? 1u : 0u;
+      if (!bad && tile_base + TILE >= m_in) ctrl->m = (uint32_t)(excl + tile_cnt);  // last tile
     }
   }
   __syncthreads();
+  if (s_abort) return;  // the tile's place in the output is unknown
   const uint32_t base = s_excl;
   for (uint32_t j = tid; j < tile_cnt; j += kOrientThreads) okeys[base + j] = s_buf[swz(j)];
   __syncthreads();
@@ -610,11 +662,18 @@ k_offsets(const int32_t *__restrict__ counts, int32_t n, int32_t *__restrict__ o
           uint32_t shards) {
   constexpr int IPT = kScanItemsPerThread, TILE = kScanTile;
   __shared__ uint32_t s_scratch[32];
-  __shared__ uint32_t s_tile, s_excl;
+  __shared__ uint32_t s_tile, s_excl, s_abort;
   const int tid = threadIdx.x, lane = tid & 31;
-  if (tid == 0) s_tile = atomicAdd(ticket, 1u);
+  if (tid == 0) {
+    s_tile = atomicAdd(ticket, 1u);
+    s_abort = aborted(ctrl) ? 1u : 0u;
+  }
   __syncthreads();
   const uint32_t tile = s_tile;
+  if (s_abort) {  // an earlier wait of this call ran out
+    if (tid == 0) poison_tile(status, tile);
+    return;
+  }
   const uint32_t items = (uint32_t)n + 1;  // off[0..n]
   const uint32_t tile_base = tile * (uint32_t)TILE;
   if (tile_base >= items) return;
@@ -631,10 +690,15 @@ k_offsets(const int32_t *__restrict__ counts, int32_t n, int32_t *__restrict__ o
   uint32_t tile_sum;
   const uint32_t toff = block_scan_exclusive<kScanThreads>(sum, s_scratch, &tile_sum);
   if (tid < 32) {
-    const uint32_t excl = (uint32_t)lookback_warp(status, tile, tile_sum, ctrl);
-    if (tid == 0) s_excl = excl;
+    bool bad;
+    const uint32_t excl = (uint32_t)lookback_warp(status, tile, tile_sum, ctrl, &bad);
+    if (tid == 0) {
+      s_excl = excl;
+      s_abort = bad ? 1u : 0u;
+    }
   }
   __syncthreads();
+  if (s_abort) return;  // the tile's prefix is unknown
   uint32_t run = s_excl + toff;
 #pragma unroll
   for (int i = 0; i < IPT; ++i) {
@@ -686,6 +750,13 @@ int num_sms() {
 }
 
 }  // namespace
+
+cudaError_t set_wait_hooks(uint32_t spin_limit, uint32_t unpublished_tile) {
+  cudaError_t e = cudaMemcpyToSymbol(g_spin_limit, &spin_limit, sizeof(spin_limit));
+  if (e == cudaSuccess)
+    e = cudaMemcpyToSymbol(g_unpublished_tile, &unpublished_tile, sizeof(unpublished_tile));
+  return e;
+}
 
 void launch_canon(const int32_t *src, const int32_t *dst, uint32_t m_in, int32_t n, int b,
                   int passes, const BatchDesc *batch, uint64_t *keys, uint32_t *hist,

@@ -9,6 +9,7 @@
 
 #include "tc.h"
 #include "tc_common.cuh"
+#include "tc_debug.h"
 
 namespace tc {
 
@@ -38,6 +39,7 @@ tc_status set_status(tc_status s, const char *fmt = nullptr, ...) {
 }
 
 tc_status cuda_fail(cudaError_t e, const char *what) {
+  cudaGetLastError();  // a failed runtime call is not charged to the next call
   if (e == cudaErrorMemoryAllocation)
     return set_status(TC_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
   return set_status(TC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
@@ -48,6 +50,35 @@ tc_status cuda_fail(cudaError_t e, const char *what) {
     cudaError_t e_ = (call);                    \
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
+
+// ---- allocation-failure injection (tc_debug_fail_allocations) ----
+std::atomic<bool> g_inject_on{false};
+std::mutex g_inject_mu;
+int64_t g_inject_skip = 0, g_inject_fail = 0;
+
+// Whether this device allocation is to fail as if the device were out of
+// memory (only ever true in the allocation-failure tests).
+bool injected_alloc_failure() {
+  if (!g_inject_on.load(std::memory_order_relaxed)) return false;
+  std::lock_guard<std::mutex> lk(g_inject_mu);
+  if (g_inject_fail <= 0) return false;
+  if (g_inject_skip > 0) {
+    --g_inject_skip;
+    return false;
+  }
+  if (--g_inject_fail == 0) g_inject_on.store(false);
+  return true;
+}
+
+// Every device allocation of the library goes through these two.
+cudaError_t dev_alloc_async(void **p, size_t bytes, cudaStream_t st) {
+  if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
+  return cudaMallocAsync(p, bytes, st);
+}
+cudaError_t dev_alloc(void **p, size_t bytes) {
+  if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
 
 // ---- instrumentation ----
 std::atomic<int> g_prof_on{0};
@@ -336,12 +367,12 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   pt.start(TC_PHASE_COUNT);
   cudaError_t e = launch_count(off, voff, col4, goff, part, warp_groups, cta_groups, big_groups,
                                n, ctrl, t_out ? t_rank : nullptr, t_out ? nullptr : t_rank, st);
-  if (e == cudaSuccess && t_out) launch_gather_counts(t_rank, rank, n, t_out, st);
+  if (e == cudaSuccess && t_out) launch_gather_counts(t_rank, rank, n, t_out, ctrl, st);
   if (e == cudaSuccess && batch) {
     if (t_out) {  // per graph: (sum of t) / 3
       launch_segment_sums(t_out, batch->desc, batch->num_graphs_bound, 3, batch->totals, st);
     } else {      // per graph: sum of the group totals
-      launch_gather_counts(t_rank, rank, n, tg_union, st);
+      launch_gather_counts(t_rank, rank, n, tg_union, ctrl, st);
       launch_segment_sums(tg_union, batch->desc, batch->num_graphs_bound, 1, batch->totals, st);
     }
   }
@@ -354,10 +385,10 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
 
 // Status of a run from its control block (after the stream has synchronised).
 tc_status finish_core(const Ctrl *h, int32_t n, uint64_t *total) {
-  if (h->err & kErrIdRange)
-    return set_status(TC_ERR_ID_RANGE, "a vertex id is outside [0, %d) of its graph", n);
   if (h->err & kErrTimeout)
     return set_status(TC_ERR_TIMEOUT, "a device-side wait reached its iteration limit");
+  if (h->err & kErrIdRange)
+    return set_status(TC_ERR_ID_RANGE, "a vertex id is outside [0, %d) of its graph", n);
   if (total) *total = (uint64_t)h->total;
   return set_status(TC_OK);
 }
@@ -416,7 +447,7 @@ tc_status count_impl(const int32_t *src, const int32_t *dst, int64_t m, int32_t 
   }
   keep_pool_memory();
   void *ws = nullptr;
-  TC_CUDA(cudaMallocAsync(&ws, L.total, st), "workspace allocation");
+  TC_CUDA(dev_alloc_async(&ws, L.total, st), "workspace allocation");
   s = run_core(src, dst, m, n, st, (unsigned char *)ws, L, t_out, deg_out, total, nullptr, true,
                shard, shards);
   const tc_status keep = s;
@@ -463,20 +494,33 @@ tc_status host_impl(const int32_t *src_h, const int32_t *dst_h, int64_t m, int32
   int32_t *d_src = nullptr, *d_dst = nullptr, *d_deg = nullptr;
   int64_t *d_t = nullptr;
   const bool in_place = kernels_read_host_memory();
+  // what was allocated is released on every path below, failed ones included
+  cudaError_t e = cudaSuccess;
+  const char *what = nullptr;
   if (m > 0 && !in_place) {
-    TC_CUDA(cudaMallocAsync((void **)&d_src, in_bytes, st), "input allocation");
-    TC_CUDA(cudaMallocAsync((void **)&d_dst, in_bytes, st), "input allocation");
-    TC_CUDA(cudaMemcpyAsync(d_src, src_h, in_bytes, cudaMemcpyHostToDevice, st), "copy in");
-    TC_CUDA(cudaMemcpyAsync(d_dst, dst_h, in_bytes, cudaMemcpyHostToDevice, st), "copy in");
+    if ((e = dev_alloc_async((void **)&d_src, in_bytes, st)) != cudaSuccess ||
+        (e = dev_alloc_async((void **)&d_dst, in_bytes, st)) != cudaSuccess)
+      what = "input allocation";
+    else if ((e = cudaMemcpyAsync(d_src, src_h, in_bytes, cudaMemcpyHostToDevice, st)) !=
+                 cudaSuccess ||
+             (e = cudaMemcpyAsync(d_dst, dst_h, in_bytes, cudaMemcpyHostToDevice, st)) !=
+                 cudaSuccess)
+      what = "copy in";
   }
-  if (per_vertex && n > 0) {
-    TC_CUDA(cudaMallocAsync((void **)&d_t, sizeof(int64_t) * (size_t)n, st), "t allocation");
-    if (deg_h)
-      TC_CUDA(cudaMallocAsync((void **)&d_deg, sizeof(int32_t) * (size_t)n, st), "deg allocation");
+  if (!what && per_vertex && n > 0) {
+    if ((e = dev_alloc_async((void **)&d_t, sizeof(int64_t) * (size_t)n, st)) != cudaSuccess)
+      what = "t allocation";
+    else if (deg_h &&
+             (e = dev_alloc_async((void **)&d_deg, sizeof(int32_t) * (size_t)n, st)) !=
+                 cudaSuccess)
+      what = "deg allocation";
   }
   uint64_t T = 0;
-  s = count_impl(in_place ? src_h : d_src, in_place ? dst_h : d_dst, m, n, st, nullptr, 0,
-                 per_vertex ? d_t : nullptr, d_deg, &T);
+  if (what)
+    s = cuda_fail(e, what);
+  else
+    s = count_impl(in_place ? src_h : d_src, in_place ? dst_h : d_dst, m, n, st, nullptr, 0,
+                   per_vertex ? d_t : nullptr, d_deg, &T);
   if (s == TC_OK && per_vertex && n > 0) {
     cudaError_t e = cudaMemcpyAsync(t_h, d_t, sizeof(int64_t) * (size_t)n,
                                     cudaMemcpyDeviceToHost, st);
@@ -488,7 +532,7 @@ tc_status host_impl(const int32_t *src_h, const int32_t *dst_h, int64_t m, int32
   if (d_dst) cudaFreeAsync(d_dst, st);
   if (d_t) cudaFreeAsync(d_t, st);
   if (d_deg) cudaFreeAsync(d_deg, st);
-  cudaError_t e = cudaStreamSynchronize(st);
+  e = cudaStreamSynchronize(st);
   if (s != TC_OK) return s;
   if (e != cudaSuccess) return cuda_fail(e, "synchronize");
   if (total) *total = T;
@@ -502,32 +546,33 @@ tc_status host_impl(const int32_t *src_h, const int32_t *dst_h, int64_t m, int32
 // that hands all device memory to its own pool allocator at start-up and
 // forbids driver allocations afterwards, or a service whose memory budget is
 // fixed when it starts.  For them the whole workspace lives in this
-// file-scope array, reserved when the library is loaded and held by every GPU
-// that loads it until the process exits.  Host code cannot pass the array's
-// name to a kernel (on the host it is only a stand-in symbol), so its device
-// address is looked up once per device with cudaGetSymbolAddress, with that
-// device current, on the first call made there.
+// file-scope array, held by every GPU that has loaded it until the process
+// exits.  When the array comes into being on a device depends on how CUDA
+// loads modules: eagerly (CUDA_MODULE_LOADING=EAGER) when the library's
+// context is set up there, lazily (the default) on the first use of this
+// file's module on that device -- which is the first tc_count_noalloc call
+// there, since no kernel lives in this file.  So the first call on each
+// device may reserve the 32 MiB; callers that reserve all device memory
+// later should make that first call at start-up, before they do.
+//
+// Host code cannot pass the array's name to a kernel (on the host it is only
+// a stand-in symbol), so every call looks up its device address on the
+// current device with cudaGetSymbolAddress (cheap once the module is
+// loaded).  Nothing is cached, so a context torn down and set up again
+// (cudaDeviceReset) gets the array's new address.
 // ---------------------------------------------------------------------------
 static __device__ __align__(256) unsigned char g_noalloc_scratch[TC_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kNoAllocMaxDevices = 64;
-std::mutex g_noalloc_mu;
-unsigned char *g_noalloc_addr[kNoAllocMaxDevices] = {};
-
 // Device address of g_noalloc_scratch on the current device.
 tc_status noalloc_scratch(unsigned char **out) {
-  int dev = -1;
-  TC_CUDA(cudaGetDevice(&dev), "current device");
-  if (dev < 0 || dev >= kNoAllocMaxDevices)
-    return set_status(TC_ERR_INVALID_ARG, "device %d is beyond the %d supported", dev,
-                      kNoAllocMaxDevices);
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    void *p = nullptr;
-    TC_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch), "scratch symbol address");
-    g_noalloc_addr[dev] = static_cast<unsigned char *>(p);
-  }
-  *out = g_noalloc_addr[dev];
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e == cudaErrorMemoryAllocation)
+    return cuda_fail(e, "loading the static scratch array on this device (the first "
+                        "tc_count_noalloc call on a device reserves it; make that call "
+                        "before device memory runs out)");
+  if (e != cudaSuccess) return cuda_fail(e, "scratch symbol address");
+  *out = static_cast<unsigned char *>(p);
   return TC_OK;
 }
 
@@ -620,7 +665,7 @@ tc_status batch_impl(const int32_t *src, const int32_t *dst, int32_t G, const in
   const BatchRegion R = batch_region(G);
   keep_pool_memory();
   unsigned char *ws = nullptr;
-  TC_CUDA(cudaMallocAsync((void **)&ws, L.total + R.bytes, st), "workspace allocation");
+  TC_CUDA(dev_alloc_async((void **)&ws, L.total + R.bytes, st), "workspace allocation");
   unsigned char *bd = ws + L.total;
   std::vector<unsigned char> staging(R.totals);
   BatchDesc desc{G, 0, reinterpret_cast<int32_t *>(bd + R.block),
@@ -703,7 +748,7 @@ tc_status engine_build(tc_engine *e) {
   e->L = make_layout(e->max_pairs, e->max_vertices);
   e->R = batch_region(e->max_graphs);
   const size_t in_bytes = align256(sizeof(int32_t) * (size_t)e->max_pairs);
-  TC_CUDA(cudaMalloc((void **)&e->dbuf, 2 * in_bytes + e->L.total + e->R.bytes),
+  TC_CUDA(dev_alloc((void **)&e->dbuf, 2 * in_bytes + e->L.total + e->R.bytes),
           "engine device memory");
   e->src = reinterpret_cast<int32_t *>(e->dbuf);
   e->dst = reinterpret_cast<int32_t *>(e->dbuf + in_bytes);
@@ -796,7 +841,7 @@ tc_status tc_clustering(const int64_t *t, const int32_t *deg, int32_t n, tc_stre
   }
   keep_pool_memory();
   unsigned char *buf = nullptr;
-  TC_CUDA(cudaMallocAsync((void **)&buf, 32, st), "scratch allocation");
+  TC_CUDA(dev_alloc_async((void **)&buf, 32, st), "scratch allocation");
   auto *sums = reinterpret_cast<unsigned long long *>(buf);
   double *dev_out = reinterpret_cast<double *>(buf + 16);
   TC_CUDA(cudaMemsetAsync(buf, 0, 32, st), "memset");
@@ -1016,7 +1061,7 @@ tc_status tc_count_work(const int32_t *src, const int32_t *dst, int64_t m, int32
   const Layout L = make_layout(m, n);
   keep_pool_memory();
   unsigned char *ws = nullptr;
-  TC_CUDA(cudaMallocAsync((void **)&ws, L.total, st), "workspace allocation");
+  TC_CUDA(dev_alloc_async((void **)&ws, L.total, st), "workspace allocation");
   Ctrl *h = host_ctrl();
   PhaseTimer pt(st, false);
   if (!h) s = set_status(TC_ERR_OOM, "pinned staging buffer");
@@ -1059,6 +1104,26 @@ tc_status tc_get_tuning(tc_tuning *out) {
   out->warp_max_partners = t.warp_max_partners;
   out->heavy_ratio_pct = t.heavy_ratio_pct;
   return set_status(TC_OK);
+}
+
+tc_status tc_debug_set_wait_limit(uint32_t spin_limit, int32_t unpublished_tile) {
+  TC_CUDA(cudaDeviceSynchronize(), "synchronize");
+  TC_CUDA(set_wait_hooks(spin_limit, unpublished_tile < 0 ? 0xffffffffu : (uint32_t)unpublished_tile),
+          "wait hooks");
+  return set_status(TC_OK);
+}
+
+tc_status tc_debug_fail_allocations(int32_t skip, int32_t count) {
+  std::lock_guard<std::mutex> lk(g_inject_mu);
+  g_inject_skip = skip > 0 ? skip : 0;
+  g_inject_fail = count > 0 ? count : 0;
+  g_inject_on.store(g_inject_fail > 0);
+  return set_status(TC_OK);
+}
+
+tc_status tc_debug_reset(void) {
+  tc_debug_fail_allocations(0, 0);
+  return tc_debug_set_wait_limit(kSpinLimit, -1);
 }
 
 tc_status tc_last_error(void) { return t_last; }

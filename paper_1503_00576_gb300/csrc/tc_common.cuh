@@ -14,7 +14,11 @@ enum : uint32_t { kErrIdRange = 1u, kErrTimeout = 2u };
 // library is on a predecessor tile that is already resident (tiles are handed
 // out in launch order through an atomic ticket), so the bound is a safety
 // net: if it is ever reached the kernel records kErrTimeout, stops waiting
-// and the host reports TC_ERR_TIMEOUT.
+// and the host reports TC_ERR_TIMEOUT.  What a timed-out tile would have
+// written is not trusted: the tile publishes a poisoned status instead of its
+// prefix and writes nothing, every tile that reads a poisoned status does the
+// same, and every later kernel of the call returns at entry once kErrTimeout
+// is set (see aborted()), so no kernel runs on incomplete data.
 constexpr uint32_t kSpinLimit = 1u << 24;
 
 constexpr int kMaxSort1Passes = 8;  // 2 * 31 id bits / 8-bit digits
@@ -60,7 +64,16 @@ static_assert(kTicketVecScan < 24, "ticket slots");
 // Look-back status words: value in the low 62 bits, flag in the top 2.
 constexpr unsigned long long kFlagAggregate = 1ull << 62;
 constexpr unsigned long long kFlagInclusive = 2ull << 62;
+constexpr unsigned long long kFlagPoison = 3ull << 62;  // the tile gave up: its prefix is unknown
 constexpr unsigned long long kValueMask = (1ull << 62) - 1;
+
+#ifdef __CUDACC__
+// True once some kernel of this call has recorded a wait that ran out: the
+// data it left behind is incomplete, so later kernels must not read it.
+__device__ __forceinline__ bool aborted(const Ctrl *ctrl) {
+  return (*(const volatile uint32_t *)&ctrl->err & kErrTimeout) != 0u;
+}
+#endif
 
 // Partner groups whose hashed forward list has at most kWarpMaxRow entries
 // are counted by one warp, up to kCtaMaxRow by a 256-thread CTA, and longer
@@ -179,6 +192,12 @@ inline Layout make_layout(int64_t m_in, int32_t n) {
 // Kernel-launch bookkeeping (defined in tc_api.cu).
 void note_launch();
 
+// Test hooks of the wait paths (preprocess.cu), on the current device:
+// spin_limit bounds every spin-wait (kSpinLimit by default); the radix-pass
+// tile numbered unpublished_tile (UINT32_MAX: none) never publishes its
+// status, so the tiles after it wait on a word that nothing sets.
+cudaError_t set_wait_hooks(uint32_t spin_limit, uint32_t unpublished_tile);
+
 // ---- launchers (preprocess.cu) ----
 // batch == nullptr: one graph on ids [0, n).  Otherwise ids of pair i are
 // local to its graph, checked against that graph's vertex count, and
@@ -255,6 +274,6 @@ void launch_clustering(const int64_t *t, const int32_t *deg, int32_t n, double *
 void launch_transitivity(const unsigned long long *sums, double *out, cudaStream_t st);
 // t_out[v] = t_rank[rank[v]]: per-vertex counts back to the caller's ids.
 void launch_gather_counts(const int64_t *t_rank, const int32_t *rank, int32_t n, int64_t *t_out,
-                          cudaStream_t st);
+                          const Ctrl *ctrl, cudaStream_t st);
 
 }  // namespace tc

@@ -1,8 +1,9 @@
-"""The C-ABI library builds, loads and exports every symbol of include/tc.h.
+"""The C-ABI library builds, loads and exports every symbol of include/*.h.
 
 CPU only: nothing here calls into the GPU code (no device is needed to load
 the shared library, and no compute entry point is invoked)."""
 import ctypes
+import glob
 import os
 import re
 import shutil
@@ -10,14 +11,16 @@ import shutil
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "tc.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 def header_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^[A-Za-z_][\w \*]*?\b(tc_\w+)\s*\(", text, flags=re.M)
-    return sorted(set(names))
+    names = set()
+    for path in HEADERS:
+        text = open(path).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names.update(re.findall(r"^[A-Za-z_][\w \*]*?\b(tc_\w+)\s*\(", text, flags=re.M))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -32,7 +35,9 @@ def lib():
 
 def test_header_lists_the_api():
     names = header_functions()
+    assert [os.path.basename(h) for h in HEADERS] == ["tc.h", "tc_debug.h"]
     assert "tc_count" in names and "tc_count_per_vertex" in names
+    assert "tc_debug_set_wait_limit" in names
     assert len(names) >= 12
 
 

@@ -1,12 +1,14 @@
-"""The allocation-free entry point against the ordinary one.
+"""The allocation-free entry point against the ordinary one and the oracle.
 
 tc_count_noalloc serves callers that cannot allocate device memory while
 they run (their own allocator owns the device memory, or their memory budget
 is fixed at start-up).  It must count exactly what tc_count counts -- the
 counts are integers, so the tolerance is zero -- on two calls in a row, since
-every call reuses the same static scratch array.  This file sorts last so
-that a run stopping at the first failure has already run every other test;
-it also passes on its own in a fresh process.
+every call reuses the same static scratch array, and what the CPU oracle
+counts.  A warm call must take no device memory: with every library
+allocation made to fail, and with the device's free memory unchanged.  This
+file sorts last so that a run stopping at the first failure has already run
+every other test; it also passes on its own in a fresh process.
 """
 import ctypes
 
@@ -14,6 +16,7 @@ import numpy as np
 import pytest
 
 import graphgen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -82,3 +85,41 @@ def test_rejects_oversize_then_recovers(tc):
     small = graphgen.rmat(10, 16 << 10, 12)
     assert tc.tc_count_noalloc(_dev(small[0]), _dev(small[1]), 1 << 10) == \
         tc.tc_count(_dev(small[0]), _dev(small[1]), 1 << 10)
+
+
+def test_matches_the_oracle(tc):
+    src, dst = graphgen.rmat(14, 16 << 14, 21)
+    n = 1 << 14
+    want = oracle.forward(src, dst, n, per_vertex=False)["T"]
+    s, d = _dev(src), _dev(dst)
+    for _ in range(2):
+        rc, got = _noalloc(tc, s, d, n)
+        assert rc == tc.TC_OK
+        assert got == want
+
+
+def test_warm_call_takes_no_device_memory(tc):
+    """After a first (warm-up) call on the device, a call allocates nothing:
+    it succeeds while every allocation the library could make is set to
+    fail, and the device's free memory does not move."""
+    import torch
+
+    src, dst = graphgen.rmat(13, 16 << 13, 22)
+    n = 1 << 13
+    s, d = _dev(src), _dev(dst)
+    want = tc.tc_count(s, d, n)
+    assert _noalloc(tc, s, d, n) == (tc.TC_OK, want)  # warm-up: loads the array
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    tc.tc_debug_fail_allocations(0, 1 << 30)
+    try:
+        got = [_noalloc(tc, s, d, n) for _ in range(2)]
+        # the ordinary entry point does allocate: it must fail meanwhile
+        with pytest.raises(tc.TCError) as ei:
+            tc.tc_count(s, d, n)
+        assert ei.value.code == tc.TC_ERR_OOM
+    finally:
+        tc.tc_debug_fail_allocations(0, 0)
+    torch.cuda.synchronize()
+    assert got == [(tc.TC_OK, want)] * 2
+    assert torch.cuda.mem_get_info()[0] == free0
