@@ -272,6 +272,21 @@ def time_oracle(src, dst, n, pairs: int) -> tuple[float, int]:
 
 
 # ---------------------------------------------------------------- batched
+def stored_batch_totals(count: int):
+    """The CPU oracle's per-graph totals of graph_batch(count, 1005), written
+    by tests/golden/make_batch_golden.py, or None for another batch."""
+    import numpy as np
+
+    path = os.path.join(ROOT, "tests", "golden", "batch4096.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        gold = json.load(f)
+    if gold["count"] != count or gold["seed"] != 1005:
+        return None
+    return np.array(gold["T"], np.uint64)
+
+
 def run_batched(args, tc) -> dict:
     """Graphs/s of the persistent CUDA-graph batch engines (autotuned) against
     the per-graph launch loop, on the same device-resident graphs; the
@@ -316,6 +331,10 @@ def run_batched(args, tc) -> dict:
             assert np.array_equal(got, ref)
     batched_s = min(times)
     exact = bool(np.array_equal(ref, plain))
+    oracle_identical = None
+    gold = stored_batch_totals(args.batch_graphs)
+    if gold is not None:
+        oracle_identical = bool(np.array_equal(ref, gold) and np.array_equal(plain, gold))
     plan = batching.plan_subbatches(eo, vn, cap)
     del s, d
     served = None
@@ -326,6 +345,9 @@ def run_batched(args, tc) -> dict:
             "graphs_per_s": G / batched_s, "edges_per_s": m_total / batched_s,
             "plain_graphs_per_s": G / plain_s, "plain_edges_per_s": m_total / plain_s,
             "speedup_vs_plain": plain_s / batched_s, "counts_identical": exact,
+            "oracle_identical": oracle_identical,
+            "oracle_totals": "tests/golden/batch4096.json (CPU oracle, one graph per core)"
+                             if gold is not None else None,
             "batched_s": batched_s, "plain_s": plain_s, "subbatches": len(plan),
             "engines": 2, "capacity": {"pairs": cap.pairs, "vertices": cap.vertices,
                                         "graphs": cap.graphs},
@@ -549,6 +571,11 @@ def run_ours(args, world, rank, local, pg):
                              args.total_only),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "phase_ms_per_step": steps_ms, "batched": batched,
+        "counting_work": {"lookups": work["lookups"], "inserts": work["inserts"],
+                          "merge_work_W": work["merge_work"],
+                          "max_out_degree": work["max_out_degree"],
+                          "hub_lookup_share": {str(k): round(v / max(work["lookups"], 1), 4)
+                                               for k, v in work["hub_lookups"].items()}},
     }
     print(json.dumps(line), flush=True)
 

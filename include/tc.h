@@ -254,6 +254,12 @@ tc_status tc_engine_destroy(tc_engine *engine);
  *                  a sorted-list merge of Sec. II-B would read
  *   max_out_degree the largest d+(v), at most sqrt(2m) (Sec. II-B)
  *   triangles      T
+ *   hub_lookups[i] the lookups of the forward edges whose endpoints both
+ *                  lie in the hub set H_i of the 2^(12+i) vertices highest
+ *                  in the (degree, id) order; H_i is closed under forward
+ *                  edges, so these edges' triangles lie wholly in H_i and a
+ *                  dense count of the block A_{H_i H_i} (the matrix methods
+ *                  of Sec. VI) could replace exactly this share of lookups
  * Same arguments and errors as tc_count; synchronises `stream`.
  */
 typedef struct tc_work {
@@ -264,6 +270,7 @@ typedef struct tc_work {
   uint64_t triangles;
   int32_t max_out_degree;
   int32_t vertices;
+  int64_t hub_lookups[4];
 } tc_work;
 tc_status tc_count_work(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
                         tc_stream_t stream, tc_work *out);

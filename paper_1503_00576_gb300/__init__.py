@@ -62,7 +62,7 @@ class Work(ctypes.Structure):
     _fields_ = [("edges", ctypes.c_int64), ("lookups", ctypes.c_int64),
                 ("inserts", ctypes.c_int64), ("merge_work", ctypes.c_int64),
                 ("triangles", ctypes.c_uint64), ("max_out_degree", ctypes.c_int32),
-                ("vertices", ctypes.c_int32)]
+                ("vertices", ctypes.c_int32), ("hub_lookups", ctypes.c_int64 * 4)]
 
 
 class Tuning(ctypes.Structure):
@@ -526,7 +526,9 @@ def tc_count_work(src, dst, n: int, stream=None) -> dict:
         rc = lib.tc_count_work(src.data_ptr(), dst.data_ptr(), src.numel(), n,
                                _stream_of(stream, dev), ctypes.byref(w))
     _check(rc)
-    return {f: int(getattr(w, f)) for f, _ in w._fields_}
+    out = {f: int(getattr(w, f)) for f, _ in w._fields_ if f != "hub_lookups"}
+    out["hub_lookups"] = {1 << (12 + i): int(w.hub_lookups[i]) for i in range(4)}
+    return out
 
 
 TC_NOALLOC_SCRATCH_BYTES = 32 << 20

@@ -98,14 +98,18 @@ k_group_keys(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
 // of a count): per forward edge (h, l) of group h, the list streamed
 // through the hash set, d+(l) lookups, and the merge work d+(h) + d+(l) of
 // Sec. II-B; per non-empty group, the list hashed once, d+(h) inserts; the
-// largest d+.  One warp per vertex h.
+// largest d+.  Also, per hub set H = the 2^12 .. 2^15 highest ranks, the
+// lookups of the edges with both endpoints in H: ranks follow (degree, id),
+// so every forward neighbour of a vertex of H is in H, and those edges'
+// intersections lie wholly inside H (what a dense count of the hub block
+// A_HH would take over, Sec. VI).  One warp per vertex h.
 __global__ void __launch_bounds__(kGroupThreads)
 k_work(const int32_t *__restrict__ off, const int32_t *__restrict__ goff,
        const int32_t *__restrict__ part, int32_t n, Ctrl *ctrl) {
   if (aborted(ctrl)) return;
   const int lane = threadIdx.x & 31;
   const uint32_t warps = gridDim.x * (kGroupThreads / 32);
-  unsigned long long lookups = 0, inserts = 0, merge = 0, dmax = 0;
+  unsigned long long lookups = 0, inserts = 0, merge = 0, dmax = 0, hub[kHubSizes] = {};
   for (uint32_t h = (blockIdx.x * kGroupThreads + threadIdx.x) >> 5; h < (uint32_t)n;
        h += warps) {
     const unsigned long long dh = (unsigned long long)(__ldg(off + h + 1) - __ldg(off + h));
@@ -119,6 +123,11 @@ k_work(const int32_t *__restrict__ off, const int32_t *__restrict__ goff,
       const unsigned long long dl = (unsigned long long)(__ldg(off + l + 1) - __ldg(off + l));
       lookups += dl;
       merge += dh + dl;
+#pragma unroll
+      for (int k = 0; k < kHubSizes; ++k) {
+        const int64_t lo = (int64_t)n - ((int64_t)1 << (kHubLog2Min + k));
+        if ((int64_t)h >= lo && (int64_t)l >= lo) hub[k] += dl;
+      }
     }
   }
   for (int o = 16; o; o >>= 1) {
@@ -127,12 +136,17 @@ k_work(const int32_t *__restrict__ off, const int32_t *__restrict__ goff,
     merge += __shfl_xor_sync(0xffffffffu, merge, o);
     const unsigned long long x = __shfl_xor_sync(0xffffffffu, dmax, o);
     dmax = x > dmax ? x : dmax;
+#pragma unroll
+    for (int k = 0; k < kHubSizes; ++k) hub[k] += __shfl_xor_sync(0xffffffffu, hub[k], o);
   }
   if (lane == 0) {
     atomicAdd(&ctrl->work[0], lookups);
     atomicAdd(&ctrl->work[1], inserts);
     atomicAdd(&ctrl->work[2], merge);
     atomicMax(&ctrl->work[3], dmax);
+#pragma unroll
+    for (int k = 0; k < kHubSizes; ++k)
+      if (hub[k]) atomicAdd(&ctrl->work[4 + k], hub[k]);
   }
 }
 

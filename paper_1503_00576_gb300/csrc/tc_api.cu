@@ -1080,6 +1080,7 @@ tc_status tc_count_work(const int32_t *src, const int32_t *dst, int64_t m, int32
   out->inserts = (int64_t)h->work[1];
   out->merge_work = (int64_t)h->work[2];
   out->max_out_degree = (int32_t)h->work[3];
+  for (int k = 0; k < kHubSizes; ++k) out->hub_lookups[k] = (int64_t)h->work[4 + k];
   return set_status(TC_OK);
 }
 

@@ -31,6 +31,11 @@ constexpr int kSort2Slot = kMaxSort1Passes;
 constexpr int kRankSlot = kMaxSort1Passes + kMaxSort2Passes;
 constexpr int kGroupSlot = kMaxSort1Passes + kMaxSort2Passes + kMaxRankPasses;
 
+// Hub sets of the work instrumentation: the 2^(kHubLog2Min + i) highest
+// ranks, i < kHubSizes.
+constexpr int kHubSizes = 4;
+constexpr int kHubLog2Min = 12;
+
 // Control block: zeroed at the start of every call.
 struct Ctrl {
   uint32_t err;                    // kErr* bits
@@ -46,8 +51,9 @@ struct Ctrl {
   uint32_t m_in;                   // input pairs that are real (not batch padding)
   uint32_t pad[1];
   // work of the counting phase (filled only when asked for; see launch_work):
-  // hash lookups, hash inserts, merge work W, max out-degree
-  unsigned long long work[4];
+  // hash lookups, hash inserts, merge work W, max out-degree, then the
+  // lookups of edges with both endpoints among the 2^12 .. 2^15 top ranks
+  unsigned long long work[4 + kHubSizes];
 };
 static_assert(sizeof(Ctrl) % 16 == 0, "Ctrl must keep 16-byte alignment");
 

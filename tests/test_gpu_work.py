@@ -46,11 +46,21 @@ def expected_work(src, dst, n):
     W = (du + dv).sum()
     assert W == (deg * dp).sum()  # the two forms of the merge work agree
     assert dp.sum() == len(key)
+    # hub sets: the 2^12 .. 2^15 vertices highest in the (degree, id) order
+    order = np.lexsort((np.arange(n), deg))  # ascending degree, then id
+    rank = np.empty(n, np.int64)
+    rank[order] = np.arange(n)
+    hub = {}
+    for k in range(4):
+        size = 1 << (12 + k)
+        inside = (rank[u] >= n - size) & (rank[v] >= n - size)
+        hub[size] = int(np.minimum(du, dv)[inside].sum())
     return {"edges": len(key), "lookups": int(lookups), "inserts": int(inserts),
-            "merge_work": int(W), "max_out_degree": int(dp.max()) if n else 0}
+            "merge_work": int(W), "max_out_degree": int(dp.max()) if n else 0,
+            "hub_lookups": hub}
 
 
-@pytest.mark.parametrize("case", ["rmat12", "er", "k9", "rgg"])
+@pytest.mark.parametrize("case", ["rmat12", "er", "k9", "rgg", "rmat16"])
 def test_work_matches_oracle(tc, case):
     import torch
 
@@ -63,9 +73,12 @@ def test_work_matches_oracle(tc, case):
     elif case == "k9":
         src, dst = (np.asarray(x, np.int32) for x in np.triu_indices(9, 1))
         n = 9
-    else:
+    elif case == "rgg":
         src, dst = graphgen.rgg(1 << 13, graphgen.rgg_radius(1 << 13, 12.0), 6)
         n = 1 << 13
+    else:  # more vertices than the largest hub set
+        src, dst = graphgen.rmat(16, 16 << 16, 10)
+        n = 1 << 16
     want = expected_work(src, dst, n)
     want["triangles"] = oracle.forward(src, dst, n, per_vertex=False)["T"]
     want["vertices"] = n
@@ -73,5 +86,10 @@ def test_work_matches_oracle(tc, case):
                            torch.from_numpy(np.ascontiguousarray(dst, np.int32)).cuda(), n)
     assert got == want
     assert got["max_out_degree"] ** 2 <= 2 * got["edges"]
+    # nested hub sets: shares grow with |H| and reach all lookups once |H| >= n
+    hub = [got["hub_lookups"][1 << (12 + k)] for k in range(4)]
+    assert hub == sorted(hub) and hub[-1] <= got["lookups"]
+    if n <= 1 << 12:
+        assert hub == [got["lookups"]] * 4
     if case == "k9":  # K_n: d+ = n-1, ..., 0, so W = (n-1) C(n,2) and lookups = C(n,3)
         assert got["merge_work"] == 8 * 36 and got["lookups"] == 84 == got["triangles"]
