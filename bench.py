@@ -14,8 +14,11 @@ buffers (2.9 GB) are far larger than the 126 MB L2, so no flush is needed
 between steps.
 
 Printed: one JSON line on rank 0.  `value` is input pairs per second over
-all ranks (each rank counts its own replica of the graph: the graph fits one
-GPU and the path needs no exchange, so N GPUs run N independent copies).
+all ranks.  With N > 1 GPUs (torchrun) the ranks count ONE graph by default:
+every rank preprocesses its own copy, counts its share of the partner groups
+(tc_count_per_vertex_part) and one sum all-reduce joins the shares
+(Sec. III-E, strong scaling); `--replicas` lets each rank count its own copy
+instead (weak scaling).
 `--impl reference` times the CPU oracle (the paper's own baseline is a
 single-threaded CPU forward algorithm, Sec. IV) on a bounded sample of the
 same workload, on the host cores.
@@ -54,6 +57,9 @@ def parse_args():
     p.add_argument("--workload", default="rmat24")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-full", action="store_true",
+                   help="time the CPU oracle on the WHOLE workload (rmat24: about ten "
+                        "minutes on one core) instead of the bounded sample")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--total-only", action="store_true",
                    help="time tc_count (T only) instead of tc_count_per_vertex")
@@ -62,11 +68,11 @@ def parse_args():
     p.add_argument("--batch-graphs", type=int, default=4096)
     p.add_argument("--serve-graphs", type=int, default=2048,
                    help="requests per arrival rate in the serving run (0: skip it)")
-    p.add_argument("--shard", action="store_true",
-                   help="with several GPUs, count ONE graph: each rank counts its share of "
-                        "the partner groups and one sum all-reduce joins the shares "
-                        "(Sec. III-E; strong scaling).  Default: each rank counts its own "
-                        "replica (weak scaling)")
+    p.add_argument("--replicas", action="store_true",
+                   help="with several GPUs, let each rank count its own replica of the graph "
+                        "(weak scaling).  Default: all ranks count ONE graph, each its share "
+                        "of the partner groups, joined by one sum all-reduce (Sec. III-E; "
+                        "strong scaling)")
     return p.parse_args()
 
 
@@ -456,7 +462,7 @@ def run_ours(args, world, rank, local, pg):
     deg_out = torch.empty(n, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    sharded = args.shard and world > 1
+    sharded = world > 1 and not args.replicas
     if sharded:
         from paper_1503_00576_gb300.shard import count_sharded
 
@@ -543,11 +549,20 @@ def run_ours(args, world, rank, local, pg):
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        dt, pairs = time_oracle(src, dst, n, CPU_SAMPLE_PAIRS)
+        pairs_wanted = m_in if args.cpu_full else CPU_SAMPLE_PAIRS
+        dt, pairs = time_oracle(src, dst, n, pairs_wanted)
+        if pairs == m_in:
+            sample = ("the whole %s edge array (%d pairs), single-threaded C oracle, %.1f s"
+                      % (args.workload, pairs, dt))
+        else:
+            sample = ("first %d of the %d pairs of the %s edge array, single-threaded C "
+                      "oracle, %.1f s.  A bounded sample: the pairs are in random draw order, "
+                      "so this is a uniform edge sample -- a sparser graph with less merge "
+                      "work per edge than the whole, on which the oracle runs several times "
+                      "slower per edge (bench.py --cpu-full times the whole graph)"
+                      % (pairs, m_in, args.workload, dt))
         cpu = {"value": pairs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "first %d pairs of the %s edge array (a uniform edge sample: the "
-                         "pairs are in random draw order), single-threaded C oracle, "
-                         "%.1f s" % (pairs, args.workload, dt)}
+               "sample": sample, "seconds": round(dt, 2)}
     batched = None
     if not args.no_batched and world == 1:
         del s, d, t_out, deg_out

@@ -274,6 +274,13 @@ typedef struct tc_work {
 } tc_work;
 tc_status tc_count_work(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
                         tc_stream_t stream, tc_work *out);
+/* The same counters over the share that tc_count_part(part, parts) counts:
+ * lookups, inserts, merge work, hub lookups and triangles of its partner
+ * groups (edges, max_out_degree and vertices stay those of the whole
+ * graph).  Summing one of those counters over the parts gives
+ * tc_count_work's. */
+tc_status tc_count_work_part(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
+                             int32_t part, int32_t parts, tc_stream_t stream, tc_work *out);
 
 /*
  * Allocation-free count, for callers that cannot allocate device memory

@@ -51,7 +51,7 @@ EXPORTS = ("tc_count", "tc_count_per_vertex", "tc_count_part", "tc_count_per_ver
            "tc_count_per_vertex_host", "tc_workspace_bytes", "tc_count_ws", "tc_set_tuning",
            "tc_get_tuning", "tc_count_batch", "tc_engine_create", "tc_engine_submit",
            "tc_engine_wait", "tc_engine_submit_parts", "tc_engine_poll", "tc_engine_count",
-           "tc_engine_destroy", "tc_count_work", "tc_count_noalloc",
+           "tc_engine_destroy", "tc_count_work", "tc_count_work_part", "tc_count_noalloc",
            "tc_last_error", "tc_status_string", "tc_last_error_detail", "tc_launch_count",
            "tc_profile_enable", "tc_profile_read", "tc_phase_name",
            "tc_debug_set_wait_limit", "tc_debug_fail_allocations", "tc_debug_reset")
@@ -107,6 +107,7 @@ def _bind(lib):
         "tc_count_ws": ([vp, vp, i64, i32, vp, vp, sz, c.POINTER(u64)], c.c_int),
         "tc_count_noalloc": ([vp, vp, i64, i32, vp, c.POINTER(u64)], c.c_int),
         "tc_count_work": ([vp, vp, i64, i32, vp, vp], c.c_int),
+        "tc_count_work_part": ([vp, vp, i64, i32, i32, i32, vp, vp], c.c_int),
         "tc_set_tuning": ([c.POINTER(Tuning)], c.c_int),
         "tc_get_tuning": ([c.POINTER(Tuning)], c.c_int),
         "tc_count_batch": ([vp, vp, i32, vp, vp, vp, vp], c.c_int),
@@ -514,17 +515,18 @@ class Engine:
         self.close()
 
 
-def tc_count_work(src, dst, n: int, stream=None) -> dict:
+def tc_count_work(src, dst, n: int, stream=None, part: int = 0, parts: int = 1) -> dict:
     """Work of the counting phase for this graph (tc_work as a dict): hash
     lookups and inserts, the merge work W of a sorted-list merge, the largest
-    out-degree, m and T.  Instrumentation: runs the whole pipeline once."""
+    out-degree, m and T; with parts > 1, the work of share `part`
+    (tc_count_work_part).  Instrumentation: runs the whole pipeline once."""
     torch = _torch()
     dev = _edges(src, dst)
     w = Work()
     lib = load_library()
     with torch.cuda.device(dev):
-        rc = lib.tc_count_work(src.data_ptr(), dst.data_ptr(), src.numel(), n,
-                               _stream_of(stream, dev), ctypes.byref(w))
+        rc = lib.tc_count_work_part(src.data_ptr(), dst.data_ptr(), src.numel(), n, part, parts,
+                                    _stream_of(stream, dev), ctypes.byref(w))
     _check(rc)
     out = {f: int(getattr(w, f)) for f, _ in w._fields_ if f != "hub_lookups"}
     out["hub_lookups"] = {1 << (12 + i): int(w.hub_lookups[i]) for i in range(4)}

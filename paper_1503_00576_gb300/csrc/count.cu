@@ -89,9 +89,10 @@ __device__ __forceinline__ uint32_t table_slots(int32_t len, uint32_t capacity) 
 struct Lists {
   const int32_t *__restrict__ off;   // node array (rank space): list lengths
   const int32_t *__restrict__ voff;  // node array of col4, in 16-byte words (even)
-  const int32_t *__restrict__ col4;  // forward lists, each padded with -1 to whole 32-byte blocks
+  const int32_t *__restrict__ col4;  // forward lists, sorted, each padded with -1 to whole 32-byte blocks
   const int32_t *__restrict__ goff;  // partner-group offsets
   const int32_t *__restrict__ part;  // partners
+  const int32_t *__restrict__ pskip;  // per partner: leading blocks of its list skipped
 };
 
 // One hash set in shared memory.
@@ -321,16 +322,22 @@ __device__ __forceinline__ void probe_windows(const Lists &g, int32_t w, int32_t
 // to the counter beside w's slot.
 template <bool PV, int W>
 __device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__restrict__ part,
-                                            int32_t np, int32_t c0, int32_t cs,
-                                            const Table &tb, WarpScratch &ws, int64_t *t,
-                                            uint64_t &found_total, uint64_t &found_group) {
+                                            const int32_t *__restrict__ pskip, int32_t np,
+                                            int32_t c0, int32_t cs, const Table &tb,
+                                            WarpScratch &ws, int64_t *t, uint64_t &found_total,
+                                            uint64_t &found_group) {
   const int lane = threadIdx.x & 31;
   const int32_t j = c0 + lane;
   int32_t l = 0, dl = 0, vb = 0;
   if (lane < cs && j < np) {
     l = __ldg(part + j);
+    const int32_t skip = __ldg(pskip + j);
     dl = __ldg(g.off + l + 1) - __ldg(g.off + l);
     vb = __ldg(g.voff + l);
+    // the leading blocks of N+(l) below the hashed list's smallest id
+    // cannot meet it: stream from the first block that can
+    vb += 2 * skip;
+    dl = max(dl - 8 * skip, 0);
   }
   const uint32_t nonempty = __ballot_sync(kFull, dl > 0);
   if (nonempty == 0) return;
@@ -475,7 +482,7 @@ __device__ __forceinline__ void cta_groups(const Lists &g, const int32_t *__rest
         c = __shfl_sync(kFull, c, 0);
         cs = __shfl_sync(kFull, cs, 0);
         if ((int32_t)c >= np) break;
-        probe_chunk<PV, W>(g, g.part + pb, np, (int32_t)c, (int32_t)cs, tb, s_ws[warp], t,
+        probe_chunk<PV, W>(g, g.part + pb, g.pskip + pb, np, (int32_t)c, (int32_t)cs, tb, s_ws[warp], t,
                            found_total, found_group);
       }
       __syncthreads();
@@ -523,7 +530,7 @@ __device__ __forceinline__ void warp_groups(const Lists &g, const int32_t *__res
       __syncwarp();
       uint64_t found_group = 0;
       for (int32_t c0 = 0; c0 < np; c0 += 32)
-        probe_chunk<PV, kWindows>(g, g.part + pb, np, c0, 32, tb, ws, t, found_total,
+        probe_chunk<PV, kWindows>(g, g.part + pb, g.pskip + pb, np, c0, 32, tb, ws, t, found_total,
                                   found_group);
       if (PV || tg) {
         found_group = warp_sum_u64(found_group);
@@ -728,14 +735,15 @@ cudaError_t prepare_count_kernels() {
 }
 
 cudaError_t launch_count(const int32_t *off, const int32_t *voff, const int32_t *col4,
-                         const int32_t *goff, const int32_t *part, const int32_t *warp_groups,
+                         const int32_t *goff, const int32_t *part, const int32_t *pskip,
+                         const int32_t *warp_groups,
                          const int32_t *cta_groups, const int32_t *big_groups, int32_t n,
                          Ctrl *ctrl, int64_t *t, int64_t *tg, cudaStream_t st) {
   const bool pv = t != nullptr;
   CountGrid cg;
   cudaError_t e = count_grid(pv, &cg);
   if (e != cudaSuccess) return e;
-  const Lists g{off, voff, col4, goff, part};
+  const Lists g{off, voff, col4, goff, part, pskip};
   // the long lists first, on their own wide CTAs
   if (pv) {
     k_count_big<true><<<cg.big_blocks, kBigThreads, big_smem<true>(), st>>>(g, big_groups, n, ctrl,

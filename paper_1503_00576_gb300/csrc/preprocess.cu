@@ -278,10 +278,12 @@ template <int MODE>
 __device__ __forceinline__ void radix_out(uint64_t key, uint32_t pos, void *__restrict__ out,
                                           uint32_t col_mask, uint32_t *__restrict__ row_out,
                                           int owner_shift, int32_t *outdeg, uint32_t active) {
-  if (MODE == kOutColRow) {
-    const uint32_t owner = (uint32_t)(key >> owner_shift);
+  if (MODE == kOutColRow || MODE == kOutPartSkip) {
+    const uint32_t owner = MODE == kOutColRow ? (uint32_t)(key >> owner_shift)
+                                              : (uint32_t)(key >> owner_shift) & col_mask;
     ((uint32_t *)out)[pos] = (uint32_t)key & col_mask;
-    if (row_out) row_out[pos] = owner;
+    if (MODE == kOutPartSkip) row_out[pos] = (uint32_t)(key >> kSkipShift);
+    else if (row_out) row_out[pos] = owner;
     // the staged tile is in owner order: consecutive lanes share owners,
     // and one atomic per run gives the out-degrees (the node array's counts)
     const uint32_t peers = __match_any_sync(active, owner);
@@ -775,7 +777,11 @@ void launch_radix_pass(const uint64_t *in, void *out, RadixOut mode, uint32_t *r
                        unsigned long long *status, uint32_t *ticket, Ctrl *ctrl,
                        cudaStream_t st) {
   const uint32_t grid = max(1u, (n_keys_bound + kSortTile - 1) / kSortTile);
-  if (mode == kOutColRow)
+  if (mode == kOutPartSkip)
+    k_radix_pass<kOutPartSkip><<<grid, kSortThreads, 0, st>>>(
+        in, out, n_keys_bound, n_keys_dev, shift, col_mask, row_out, owner_shift, outdeg, hist,
+        status, ticket, ctrl);
+  else if (mode == kOutColRow)
     k_radix_pass<kOutColRow><<<grid, kSortThreads, 0, st>>>(
         in, out, n_keys_bound, n_keys_dev, shift, col_mask, row_out, owner_shift, outdeg, hist,
         status, ticket, ctrl);

@@ -223,6 +223,8 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   int32_t *cta_groups = reinterpret_cast<int32_t *>(ws + L.cta_groups);
   int32_t *big_groups = reinterpret_cast<int32_t *>(ws + L.big_groups);
   int32_t *rank = reinterpret_cast<int32_t *>(ws + L.rank);
+  // smallest entry of every forward list (the rank keys are free by then)
+  int32_t *lmin = reinterpret_cast<int32_t *>(ws + L.vkeys_b);
   // per-vertex counts, or per-group totals of a batch, in rank space
   int64_t *t_rank = (t_out || batch) ? reinterpret_cast<int64_t *>(ws + L.t_rank) : nullptr;
   // group totals back in union ids (the rank keys are free by then)
@@ -332,24 +334,32 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   pt.stop(TC_PHASE_OFFSETS);
 
   // partner groups: each forward edge goes to the endpoint with the longer
-  // forward list.  Group keys go to `in` (sort 2's input, free now) and the
-  // same pass copies the lists into the padded column array col4; a radix
-  // sort over the group bits then gathers every group's partners, its last
-  // pass counting the group sizes into gcnt (the out-degree array's space).
+  // forward list.  First every list is sorted into the padded column array
+  // col4 (lmin: each list's smallest entry; the warp-group list is free
+  // scratch until the binning).  Group keys, read from the sorted lists, go
+  // to `in` (sort 2's input, free now); a radix sort over the group bits
+  // then gathers every group's partners, its last pass counting the group
+  // sizes into gcnt (the out-degree array's space) and writing the skipped
+  // blocks of each partner's stream beside the partner array.
   pt.start(TC_PHASE_GROUPS);
-  launch_group_keys(row, col, off, voff, m, b, passes3, tune.heavy_ratio_pct, ctrl, in,
-                    hist + 256 * kGroupSlot, col4, st);
+  launch_sort_lists(col, off, voff, n, ctrl, col4, lmin, warp_groups, st);
+  launch_group_keys(row, col4, off, voff, lmin, m, b, passes3, tune.heavy_ratio_pct, ctrl, in,
+                    hist + 256 * kGroupSlot, st);
   int32_t *gcnt = outdeg;
   TC_CUDA(cudaMemsetAsync(gcnt, 0, sizeof(int32_t) * (size_t)n, st), "memset groups");
+  const bool skip_in_key = 2 * b <= kSkipShift;
   uint64_t *gin = in, *gout = out;  // row and col are dead after the group keys
   for (int p = 0; p < passes3; ++p) {
     unsigned long long *status;
     uint32_t *ticket;
     next_pass(&status, &ticket);
     const bool last = p == passes3 - 1;
-    launch_radix_pass(gin, gout, last ? kOutColRow : kOutKeys, nullptr, last ? gcnt : nullptr, m,
-                      &ctrl->m, b + 8 * p, id_mask, b, hist + 256 * (kGroupSlot + p), status,
-                      ticket, ctrl, st);
+    // the last pass writes the partners l (first half of gout) and the
+    // blocks their streams skip (second half)
+    const RadixOut mode = !last ? kOutKeys : skip_in_key ? kOutPartSkip : kOutColRow;
+    uint32_t *skip_target = last && skip_in_key ? reinterpret_cast<uint32_t *>(gout) + m : nullptr;
+    launch_radix_pass(gin, gout, mode, skip_target, last ? gcnt : nullptr, m, &ctrl->m, b + 8 * p,
+                      id_mask, b, hist + 256 * (kGroupSlot + p), status, ticket, ctrl, st);
     if (!last) {
       uint64_t *x = gin;
       gin = gout;
@@ -357,16 +367,22 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
     }
   }
   const int32_t *part = reinterpret_cast<const int32_t *>(gout);
+  const int32_t *pskip = reinterpret_cast<const int32_t *>(gout) + m;
+  if (!skip_in_key)  // ids of more than 24 bits leave no room for the skip: stream lists whole
+    TC_CUDA(cudaMemsetAsync(reinterpret_cast<int32_t *>(gout) + m, 0, sizeof(int32_t) * (size_t)m,
+                            st),
+            "memset skips");
   // only this run's share of the groups is binned (all of them unless the
   // counting is split over several devices, Sec. III-E)
   launch_offsets(gcnt, n, goff, off, warp_groups, cta_groups, big_groups, tune, st_scan2,
                  &ctrl->tile_ticket[kTicketGroupScan], ctrl, st, shard, shards);
   pt.stop(TC_PHASE_GROUPS);
-  if (work_stats) launch_work(off, goff, part, n, ctrl, st);
+  if (work_stats) launch_work(off, goff, part, pskip, n, ctrl, st, shard, shards);
 
   pt.start(TC_PHASE_COUNT);
-  cudaError_t e = launch_count(off, voff, col4, goff, part, warp_groups, cta_groups, big_groups,
-                               n, ctrl, t_out ? t_rank : nullptr, t_out ? nullptr : t_rank, st);
+  cudaError_t e = launch_count(off, voff, col4, goff, part, pskip, warp_groups, cta_groups,
+                               big_groups, n, ctrl, t_out ? t_rank : nullptr,
+                               t_out ? nullptr : t_rank, st);
   if (e == cudaSuccess && t_out) launch_gather_counts(t_rank, rank, n, t_out, ctrl, st);
   if (e == cudaSuccess && batch) {
     if (t_out) {  // per graph: (sum of t) / 3
@@ -1048,12 +1064,14 @@ tc_status tc_engine_count(tc_engine *e, const int32_t *src, const int32_t *dst,
   return tc_engine_wait(e, totals_out);
 }
 
-tc_status tc_count_work(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
-                        tc_stream_t stream, tc_work *out) {
+tc_status tc_count_work_part(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
+                             int32_t part, int32_t parts, tc_stream_t stream, tc_work *out) {
   if (!out) return set_status(TC_ERR_INVALID_ARG, "out is NULL");
   memset(out, 0, sizeof(*out));
   tc_status s = check_args(src, dst, m, n);
   if (s != TC_OK) return s;
+  if (parts < 1 || part < 0 || part >= parts)
+    return set_status(TC_ERR_INVALID_ARG, "part %d of %d", part, parts);
   if (m > 0 && n == 0) return set_status(TC_ERR_ID_RANGE, "n = 0 but m > 0");
   out->vertices = n;
   if (m == 0) return set_status(TC_OK);
@@ -1066,7 +1084,7 @@ tc_status tc_count_work(const int32_t *src, const int32_t *dst, int64_t m, int32
   PhaseTimer pt(st, false);
   if (!h) s = set_status(TC_ERR_OOM, "pinned staging buffer");
   else s = enqueue_core(src, dst, m, n, st, ws, L, nullptr, nullptr, nullptr, current_tuning(), pt,
-                        h, true);
+                        h, true, part, parts);
   cudaFreeAsync(ws, st);
   const cudaError_t e = cudaStreamSynchronize(st);
   if (s != TC_OK) return s;
@@ -1082,6 +1100,11 @@ tc_status tc_count_work(const int32_t *src, const int32_t *dst, int64_t m, int32
   out->max_out_degree = (int32_t)h->work[3];
   for (int k = 0; k < kHubSizes; ++k) out->hub_lookups[k] = (int64_t)h->work[4 + k];
   return set_status(TC_OK);
+}
+
+tc_status tc_count_work(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
+                        tc_stream_t stream, tc_work *out) {
+  return tc_count_work_part(src, dst, m, n, 0, 1, stream, out);
 }
 
 tc_status tc_engine_destroy(tc_engine *e) {

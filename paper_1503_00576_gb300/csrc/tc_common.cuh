@@ -21,6 +21,17 @@ enum : uint32_t { kErrIdRange = 1u, kErrTimeout = 2u };
 // is set (see aborted()), so no kernel runs on incomplete data.
 constexpr uint32_t kSpinLimit = 1u << 24;
 
+// Sorted forward lists (the padded column array col4).  Lists of up to
+// kWarpSortMax entries are sorted by one warp, up to kCtaSortMax by a CTA;
+// longer ones (never met in the workloads: they need a dense core of more
+// than 8192 vertices) stay unsorted and are flagged in lmin (below).
+constexpr int kWarpSortMax = 512;
+constexpr int kCtaSortMax = 8192;
+// Group keys carry, above the 2b bits of h and l, the number of leading
+// 32-byte blocks of the streamed list that the intersection skips; there is
+// room for it when 2b <= kSkipShift.
+constexpr int kSkipShift = 48;
+
 constexpr int kMaxSort1Passes = 8;  // 2 * 31 id bits / 8-bit digits
 constexpr int kMaxSort2Passes = 4;  // 31 owner bits / 8-bit digits
 constexpr int kMaxRankPasses = 4;   // 31 degree bits / 8-bit digits
@@ -49,7 +60,9 @@ struct Ctrl {
   uint32_t next_big_group;
   unsigned long long total;        // triangle count T
   uint32_t m_in;                   // input pairs that are real (not batch padding)
-  uint32_t pad[1];
+  uint32_t n_long_lists;           // forward lists sorted by the long-list kernel
+  uint32_t next_long_list;         // its work cursor
+  uint32_t pad[3];
   // work of the counting phase (filled only when asked for; see launch_work):
   // hash lookups, hash inserts, merge work W, max out-degree, then the
   // lookups of edges with both endpoints among the 2^12 .. 2^15 top ranks
@@ -79,6 +92,11 @@ constexpr unsigned long long kValueMask = (1ull << 62) - 1;
 __device__ __forceinline__ bool aborted(const Ctrl *ctrl) {
   return (*(const volatile uint32_t *)&ctrl->err & kErrTimeout) != 0u;
 }
+
+// lmin[v] describes forward list v: its smallest entry if the list is
+// sorted, -1 - (its smallest entry) if it was left unsorted, INT32_MAX if
+// it is empty.
+__device__ __forceinline__ int32_t list_min(int32_t lm) { return lm >= 0 ? lm : -1 - lm; }
 #endif
 
 // Partner groups whose hashed forward list has at most kWarpMaxRow entries
@@ -217,7 +235,10 @@ void launch_canon(const int32_t *src, const int32_t *dst, uint32_t m_in, int32_t
 // sorted position (to `out`).
 // kOutKeysDeg: keys out, and deg[key & col_mask] += 1 for every key but the
 // sentinel (the pass after which equal low fields are adjacent).
-enum RadixOut { kOutKeys = 0, kOutColRow = 1, kOutRank = 2, kOutKeysDeg = 3 };
+// kOutPartSkip: the group sort's last pass: low bits to `out` (partners),
+// key >> kSkipShift to `row_out` (skipped blocks) and the group sizes (the
+// field at owner_shift, under col_mask) added to `outdeg`.
+enum RadixOut { kOutKeys = 0, kOutColRow = 1, kOutRank = 2, kOutKeysDeg = 3, kOutPartSkip = 4 };
 void launch_radix_pass(const uint64_t *in, void *out, RadixOut mode, uint32_t *row_out,
                        int32_t *outdeg, uint32_t n_keys_bound, const uint32_t *n_keys_dev,
                        int shift, uint32_t col_mask, int owner_shift, const uint32_t *hist,
@@ -247,25 +268,35 @@ void launch_word_offsets(const int32_t *counts, int32_t n, int32_t *voff,
                          unsigned long long *status, uint32_t *ticket, Ctrl *ctrl,
                          cudaStream_t st);
 // ---- launchers (group.cu) ----
-// Group keys h << b | l of every forward edge (h: the endpoint with the
-// longer forward list, l: the other one), with the digit histograms of the
-// h field for the group sort; also copies every forward list into the
-// padded column array col4 (list v starts at 16-byte word voff[v], always
-// even; the rest of its last 32-byte block is -1).
-void launch_group_keys(const int32_t *row, const int32_t *col, const int32_t *off,
-                       const int32_t *voff, uint32_t m_bound, int b, int passes,
-                       int32_t heavy_ratio_pct, Ctrl *ctrl, uint64_t *gkeys, uint32_t *hist,
-                       int32_t *col4, cudaStream_t st);
+// Sorts every forward list (the column array col, grouped by owner, node
+// array off) into the padded column array col4 (list v from 16-byte word
+// voff[v], padded with -1 to whole 32-byte blocks) and writes lmin.
+// long_lists: scratch of n entries.
+void launch_sort_lists(const int32_t *col, const int32_t *off, const int32_t *voff, int32_t n,
+                       Ctrl *ctrl, int32_t *col4, int32_t *lmin, int32_t *long_lists,
+                       cudaStream_t st);
+// Group keys s << kSkipShift | h << b | l of every forward edge (h: the
+// endpoint with the longer forward list, l: the other one, s: the leading
+// blocks of N+(l) the intersection skips, 0 when 2b > kSkipShift), with the
+// digit histograms of the h field for the group sort.  Reads the sorted
+// lists (col4, lmin) in owner order (row).
+void launch_group_keys(const int32_t *row, const int32_t *col4, const int32_t *off,
+                       const int32_t *voff, const int32_t *lmin, uint32_t m_bound, int b,
+                       int passes, int32_t heavy_ratio_pct, Ctrl *ctrl, uint64_t *gkeys,
+                       uint32_t *hist, cudaStream_t st);
 // Instrumentation: adds the counting phase's work into ctrl->work (from the
-// partner groups and the node array).
-void launch_work(const int32_t *off, const int32_t *goff, const int32_t *part, int32_t n,
-                 Ctrl *ctrl, cudaStream_t st);
+// partner groups, the node array and the skipped blocks), over the groups h
+// with h mod shards = shard (the share one part counts).
+void launch_work(const int32_t *off, const int32_t *goff, const int32_t *part,
+                 const int32_t *pskip, int32_t n, Ctrl *ctrl, cudaStream_t st,
+                 int32_t shard = 0, int32_t shards = 1);
 // ---- launchers (count.cu) ----
 // t != nullptr: per-vertex counts (rank space).  Otherwise, if tg is not
 // nullptr, tg[h] += triangles found in group h (their sum per graph is the
 // graph's count).
 cudaError_t launch_count(const int32_t *off, const int32_t *voff, const int32_t *col4,
-                         const int32_t *goff, const int32_t *part, const int32_t *warp_groups,
+                         const int32_t *goff, const int32_t *part, const int32_t *pskip,
+                         const int32_t *warp_groups,
                          const int32_t *cta_groups, const int32_t *big_groups, int32_t n,
                          Ctrl *ctrl, int64_t *t, int64_t *tg, cudaStream_t st);
 // Sets the counting kernels' attributes and occupancy for the current

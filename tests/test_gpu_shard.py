@@ -48,6 +48,21 @@ def test_total_shares_add_up(tc, rmat16, parts):
         assert max(shares) < 1.4 * whole / parts
 
 
+@pytest.mark.parametrize("parts", [2, 3, 8])
+def test_shares_carry_like_work(tc, rmat16, parts):
+    """Every share's counting work (hash lookups of its partner groups,
+    tc_count_work_part) is within 10% of an equal split, and the shares'
+    work adds up to the whole graph's."""
+    s, d, n = rmat16
+    whole = tc.tc_count_work(s, d, n)
+    shares = [tc.tc_count_work(s, d, n, part=p, parts=parts) for p in range(parts)]
+    for key in ("lookups", "inserts", "merge_work", "triangles"):
+        assert sum(w[key] for w in shares) == whole[key], key
+    mean = whole["lookups"] / parts
+    for w in shares:
+        assert 0.9 * mean < w["lookups"] < 1.1 * mean, [x["lookups"] for x in shares]
+
+
 def test_per_vertex_shares_add_up_to_the_oracle(tc):
     src, dst = graphgen.rmat(12, 16 << 12, 22)
     n = 1 << 12
