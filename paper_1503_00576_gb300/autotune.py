@@ -20,16 +20,16 @@ import numpy as np
 from . import DEFAULT_TUNING, Engine, _torch, tc_count, tc_set_tuning
 from .batching import Capacity, plan_subbatches
 
-CANDIDATES = [
-    dict(DEFAULT_TUNING),
+CANDIDATES = [{**DEFAULT_TUNING, **c} for c in (
+    {},
     {"warp_max_list": 64, "warp_max_partners": 32, "heavy_ratio_pct": 100},
     {"warp_max_list": 128, "warp_max_partners": 128, "heavy_ratio_pct": 100},
     {"warp_max_list": 32, "warp_max_partners": 16, "heavy_ratio_pct": 100},
     {"warp_max_list": 128, "warp_max_partners": 64, "heavy_ratio_pct": 150},
     {"warp_max_list": 128, "warp_max_partners": 64, "heavy_ratio_pct": 300},
-]
+)]
 
-CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tuning_cache.json")
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tuning_cache_v2.json")
 
 
 def _device_key() -> str:

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libtc.so")
-SOURCES = ["preprocess.cu", "group.cu", "count.cu", "tc_api.cu"]
+SOURCES = ["preprocess.cu", "group.cu", "count.cu", "hub.cu", "tc_api.cu"]
 HEADERS = [os.path.join(CSRC, "tc_common.cuh"), os.path.join(INCLUDE, "tc.h"),
            os.path.join(INCLUDE, "tc_debug.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -280,6 +280,8 @@ k_group_keys(const int32_t *__restrict__ row, const int32_t *__restrict__ col4,
   __syncthreads();
   const uint32_t m = ctrl->m;
   const bool carry_skip = 2 * b <= kSkipShift;
+  const bool hub_on = carry_skip && ctrl->hub_on != 0u;
+  const int32_t hub_lo = (int32_t)ctrl->hub_lo;
   const uint32_t stride = gridDim.x * kGroupThreads;
   // kGroupUnroll edges per thread per round, each step's loads issued for
   // all of them together: the offsets are gathers that depend on the edge
@@ -313,9 +315,12 @@ k_group_keys(const int32_t *__restrict__ row, const int32_t *__restrict__ col4,
       if (e >= m) break;
       int32_t h, l;
       split_edge(u[q], v[q], ue[q] - ub[q], vd[q], heavy_ratio_pct, h, l);
-      // the list of u is sorted unless it was too long to sort (um < 0)
-      const uint64_t skip = (carry_skip && h == v[q] && um[q] >= 0)
-                                ? (uint64_t)(((int32_t)e - ub[q]) >> 3) : 0ull;
+      // the list of u is sorted unless it was too long to sort (um < 0); an
+      // edge inside the dense hub block (owner u, hence v, of rank >=
+      // hub_lo) is left to it: its stream is skipped whole
+      uint64_t skip = (carry_skip && h == v[q] && um[q] >= 0)
+                          ? (uint64_t)(((int32_t)e - ub[q]) >> 3) : 0ull;
+      if (hub_on && u[q] >= hub_lo) skip = kSkipAll;
       gkeys[e] = (skip << kSkipShift) | ((uint64_t)(uint32_t)h << b) | (uint32_t)l;
       for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p * 256 + ((h >> (8 * p)) & 255)], 1u);
     }

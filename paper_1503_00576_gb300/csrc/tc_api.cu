@@ -331,6 +331,10 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   launch_offsets(outdeg, n, off, nullptr, nullptr, nullptr, nullptr, tune, st_scan,
                  &ctrl->tile_ticket[kTicketScan], ctrl, st);
   launch_word_offsets(outdeg, n, voff, st_scan3, &ctrl->tile_ticket[kTicketVecScan], ctrl, st);
+  // whether the top ranks are counted densely (their edges are then left
+  // out of the partner groups)
+  const bool hub = L.has_hub && tune.hub_min_edges >= 0;
+  if (hub) launch_hub_decide(off, n, kHubSize, tune.hub_min_edges, ctrl, st);
   pt.stop(TC_PHASE_OFFSETS);
 
   // partner groups: each forward edge goes to the endpoint with the longer
@@ -380,6 +384,11 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   if (work_stats) launch_work(off, goff, part, pskip, n, ctrl, st, shard, shards);
 
   pt.start(TC_PHASE_COUNT);
+  if (hub) {
+    TC_CUDA(launch_hub_count(off, voff, col4, n, kHubSize, ws + L.hub, ctrl,
+                             t_out ? t_rank : nullptr, st),
+            "dense hub block");
+  }
   cudaError_t e = launch_count(off, voff, col4, goff, part, pskip, warp_groups, cta_groups,
                                big_groups, n, ctrl, t_out ? t_rank : nullptr,
                                t_out ? nullptr : t_rank, st);
@@ -403,6 +412,8 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
 tc_status finish_core(const Ctrl *h, int32_t n, uint64_t *total) {
   if (h->err & kErrTimeout)
     return set_status(TC_ERR_TIMEOUT, "a device-side wait reached its iteration limit");
+  if (h->err & kErrInternal)
+    return set_status(TC_ERR_CUDA, "the dense hub block failed its consistency check");
   if (h->err & kErrIdRange)
     return set_status(TC_ERR_ID_RANGE, "a vertex id is outside [0, %d) of its graph", n);
   if (total) *total = (uint64_t)h->total;
@@ -451,7 +462,7 @@ tc_status count_impl(const int32_t *src, const int32_t *dst, int64_t m, int32_t 
     *total = 0;
     return set_status(TC_OK);
   }
-  const Layout L = make_layout(m, n);
+  const Layout L = make_layout(m, n, true);
   if (ws_user) {
     if (ws_bytes < L.total)
       return set_status(TC_ERR_INVALID_ARG, "workspace has %zu bytes, needs %zu", ws_bytes,
@@ -887,7 +898,7 @@ tc_status tc_count_per_vertex_host(const int32_t *src_host, const int32_t *dst_h
 
 size_t tc_workspace_bytes(int64_t m, int32_t n) {
   if (m < 0 || n < 0 || m > (int64_t)INT32_MAX) return 0;
-  return make_layout(m, n).total;
+  return make_layout(m, n, true).total;
 }
 
 tc_status tc_count_ws(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
@@ -907,7 +918,7 @@ tc_status tc_count_noalloc(const int32_t *src, const int32_t *dst, int64_t m, in
     *total_out = 0;
     return set_status(TC_OK);
   }
-  const Layout L = make_layout(m, n);
+  const Layout L = make_layout(m, n, true);
   if (L.total > (size_t)TC_NOALLOC_SCRATCH_BYTES)
     return set_status(TC_ERR_OVERFLOW,
                       "m=%lld, n=%d needs %zu bytes of scratch; the static scratch holds %zu",
@@ -941,7 +952,7 @@ tc_status tc_engine_create(int64_t max_pairs, int32_t max_vertices, int32_t max_
   e->max_vertices = max_vertices;
   e->max_graphs = max_graphs;
   e->tune = tuning ? Tuning{tuning->warp_max_list, tuning->warp_max_partners,
-                            max(tuning->heavy_ratio_pct, 100)}
+                            max(tuning->heavy_ratio_pct, 100), tuning->hub_min_edges}
                    : current_tuning();
   tc_status s = engine_build(e);
   if (s != TC_OK) {
@@ -1076,7 +1087,7 @@ tc_status tc_count_work_part(const int32_t *src, const int32_t *dst, int64_t m, 
   out->vertices = n;
   if (m == 0) return set_status(TC_OK);
   cudaStream_t st = (cudaStream_t)stream;
-  const Layout L = make_layout(m, n);
+  const Layout L = make_layout(m, n, true);
   keep_pool_memory();
   unsigned char *ws = nullptr;
   TC_CUDA(dev_alloc_async((void **)&ws, L.total, st), "workspace allocation");
@@ -1116,7 +1127,8 @@ tc_status tc_set_tuning(const tc_tuning *t) {
   if (t && (t->warp_max_list < 0 || t->warp_max_partners < 0 || t->heavy_ratio_pct < 100))
     return set_status(TC_ERR_INVALID_ARG, "tuning values out of range");
   std::lock_guard<std::mutex> lk(g_tuning_mu);
-  g_tuning = t ? Tuning{t->warp_max_list, t->warp_max_partners, t->heavy_ratio_pct}
+  g_tuning = t ? Tuning{t->warp_max_list, t->warp_max_partners, t->heavy_ratio_pct,
+                        t->hub_min_edges}
                : kDefaultTuning;
   return set_status(TC_OK);
 }
@@ -1127,6 +1139,7 @@ tc_status tc_get_tuning(tc_tuning *out) {
   out->warp_max_list = t.warp_max_list;
   out->warp_max_partners = t.warp_max_partners;
   out->heavy_ratio_pct = t.heavy_ratio_pct;
+  out->hub_min_edges = t.hub_min_edges;
   return set_status(TC_OK);
 }
 

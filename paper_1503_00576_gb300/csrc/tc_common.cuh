@@ -8,7 +8,7 @@
 namespace tc {
 
 // Device-side error bits (Ctrl::err).
-enum : uint32_t { kErrIdRange = 1u, kErrTimeout = 2u };
+enum : uint32_t { kErrIdRange = 1u, kErrTimeout = 2u, kErrInternal = 4u };
 
 // Upper bound on iterations of any spin-wait in a kernel.  Every wait in this
 // library is on a predecessor tile that is already resident (tiles are handed
@@ -31,6 +31,17 @@ constexpr int kCtaSortMax = 8192;
 // 32-byte blocks of the streamed list that the intersection skips; there is
 // room for it when 2b <= kSkipShift.
 constexpr int kSkipShift = 48;
+// Skip value of an edge whose triangles the dense hub block counts: the
+// streamed list is skipped whole.
+constexpr uint32_t kSkipAll = 0xFFFFu;
+
+// Dense hub block (hub.cu): the kHubSize vertices of highest rank, counted
+// on the tensor cores when they hold at least kHubMinEdges edges.  Only for
+// single graphs with n >= kHubMinVertices and ids of at most 24 bits (the
+// group keys must carry the skips).
+constexpr int32_t kHubSize = 1 << 14;
+constexpr int32_t kHubMinVertices = 1 << 17;
+constexpr int64_t kHubMinEdges = 1 << 21;
 
 constexpr int kMaxSort1Passes = 8;  // 2 * 31 id bits / 8-bit digits
 constexpr int kMaxSort2Passes = 4;  // 31 owner bits / 8-bit digits
@@ -62,7 +73,9 @@ struct Ctrl {
   uint32_t m_in;                   // input pairs that are real (not batch padding)
   uint32_t n_long_lists;           // forward lists sorted by the long-list kernel
   uint32_t next_long_list;         // its work cursor
-  uint32_t pad[3];
+  uint32_t hub_on;                 // the hub block is counted densely (hub.cu)
+  uint32_t hub_lo;                 // its first rank
+  uint32_t pad[1];
   // work of the counting phase (filled only when asked for; see launch_work):
   // hash lookups, hash inserts, merge work W, max out-degree, then the
   // lookups of edges with both endpoints among the 2^12 .. 2^15 top ranks
@@ -112,8 +125,10 @@ struct Tuning {
   int32_t warp_max_partners;  //   at most this many entries and partners
   int32_t heavy_ratio_pct;    // edge (u,v) is grouped at v when |N+(v)| * 100 >
                               //   |N+(u)| * heavy_ratio_pct, else at its owner u
+  int64_t hub_min_edges;      // the dense hub block runs when it holds at least
+                              //   this many edges (< 0: never)
 };
-constexpr Tuning kDefaultTuning = {128, 64, 100};
+constexpr Tuning kDefaultTuning = {128, 64, 100, kHubMinEdges};
 
 // A batch of graphs counted as one disjoint union (device-side descriptor).
 // Graph g owns input pairs [edge_off[g], edge_off[g+1]) and union vertex ids
@@ -134,6 +149,8 @@ struct Layout {
   size_t keys_a, keys_b, deg, outdeg, off, voff, goff, warp_groups, cta_groups, big_groups;
   size_t col4;
   size_t rank, vkeys_a, vkeys_b, t_rank;
+  size_t hub;  // dense hub block (0 bytes unless the layout asked for it)
+  bool has_hub;
   size_t total;
   uint32_t sort_tiles, orient_tiles, scan_tiles;
   size_t st_sort_words_per_pass;
@@ -166,7 +183,10 @@ inline int id_bits(int32_t n) {
 // the group keys (group bits).
 inline int radix_passes(int b) { return (2 * b + 7) / 8 + 3 * ((b + 7) / 8); }
 
-inline Layout make_layout(int64_t m_in, int32_t n) {
+// Whether a single-graph run of n vertices has the dense hub block.
+inline bool hub_enabled(int32_t n, int b) { return n >= kHubMinVertices && 2 * b <= kSkipShift; }
+
+inline Layout make_layout(int64_t m_in, int32_t n, bool with_hub = false) {
   Layout L{};
   size_t p = 0;
   auto take = [&](size_t bytes) {
@@ -208,6 +228,9 @@ inline Layout make_layout(int64_t m_in, int32_t n) {
   // forward lists padded to whole 32-byte blocks: at most m + 7 min(n, m)
   // elements, since each non-empty list adds at most 7
   L.col4 = take(sizeof(int32_t) * (m + 7 * (nv < m ? nv : m)));
+  const bool hub = with_hub && hub_enabled(n, id_bits(n > 0 ? n : 1));
+  L.hub = take(hub ? (size_t)kHubSize * kHubSize + 4 * (size_t)kHubSize : 0);
+  L.has_hub = hub;
   L.total = p;
   return L;
 }
@@ -267,6 +290,20 @@ void launch_offsets(const int32_t *counts, int32_t n, int32_t *off, const int32_
 void launch_word_offsets(const int32_t *counts, int32_t n, int32_t *voff,
                          unsigned long long *status, uint32_t *ticket, Ctrl *ctrl,
                          cudaStream_t st);
+// ---- launchers (hub.cu) ----
+// Workspace of the dense hub block of H vertices: the H x H fp8 matrix and
+// the per-vertex sums.
+size_t hub_bytes(int32_t H);
+// Decides (on the device, into ctrl->hub_on) whether the top H ranks are
+// counted densely: needs the node array.
+void launch_hub_decide(const int32_t *off, int32_t n, int32_t H, int64_t min_edges, Ctrl *ctrl,
+                       cudaStream_t st);
+// Counts the triangles inside the hub block (if ctrl->hub_on): adds them to
+// ctrl->total and, if t != nullptr, to the per-vertex counts t (rank space).
+// Needs the sorted lists; region: hub_bytes(H) bytes, 256-byte aligned.
+cudaError_t launch_hub_count(const int32_t *off, const int32_t *voff, const int32_t *col4,
+                             int32_t n, int32_t H, uint8_t *region, Ctrl *ctrl, int64_t *t,
+                             cudaStream_t st);
 // ---- launchers (group.cu) ----
 // Sorts every forward list (the column array col, grouped by owner, node
 // array off) into the padded column array col4 (list v from 16-byte word
