@@ -378,29 +378,44 @@ __device__ __forceinline__ void radix_tile(RadixShared &S, const uint64_t *__res
     // decoupled look-back for this digit
     uint64_t excl = 0;
     if (tile > 0) {
+      // the statuses of kLookback predecessors are read at once (one memory
+      // latency per round), then summed back to the nearest inclusive one;
+      // a round stops early at a predecessor that has not published yet
+      constexpr int kLookback = 4;
       int64_t j = (int64_t)tile - 1;
       uint32_t spins = 0;
       const uint32_t limit = g_spin_limit;
-      bool bad = false;
-      while (j >= 0) {
-        const unsigned long long s = ld_volatile_u64(status + (size_t)j * 256 + tid);
-        const unsigned long long flag = s & ~kValueMask;
-        if (flag == 0) {
+      bool bad = false, done = false;
+      while (!done) {
+        unsigned long long s[kLookback];
+#pragma unroll
+        for (int q = 0; q < kLookback; ++q)
+          s[q] = j - q >= 0 ? ld_volatile_u64(status + (size_t)(j - q) * 256 + tid)
+                            : kFlagInclusive;  // before tile 0: an inclusive zero
+        int used = 0;
+#pragma unroll
+        for (int q = 0; q < kLookback; ++q) {
+          if (done || used < q) break;
+          const unsigned long long flag = s[q] & ~kValueMask;
+          if (flag == 0) break;  // not published yet: read again from here
+          if (flag == kFlagPoison) {
+            bad = done = true;
+            break;
+          }
+          excl += s[q] & kValueMask;
+          used = q + 1;
+          if (flag == kFlagInclusive) done = true;
+        }
+        if (done) break;
+        j -= used;
+        if (used == 0) {
           if (++spins > limit) {
             atomicOr(&ctrl->err, kErrTimeout);
             bad = true;
             break;
           }
           if (spins > 64) __nanosleep(64);
-          continue;
         }
-        if (flag == kFlagPoison) {
-          bad = true;
-          break;
-        }
-        excl += s & kValueMask;
-        if (flag == kFlagInclusive) break;
-        --j;
       }
       if (publish) st_volatile_u64(st, bad ? kFlagPoison : kFlagInclusive | (excl + tile_cnt));
       if (bad) S.abort = 1u;
