@@ -150,6 +150,9 @@ k_sort_lists(const int32_t *__restrict__ col, const int32_t *__restrict__ off,
   if (aborted(ctrl)) return;  // an earlier wait of this call ran out
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t warps = gridDim.x * kListWarps;
+  // lists of the dense hub block need no order: the hash path skips their
+  // streams whole and hashes them as they come
+  const uint32_t unsorted_from = ctrl->hub_on ? ctrl->hub_lo : 0xffffffffu;
   for (uint32_t c = blockIdx.x * kListWarps + warp; c * 32u < (uint32_t)n; c += warps) {
     const uint32_t v = c * 32u + lane;
     int32_t b = 0, d = 0;
@@ -159,6 +162,18 @@ k_sort_lists(const int32_t *__restrict__ col, const int32_t *__restrict__ off,
       d = __ldg(off + v + 1) - b;
       w4 = 4ll * __ldg(voff + v);
       if (d == 0) lmin[v] = INT32_MAX;
+    }
+    if (c * 32u >= unsorted_from) {  // a whole chunk of hub lists: copied as they are
+      const uint32_t copy = __ballot_sync(kFull, d > 0);
+      for (uint32_t todo = copy; todo; todo &= todo - 1) {
+        const int src = __ffs(todo) - 1;
+        const int32_t lb = __shfl_sync(kFull, b, src), ld = __shfl_sync(kFull, d, src);
+        const long long lw = __shfl_sync(kFull, w4, src);
+        const int r8 = (ld + 7) & ~7;
+        for (int i = lane; i < r8; i += 32) col4[lw + i] = i < ld ? __ldg(col + lb + i) : -1;
+      }
+      if (d > 0) lmin[v] = INT32_MIN;  // unsorted
+      continue;
     }
     if (d > 0 && d <= 8) {
       int32_t x[8];
