@@ -168,12 +168,14 @@ tc_status tc_count_ws(const int32_t *src, const int32_t *dst, int64_t m, int32_t
  *     with owner u is counted by hashing N+(v) and streaming N+(u) when
  *     |N+(v)| * 100 > |N+(u)| * heavy_ratio_pct, else by hashing N+(u) and
  *     streaming N+(v).  100 (default) always streams the shorter list.
- *   hub_min_edges: single graphs of at least 2^17 vertices (ids of at most
- *     24 bits) count the triangles among their 2^14 highest-ranked vertices
- *     (the hub block: every forward neighbour of such a vertex is one too)
- *     as a dense 0/1 matrix product on the tensor cores when that block
- *     holds at least this many edges; < 0 never.  Default 2^21.  Batches
- *     and engines never use it.
+ *   hub_min_edges, hub_vertices: single graphs of at least 2^17 vertices
+ *     (ids of at most 24 bits) count the triangles among their hub_vertices
+ *     highest-ranked vertices (the hub block: every forward neighbour of
+ *     such a vertex is one too) as a dense 0/1 matrix product on the tensor
+ *     cores when that block holds at least hub_min_edges edges; < 0 never.
+ *     hub_vertices is a multiple of 128 from 128 to 32768 (the workspace
+ *     grows by its square in bytes).  Defaults 2^21 and 16384.  Batches and
+ *     engines never use it.
  * tc_set_tuning(NULL) restores the defaults.
  */
 typedef struct tc_tuning {
@@ -181,6 +183,7 @@ typedef struct tc_tuning {
   int32_t warp_max_partners;
   int32_t heavy_ratio_pct;
   int64_t hub_min_edges;
+  int32_t hub_vertices;
 } tc_tuning;
 tc_status tc_set_tuning(const tc_tuning *tuning);
 tc_status tc_get_tuning(tc_tuning *out);

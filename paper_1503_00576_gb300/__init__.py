@@ -68,14 +68,15 @@ class Work(ctypes.Structure):
 class Tuning(ctypes.Structure):
     """tc_tuning: how partner groups map onto warps/CTAs and which list is hashed."""
     _fields_ = [("warp_max_list", ctypes.c_int32), ("warp_max_partners", ctypes.c_int32),
-                ("heavy_ratio_pct", ctypes.c_int32), ("hub_min_edges", ctypes.c_int64)]
+                ("heavy_ratio_pct", ctypes.c_int32), ("hub_min_edges", ctypes.c_int64),
+                ("hub_vertices", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 DEFAULT_TUNING = {"warp_max_list": 128, "warp_max_partners": 64, "heavy_ratio_pct": 100,
-                  "hub_min_edges": 1 << 21}
+                  "hub_min_edges": 1 << 21, "hub_vertices": 1 << 14}
 
 
 class TCError(RuntimeError):

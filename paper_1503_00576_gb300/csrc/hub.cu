@@ -196,24 +196,99 @@ __device__ __forceinline__ int32_t column_sums32(int32_t (&v)[32]) {
 // kernels
 // ---------------------------------------------------------------------------
 
-// Whether the dense block is worth its fixed cost: only if H holds at
-// least min_edges edges (the forward lists of ranks [lo, n): m - off[lo]).
-__global__ void k_hub_decide(const int32_t *__restrict__ off, int32_t lo, int64_t min_edges,
-                             Ctrl *ctrl) {
+// Which hub set, if any, is worth its cost.  The candidates are the top
+// Hmax/4, Hmax/2, 3Hmax/4 and Hmax ranks (multiples of 128).  For every
+// edge inside the largest one, the hash lookups it would cost
+// (min(d+(u), d+(v)), before skipping) are added to the smallest candidate
+// that holds it: one warp per owner u.
+__device__ __forceinline__ int32_t hub_candidate(int32_t Hmax, int k) {
+  return ((Hmax * (k + 1) / 4) / 128) * 128;
+}
+
+__global__ void __launch_bounds__(256)
+k_hub_estimate(const int32_t *__restrict__ off, const int32_t *__restrict__ col, int32_t n,
+               int32_t Hmax, Ctrl *ctrl) {
   if (aborted(ctrl)) return;
-  const int64_t inside = (int64_t)ctrl->m - (int64_t)__ldg(off + lo);
-  ctrl->hub_on = inside >= min_edges ? 1u : 0u;
-  ctrl->hub_lo = (uint32_t)lo;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * (blockDim.x / 32);
+  unsigned long long acc[4] = {0, 0, 0, 0};
+  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < (uint32_t)Hmax;
+       w += warps) {
+    const int32_t u = n - Hmax + (int32_t)w;
+    const int32_t du = __ldg(off + u + 1) - __ldg(off + u);
+    // the smallest candidate holding u (and so every forward neighbour)
+    int k = 3;
+    while (k > 0 && n - hub_candidate(Hmax, k - 1) <= u) --k;
+    unsigned long long sum = 0;
+    for (int32_t i = lane; i < du; i += 32) {
+      const int32_t v = __ldg(col + __ldg(off + u) + i);
+      const int32_t dv = __ldg(off + v + 1) - __ldg(off + v);
+      sum += (unsigned long long)min(du, dv);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] += q == k ? sum : 0ull;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(kFull, acc[q], o);
+    if (lane == 0 && acc[q]) atomicAdd(&ctrl->hub_est[q], acc[q]);
+  }
+}
+
+// Cost model (GB300, measured on R-MAT scale 20 and 24 over hub sizes of
+// 8192 to 24576): a lookup taken off the hash path saves about 0.63 ps of
+// the whole GPU's time (total only) or 1.03 ps (per-vertex counts, whose
+// match counters go too); the dense block costs about 0.15 ms plus
+// 1.55 ms (H / 16384)^3.
+// The candidate with the largest saving is used if it saves anything.
+// force (hub_min_edges == 0): the largest candidate, whatever the model.
+__global__ void k_hub_decide(const int32_t *__restrict__ off, int32_t n, int32_t Hmax,
+                             int64_t min_edges, int per_vertex, Ctrl *ctrl) {
+  if (aborted(ctrl)) return;
+  const double ms_per_lookup = per_vertex ? 1.03e-9 : 0.63e-9;
+  double best = 0.0;
+  int32_t H = 0;
+  unsigned long long inside = 0;
+  for (int k = 0; k < 4; ++k) {
+    inside += ctrl->hub_est[k];  // lookups inside candidate k (cumulative)
+    const int32_t h = hub_candidate(Hmax, k);
+    const double x = (double)h / 16384.0;
+    const double gain = (double)inside * ms_per_lookup - (0.15 + 1.55 * x * x * x);
+    const int64_t edges = (int64_t)ctrl->m - (int64_t)__ldg(off + (n - h));
+    if (h > 0 && edges >= min_edges && gain > best) {
+      best = gain;
+      H = h;
+    }
+  }
+  if (min_edges == 0) H = Hmax;
+  ctrl->hub_on = H > 0 ? 1u : 0u;
+  ctrl->hub_size = (uint32_t)H;
+  ctrl->hub_lo = (uint32_t)(n - H);
+}
+
+// Zeroes the H x H corner (row pitch Hmax) of the hub matrix.
+__global__ void __launch_bounds__(256)
+k_hub_zero(uint8_t *__restrict__ A, int32_t Hmax, const Ctrl *ctrl) {
+  if (aborted(ctrl) || !ctrl->hub_on) return;
+  const uint32_t H = ctrl->hub_size;
+  const uint32_t words = H / 16;  // uint4 per row
+  const uint64_t total = (uint64_t)H * words;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t row = i / words, w = i % words;
+    reinterpret_cast<uint4 *>(A + row * (uint64_t)Hmax)[w] = make_uint4(0, 0, 0, 0);
+  }
 }
 
 // A(u - lo, v - lo) = A(v - lo, u - lo) = 1 for every forward edge of H
 // (the matrix was zeroed before).  One warp per vertex of H.
 __global__ void __launch_bounds__(256)
 k_hub_scatter(const int32_t *__restrict__ off, const int32_t *__restrict__ voff,
-              const int32_t *__restrict__ col4, int32_t n, int32_t H, const Ctrl *ctrl,
+              const int32_t *__restrict__ col4, int32_t n, int32_t pitch, const Ctrl *ctrl,
               uint8_t *__restrict__ A) {
   if (aborted(ctrl) || !ctrl->hub_on) return;
-  const int32_t lo = n - H;
+  const int32_t H = (int32_t)ctrl->hub_size, lo = n - H;
   const int lane = threadIdx.x & 31;
   const uint32_t warps = gridDim.x * (blockDim.x / 32);
   for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < (uint32_t)H; w += warps) {
@@ -222,8 +297,8 @@ k_hub_scatter(const int32_t *__restrict__ off, const int32_t *__restrict__ voff,
     const int32_t *list = col4 + 4ll * __ldg(voff + u);
     for (int32_t i = lane; i < d; i += 32) {
       const int32_t v = __ldg(list + i) - lo;  // > u - lo >= 0
-      A[(size_t)w * H + v] = kOne;
-      A[(size_t)v * H + w] = kOne;
+      A[(size_t)w * pitch + v] = kOne;
+      A[(size_t)v * pitch + w] = kOne;
     }
   }
 }
@@ -232,10 +307,15 @@ k_hub_scatter(const int32_t *__restrict__ off, const int32_t *__restrict__ voff,
 // column) sums.  Warp 0 lane 0 issues the TMA loads, warp 1 lane 0 the
 // MMAs; all four warps read the accumulator back.
 __global__ void __launch_bounds__(kHubThreads, 2)
-k_hub_gemm(const __grid_constant__ CUtensorMap amap, const uint8_t *__restrict__ A, int32_t H,
-           Ctrl *ctrl, uint32_t *__restrict__ r) {
+k_hub_gemm(const __grid_constant__ CUtensorMap amap, const uint8_t *__restrict__ A,
+           int32_t pitch, Ctrl *ctrl, uint32_t *__restrict__ r) {
   extern __shared__ uint8_t smem_raw[];
   if (!ctrl->hub_on || aborted(ctrl)) return;  // uniform for the block
+  const int32_t H = (int32_t)ctrl->hub_size;
+  {
+    const uint32_t T = (uint32_t)H / kHubTile;
+    if (blockIdx.x >= T * (T + 1) / 2) return;  // a tile of a larger hub set
+  }
   HubSmem &S = *reinterpret_cast<HubSmem *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -301,7 +381,7 @@ k_hub_gemm(const __grid_constant__ CUtensorMap amap, const uint8_t *__restrict__
   const bool ok = mbar_wait(&S.done, 0) && !S.abort;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int i = tid;
-  const uint8_t *arow = A + (size_t)(I * kHubTile + i) * H + (size_t)J * kHubTile;
+  const uint8_t *arow = A + (size_t)(I * kHubTile + i) * pitch + (size_t)J * kHubTile;
   int32_t rowsum = 0;
 #pragma unroll 1
   for (int c = 0; c < kHubTile / 32; ++c) {
@@ -350,11 +430,11 @@ k_hub_gemm(const __grid_constant__ CUtensorMap amap, const uint8_t *__restrict__
 // T += (sum of r) / 6; r must be even and its sum a multiple of 6.  One
 // block.
 __global__ void __launch_bounds__(1024)
-k_hub_finish(const uint32_t *__restrict__ r, int32_t H, Ctrl *ctrl, int64_t *t) {
+k_hub_finish(const uint32_t *__restrict__ r, Ctrl *ctrl, int64_t *t) {
   __shared__ unsigned long long s_sum[32];
   __shared__ uint32_t s_odd;
   if (aborted(ctrl) || !ctrl->hub_on) return;
-  const int32_t lo = (int32_t)ctrl->hub_lo;
+  const int32_t lo = (int32_t)ctrl->hub_lo, H = (int32_t)ctrl->hub_size;
   if (threadIdx.x == 0) s_odd = 0;
   __syncthreads();
   unsigned long long sum = 0;
@@ -400,17 +480,19 @@ EncodeTiled encode_fn() {
 
 size_t hub_bytes(int32_t H) { return (size_t)H * (size_t)H + 4 * (size_t)H; }
 
-void launch_hub_decide(const int32_t *off, int32_t n, int32_t H, int64_t min_edges, Ctrl *ctrl,
-                       cudaStream_t st) {
-  k_hub_decide<<<1, 1, 0, st>>>(off, n - H, min_edges, ctrl);
+void launch_hub_decide(const int32_t *off, const int32_t *col, int32_t n, int32_t Hmax,
+                       int64_t min_edges, bool per_vertex, Ctrl *ctrl, cudaStream_t st) {
+  k_hub_estimate<<<(Hmax + 7) / 8, 256, 0, st>>>(off, col, n, Hmax, ctrl);
+  k_hub_decide<<<1, 1, 0, st>>>(off, n, Hmax, min_edges, per_vertex ? 1 : 0, ctrl);
+  note_launch();
   note_launch();
 }
 
 cudaError_t launch_hub_count(const int32_t *off, const int32_t *voff, const int32_t *col4,
-                             int32_t n, int32_t H, uint8_t *region, Ctrl *ctrl, int64_t *t,
+                             int32_t n, int32_t Hmax, uint8_t *region, Ctrl *ctrl, int64_t *t,
                              cudaStream_t st) {
   uint8_t *A = region;
-  uint32_t *r = reinterpret_cast<uint32_t *>(region + (size_t)H * H);
+  uint32_t *r = reinterpret_cast<uint32_t *>(region + (size_t)Hmax * Hmax);
   EncodeTiled enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   static bool attr_set[64] = {};
@@ -422,22 +504,26 @@ cudaError_t launch_hub_count(const int32_t *off, const int32_t *voff, const int3
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
+  // the matrix has row pitch Hmax; the chosen set uses its top-left corner
   CUtensorMap map;
-  const cuuint64_t dims[2] = {(cuuint64_t)H, (cuuint64_t)H};
-  const cuuint64_t strides[1] = {(cuuint64_t)H};
+  const cuuint64_t dims[2] = {(cuuint64_t)Hmax, (cuuint64_t)Hmax};
+  const cuuint64_t strides[1] = {(cuuint64_t)Hmax};
   const cuuint32_t box[2] = {kHubKStep, kHubTile};
   const cuuint32_t estr[2] = {1, 1};
   if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, A, dims, strides, box, estr,
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(region, 0, hub_bytes(H), st);
+  cudaError_t e = cudaMemsetAsync(r, 0, 4 * (size_t)Hmax, st);
   if (e != cudaSuccess) return e;
-  k_hub_scatter<<<(H + 7) / 8, 256, 0, st>>>(off, voff, col4, n, H, ctrl, A);
-  const int T = H / kHubTile;
-  k_hub_gemm<<<T * (T + 1) / 2, kHubThreads, kHubSmemBytes, st>>>(map, A, H, ctrl, r);
-  k_hub_finish<<<1, 1024, 0, st>>>(r, H, ctrl, t);
-  for (int i = 0; i < 3; ++i) note_launch();
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  k_hub_zero<<<(sms > 0 ? sms : 1) * 8, 256, 0, st>>>(A, Hmax, ctrl);
+  k_hub_scatter<<<(Hmax + 7) / 8, 256, 0, st>>>(off, voff, col4, n, Hmax, ctrl, A);
+  const int T = Hmax / kHubTile;
+  k_hub_gemm<<<T * (T + 1) / 2, kHubThreads, kHubSmemBytes, st>>>(map, A, Hmax, ctrl, r);
+  k_hub_finish<<<1, 1024, 0, st>>>(r, ctrl, t);
+  for (int i = 0; i < 4; ++i) note_launch();
   return cudaGetLastError();
 }
 

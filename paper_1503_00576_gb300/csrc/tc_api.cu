@@ -334,7 +334,8 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   // whether the top ranks are counted densely (their edges are then left
   // out of the partner groups)
   const bool hub = L.has_hub && tune.hub_min_edges >= 0;
-  if (hub) launch_hub_decide(off, n, kHubSize, tune.hub_min_edges, ctrl, st);
+  const int32_t H = L.hub_vertices;  // the size the workspace was laid out for
+  if (hub) launch_hub_decide(off, col, n, H, tune.hub_min_edges, t_out != nullptr, ctrl, st);
   pt.stop(TC_PHASE_OFFSETS);
 
   // partner groups: each forward edge goes to the endpoint with the longer
@@ -385,7 +386,7 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
 
   pt.start(TC_PHASE_COUNT);
   if (hub) {
-    TC_CUDA(launch_hub_count(off, voff, col4, n, kHubSize, ws + L.hub, ctrl,
+    TC_CUDA(launch_hub_count(off, voff, col4, n, H, ws + L.hub, ctrl,
                              t_out ? t_rank : nullptr, st),
             "dense hub block");
   }
@@ -462,7 +463,7 @@ tc_status count_impl(const int32_t *src, const int32_t *dst, int64_t m, int32_t 
     *total = 0;
     return set_status(TC_OK);
   }
-  const Layout L = make_layout(m, n, true);
+  const Layout L = make_layout(m, n, true, current_tuning().hub_vertices);
   if (ws_user) {
     if (ws_bytes < L.total)
       return set_status(TC_ERR_INVALID_ARG, "workspace has %zu bytes, needs %zu", ws_bytes,
@@ -899,7 +900,7 @@ tc_status tc_count_per_vertex_host(const int32_t *src_host, const int32_t *dst_h
 
 size_t tc_workspace_bytes(int64_t m, int32_t n) {
   if (m < 0 || n < 0 || m > (int64_t)INT32_MAX) return 0;
-  return make_layout(m, n, true).total;
+  return make_layout(m, n, true, current_tuning().hub_vertices).total;
 }
 
 tc_status tc_count_ws(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
@@ -919,7 +920,7 @@ tc_status tc_count_noalloc(const int32_t *src, const int32_t *dst, int64_t m, in
     *total_out = 0;
     return set_status(TC_OK);
   }
-  const Layout L = make_layout(m, n, true);
+  const Layout L = make_layout(m, n, true, current_tuning().hub_vertices);
   if (L.total > (size_t)TC_NOALLOC_SCRATCH_BYTES)
     return set_status(TC_ERR_OVERFLOW,
                       "m=%lld, n=%d needs %zu bytes of scratch; the static scratch holds %zu",
@@ -953,7 +954,8 @@ tc_status tc_engine_create(int64_t max_pairs, int32_t max_vertices, int32_t max_
   e->max_vertices = max_vertices;
   e->max_graphs = max_graphs;
   e->tune = tuning ? Tuning{tuning->warp_max_list, tuning->warp_max_partners,
-                            max(tuning->heavy_ratio_pct, 100), tuning->hub_min_edges}
+                            max(tuning->heavy_ratio_pct, 100), tuning->hub_min_edges,
+                            tuning->hub_vertices}
                    : current_tuning();
   tc_status s = engine_build(e);
   if (s != TC_OK) {
@@ -1088,7 +1090,7 @@ tc_status tc_count_work_part(const int32_t *src, const int32_t *dst, int64_t m, 
   out->vertices = n;
   if (m == 0) return set_status(TC_OK);
   cudaStream_t st = (cudaStream_t)stream;
-  const Layout L = make_layout(m, n, true);
+  const Layout L = make_layout(m, n, true, current_tuning().hub_vertices);
   keep_pool_memory();
   unsigned char *ws = nullptr;
   TC_CUDA(dev_alloc_async((void **)&ws, L.total, st), "workspace allocation");
@@ -1125,11 +1127,12 @@ tc_status tc_engine_destroy(tc_engine *e) {
 }
 
 tc_status tc_set_tuning(const tc_tuning *t) {
-  if (t && (t->warp_max_list < 0 || t->warp_max_partners < 0 || t->heavy_ratio_pct < 100))
+  if (t && (t->warp_max_list < 0 || t->warp_max_partners < 0 || t->heavy_ratio_pct < 100 ||
+            t->hub_vertices < 128 || t->hub_vertices > kHubMaxSize || t->hub_vertices % 128))
     return set_status(TC_ERR_INVALID_ARG, "tuning values out of range");
   std::lock_guard<std::mutex> lk(g_tuning_mu);
   g_tuning = t ? Tuning{t->warp_max_list, t->warp_max_partners, t->heavy_ratio_pct,
-                        t->hub_min_edges}
+                        t->hub_min_edges, t->hub_vertices}
                : kDefaultTuning;
   return set_status(TC_OK);
 }
@@ -1141,6 +1144,7 @@ tc_status tc_get_tuning(tc_tuning *out) {
   out->warp_max_partners = t.warp_max_partners;
   out->heavy_ratio_pct = t.heavy_ratio_pct;
   out->hub_min_edges = t.hub_min_edges;
+  out->hub_vertices = t.hub_vertices;
   return set_status(TC_OK);
 }
 

@@ -39,7 +39,8 @@ constexpr uint32_t kSkipAll = 0xFFFFu;
 // on the tensor cores when they hold at least kHubMinEdges edges.  Only for
 // single graphs with n >= kHubMinVertices and ids of at most 24 bits (the
 // group keys must carry the skips).
-constexpr int32_t kHubSize = 1 << 14;
+constexpr int32_t kHubSize = 1 << 14;     // default size of the hub set
+constexpr int32_t kHubMaxSize = 1 << 15;  // largest allowed (a multiple of 128)
 constexpr int32_t kHubMinVertices = 1 << 17;
 constexpr int64_t kHubMinEdges = 1 << 21;
 
@@ -75,7 +76,8 @@ struct Ctrl {
   uint32_t next_long_list;         // its work cursor
   uint32_t hub_on;                 // the hub block is counted densely (hub.cu)
   uint32_t hub_lo;                 // its first rank
-  uint32_t pad[1];
+  uint32_t hub_size;               // its number of vertices (hub_lo + hub_size = n)
+  unsigned long long hub_est[4];   // hash lookups inside each candidate hub set (hub.cu)
   // work of the counting phase (filled only when asked for; see launch_work):
   // hash lookups, hash inserts, merge work W, max out-degree, then the
   // lookups of edges with both endpoints among the 2^12 .. 2^15 top ranks
@@ -127,8 +129,9 @@ struct Tuning {
                               //   |N+(u)| * heavy_ratio_pct, else at its owner u
   int64_t hub_min_edges;      // the dense hub block runs when it holds at least
                               //   this many edges (< 0: never)
+  int32_t hub_vertices;       // size of the hub set: a multiple of 128, <= kHubMaxSize
 };
-constexpr Tuning kDefaultTuning = {128, 64, 100, kHubMinEdges};
+constexpr Tuning kDefaultTuning = {128, 64, 100, kHubMinEdges, kHubSize};
 
 // A batch of graphs counted as one disjoint union (device-side descriptor).
 // Graph g owns input pairs [edge_off[g], edge_off[g+1]) and union vertex ids
@@ -151,6 +154,7 @@ struct Layout {
   size_t rank, vkeys_a, vkeys_b, t_rank;
   size_t hub;  // dense hub block (0 bytes unless the layout asked for it)
   bool has_hub;
+  int32_t hub_vertices;  // size of the hub set the hub region was laid out for
   size_t total;
   uint32_t sort_tiles, orient_tiles, scan_tiles;
   size_t st_sort_words_per_pass;
@@ -186,7 +190,8 @@ inline int radix_passes(int b) { return (2 * b + 7) / 8 + 3 * ((b + 7) / 8); }
 // Whether a single-graph run of n vertices has the dense hub block.
 inline bool hub_enabled(int32_t n, int b) { return n >= kHubMinVertices && 2 * b <= kSkipShift; }
 
-inline Layout make_layout(int64_t m_in, int32_t n, bool with_hub = false) {
+inline Layout make_layout(int64_t m_in, int32_t n, bool with_hub = false,
+                          int32_t hub_vertices = kHubSize) {
   Layout L{};
   size_t p = 0;
   auto take = [&](size_t bytes) {
@@ -229,8 +234,10 @@ inline Layout make_layout(int64_t m_in, int32_t n, bool with_hub = false) {
   // elements, since each non-empty list adds at most 7
   L.col4 = take(sizeof(int32_t) * (m + 7 * (nv < m ? nv : m)));
   const bool hub = with_hub && hub_enabled(n, id_bits(n > 0 ? n : 1));
-  L.hub = take(hub ? (size_t)kHubSize * kHubSize + 4 * (size_t)kHubSize : 0);
+  const size_t H = (size_t)hub_vertices;
+  L.hub = take(hub ? H * H + 4 * H : 0);
   L.has_hub = hub;
+  L.hub_vertices = hub_vertices;
   L.total = p;
   return L;
 }
@@ -297,15 +304,17 @@ void launch_word_offsets(const int32_t *counts, int32_t n, int32_t *voff,
 // Workspace of the dense hub block of H vertices: the H x H fp8 matrix and
 // the per-vertex sums.
 size_t hub_bytes(int32_t H);
-// Decides (on the device, into ctrl->hub_on) whether the top H ranks are
-// counted densely: needs the node array.
-void launch_hub_decide(const int32_t *off, int32_t n, int32_t H, int64_t min_edges, Ctrl *ctrl,
-                       cudaStream_t st);
+// Decides on the device (into ctrl->hub_on, hub_size, hub_lo) whether, and
+// with how many of the top ranks (a candidate up to Hmax), the hub block is
+// counted densely; needs the node array and the column array (any order
+// within a list).
+void launch_hub_decide(const int32_t *off, const int32_t *col, int32_t n, int32_t Hmax,
+                       int64_t min_edges, bool per_vertex, Ctrl *ctrl, cudaStream_t st);
 // Counts the triangles inside the hub block (if ctrl->hub_on): adds them to
 // ctrl->total and, if t != nullptr, to the per-vertex counts t (rank space).
-// Needs the sorted lists; region: hub_bytes(H) bytes, 256-byte aligned.
+// Needs the forward lists; region: hub_bytes(Hmax) bytes, 256-byte aligned.
 cudaError_t launch_hub_count(const int32_t *off, const int32_t *voff, const int32_t *col4,
-                             int32_t n, int32_t H, uint8_t *region, Ctrl *ctrl, int64_t *t,
+                             int32_t n, int32_t Hmax, uint8_t *region, Ctrl *ctrl, int64_t *t,
                              cudaStream_t st);
 // ---- launchers (group.cu) ----
 // Sorts every forward list (the column array col, grouped by owner, node
