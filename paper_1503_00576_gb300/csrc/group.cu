@@ -212,7 +212,30 @@ k_sort_lists(const int32_t *__restrict__ col, const int32_t *__restrict__ off,
   }
 }
 
-// Lists longer than kWarpSortMax: one CTA each, sorted in shared memory up
+// Lists of kWarpSortMax + 1 to 2 kWarpSortMax entries: one warp each, 32
+// keys per lane in registers.
+constexpr int kWarpLongMax = 2 * kWarpSortMax;
+
+__global__ void __launch_bounds__(kListThreads)
+k_sort_long_lists_warp(const int32_t *__restrict__ col, const int32_t *__restrict__ off,
+                       const int32_t *__restrict__ voff, Ctrl *ctrl, int32_t *__restrict__ col4,
+                       int32_t *__restrict__ lmin, const int32_t *__restrict__ long_lists) {
+  if (aborted(ctrl)) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t count = ctrl->n_long_lists;
+  for (;;) {
+    uint32_t i = 0;
+    if (lane == 0) i = atomicAdd(&ctrl->next_long_list_warp, 1u);
+    i = __shfl_sync(kFull, i, 0);
+    if (i >= count) break;
+    const int32_t v = __ldg(long_lists + i);
+    const int32_t b = __ldg(off + v), d = __ldg(off + v + 1) - b;
+    if (d > kWarpLongMax) continue;  // the CTA kernel's
+    warp_sort_list<kWarpLongMax / 32>(col, b, d, 4ll * __ldg(voff + v), col4, lmin + v);
+  }
+}
+
+// Lists longer than kWarpLongMax: one CTA each, sorted in shared memory up
 // to kCtaSortMax entries; longer lists are copied unsorted and flagged in
 // lmin (their streams then skip nothing).
 __global__ void __launch_bounds__(kLongListThreads, kLongListBlocks)
@@ -232,29 +255,31 @@ k_sort_long_lists(const int32_t *__restrict__ col, const int32_t *__restrict__ o
     if (i >= count) break;
     const int32_t v = __ldg(long_lists + i);
     const int32_t b = __ldg(off + v), d = __ldg(off + v + 1) - b;
-    int32_t *dst = col4 + 4ll * __ldg(voff + v);
-    const int r8 = (d + 7) & ~7;
-    if (d <= kCtaSortMax) {
-      const int P = pow2_at_least(d);
-      for (int j = tid; j < P; j += kLongListThreads) s_buf[j] = j < d ? __ldg(col + b + j) : INT32_MAX;
-      __syncthreads();
-      bitonic_smem<kLongListThreads>(s_buf, P, tid);
-      for (int j = tid; j < r8; j += kLongListThreads) dst[j] = j < d ? s_buf[j] : -1;
-      if (tid == 0) lmin[v] = s_buf[0];
-    } else {
-      int32_t mn = INT32_MAX;
-      for (int j = tid; j < r8; j += kLongListThreads) {
-        const int32_t x = j < d ? __ldg(col + b + j) : -1;
-        dst[j] = x;
-        if (j < d) mn = min(mn, x);
-      }
+    if (d > kWarpLongMax) {  // shorter lists are the warp kernel's (uniform for the block)
+      int32_t *dst = col4 + 4ll * __ldg(voff + v);
+      const int r8 = (d + 7) & ~7;
+      if (d <= kCtaSortMax) {
+        const int P = pow2_at_least(d);
+        for (int j = tid; j < P; j += kLongListThreads) s_buf[j] = j < d ? __ldg(col + b + j) : INT32_MAX;
+        __syncthreads();
+        bitonic_smem<kLongListThreads>(s_buf, P, tid);
+        for (int j = tid; j < r8; j += kLongListThreads) dst[j] = j < d ? s_buf[j] : -1;
+        if (tid == 0) lmin[v] = s_buf[0];
+      } else {
+        int32_t mn = INT32_MAX;
+        for (int j = tid; j < r8; j += kLongListThreads) {
+          const int32_t x = j < d ? __ldg(col + b + j) : -1;
+          dst[j] = x;
+          if (j < d) mn = min(mn, x);
+        }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(kFull, mn, o));
-      if (lane == 0) s_min[warp] = mn;
-      __syncthreads();
-      if (tid == 0) {
-        for (int w = 1; w < kLongListThreads / 32; ++w) mn = min(mn, s_min[w]);
-        lmin[v] = -1 - mn;  // unsorted
+        for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(kFull, mn, o));
+        if (lane == 0) s_min[warp] = mn;
+        __syncthreads();
+        if (tid == 0) {
+          for (int w = 1; w < kLongListThreads / 32; ++w) mn = min(mn, s_min[w]);
+          lmin[v] = -1 - mn;  // unsorted
+        }
       }
     }
     __syncthreads();  // s_buf and s_i are reused
@@ -426,8 +451,11 @@ void launch_sort_lists(const int32_t *col, const int32_t *off, const int32_t *vo
   const uint32_t chunks = ((uint32_t)n + 31u) / 32u;
   const uint32_t grid = max(1u, min((chunks + kListWarps - 1) / kListWarps, (uint32_t)sms * 8u));
   k_sort_lists<<<grid, kListThreads, 0, st>>>(col, off, voff, n, ctrl, col4, lmin, long_lists);
+  k_sort_long_lists_warp<<<sms * 4, kListThreads, 0, st>>>(col, off, voff, ctrl, col4, lmin,
+                                                            long_lists);
   k_sort_long_lists<<<sms * kLongListBlocks, kLongListThreads, 0, st>>>(col, off, voff, ctrl,
                                                                         col4, lmin, long_lists);
+  note_launch();
   note_launch();
   note_launch();
 }

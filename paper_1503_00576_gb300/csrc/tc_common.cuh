@@ -72,11 +72,13 @@ struct Ctrl {
   uint32_t next_big_group;
   unsigned long long total;        // triangle count T
   uint32_t m_in;                   // input pairs that are real (not batch padding)
-  uint32_t n_long_lists;           // forward lists sorted by the long-list kernel
-  uint32_t next_long_list;         // its work cursor
+  uint32_t n_long_lists;           // forward lists sorted by the long-list kernels
+  uint32_t next_long_list;         // work cursor of the CTA-per-list kernel
+  uint32_t next_long_list_warp;    // work cursor of the warp-per-list kernel
   uint32_t hub_on;                 // the hub block is counted densely (hub.cu)
   uint32_t hub_lo;                 // its first rank
   uint32_t hub_size;               // its number of vertices (hub_lo + hub_size = n)
+  uint32_t pad_[3];
   unsigned long long hub_est[4];   // hash lookups inside each candidate hub set (hub.cu)
   // work of the counting phase (filled only when asked for; see launch_work):
   // hash lookups, hash inserts, merge work W, max out-degree, then the
