@@ -238,15 +238,18 @@ k_hub_estimate(const int32_t *__restrict__ off, const int32_t *__restrict__ col,
 
 // Cost model (GB300, measured on R-MAT scale 20 and 24 over hub sizes of
 // 8192 to 24576): a lookup taken off the hash path saves about 0.63 ps of
-// the whole GPU's time (total only) or 1.03 ps (per-vertex counts, whose
-// match counters go too); the dense block costs about 0.15 ms plus
-// 1.55 ms (H / 16384)^3.
+// the whole GPU's time when only T is counted and 1.03 ps with per-vertex
+// counts (whose match counters go too); one figure between the two, 0.85
+// ps, serves both, so that a graph gets the same hub set in either mode
+// (and tc_count_work reports the work of the run it describes).  The dense
+// block costs about 0.15 ms plus 1.55 ms (H / 16384)^3.
 // The candidate with the largest saving is used if it saves anything.
 // force (hub_min_edges == 0): the largest candidate, whatever the model.
 __global__ void k_hub_decide(const int32_t *__restrict__ off, int32_t n, int32_t Hmax,
                              int64_t min_edges, int per_vertex, Ctrl *ctrl) {
   if (aborted(ctrl)) return;
-  const double ms_per_lookup = per_vertex ? 1.03e-9 : 0.63e-9;
+  (void)per_vertex;
+  const double ms_per_lookup = 0.85e-9;
   double best = 0.0;
   int32_t H = 0;
   unsigned long long inside = 0;

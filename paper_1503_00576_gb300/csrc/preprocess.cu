@@ -264,52 +264,13 @@ k_canon(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, uint32
 // one LSD radix pass (8-bit digit at `shift`), onesweep style
 // ---------------------------------------------------------------------------
 struct RadixShared {
-  uint64_t in[kSortTile];                   // the next whole tile, copied in by the bulk engine
   uint64_t keys[kSortTile];                 // the tile, staged in digit order
   uint32_t whist[kSortThreads / 32][256];   // per warp and digit: count, then first position
   uint32_t gbase[256];                      // per digit: output position of staged index 0
   uint32_t scratch[32];
-  uint32_t next;                            // the tile this CTA counts next
+  uint32_t tile;
   uint32_t abort;  // some digit's look-back gave up: the tile writes nothing
-  unsigned long long bar;                   // completion of the bulk copy into `in`
 };
-constexpr int kSortBlocks = 3;  // persistent CTAs per SM (shared memory allows three)
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// Whole tile `tile` of `in` into S.in by the bulk-copy engine, completing
-// on S.bar.  Issued by one thread.
-__device__ __forceinline__ void bulk_load_tile(RadixShared &S, const uint64_t *in, uint32_t tile) {
-  constexpr uint32_t bytes = kSortTile * sizeof(uint64_t);
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&S.bar)),
-               "r"(bytes)
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(S.in)),
-      "l"(in + (size_t)tile * kSortTile), "r"(bytes), "r"(smem_addr(&S.bar))
-      : "memory");
-}
-
-// Waits (bounded) for the phase of S.bar of parity `parity`.
-__device__ __forceinline__ bool bulk_wait(RadixShared &S, uint32_t parity) {
-  const uint32_t addr = smem_addr(&S.bar);
-  const uint32_t limit = g_spin_limit;
-  for (uint32_t i = 0; i <= limit; ++i) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
 
 // Writes one staged key to its output position (and, for the column pass,
 // its row and the out-degree of its owner).
@@ -351,8 +312,7 @@ __device__ __forceinline__ void radix_tile(RadixShared &S, const uint64_t *__res
                                            uint32_t tile, uint32_t gofs, int shift,
                                            uint32_t col_mask, uint32_t *__restrict__ row_out,
                                            int owner_shift, int32_t *outdeg,
-                                           unsigned long long *__restrict__ status, Ctrl *ctrl,
-                                           uint32_t next, bool next_bulk) {
+                                           unsigned long long *__restrict__ status, Ctrl *ctrl) {
   constexpr int WARPS = kSortThreads / 32, KPT = kSortKeysPerThread, TILE = kSortTile;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t tile_base = tile * (uint32_t)TILE;
@@ -366,13 +326,9 @@ __device__ __forceinline__ void radix_tile(RadixShared &S, const uint64_t *__res
   const uint32_t lt_mask = (1u << lane) - 1u;
   uint64_t k[KPT];
   uint32_t pk[KPT];  // digit << 16 | rank among the warp's keys of that digit
-  // a whole tile was copied into S.in ahead of time; the last, partial one
-  // is read from global memory
-  const uint32_t rel = first - tile_base;
 #pragma unroll
   for (int i = 0; i < KPT; ++i)
-    k[i] = FULL ? S.in[rel + 32u * i]
-                : (first + 32u * i < n_keys ? __ldg(in + first + 32u * i) : 0ull);
+    k[i] = (FULL || first + 32u * i < n_keys) ? __ldg(in + first + 32u * i) : 0ull;
 #pragma unroll
   for (int i = 0; i < KPT; ++i) {
     const bool valid = FULL || first + 32u * i < n_keys;
@@ -391,9 +347,6 @@ __device__ __forceinline__ void radix_tile(RadixShared &S, const uint64_t *__res
     pk[i] = (d << 16) | (before + below);
   }
   __syncthreads();
-  // every key of S.in is in registers now: copy the next tile in while this
-  // one is ranked, staged and scattered
-  if (threadIdx.x == 0 && next_bulk) bulk_load_tile(S, in, next);
 
   // ---- per digit (thread tid): tile count, published at once; tile offset
   // and warp offsets; then the keys are staged, sorted by digit, before the
@@ -493,81 +446,40 @@ __device__ __forceinline__ void radix_tile(RadixShared &S, const uint64_t *__res
   }
 }
 
-// Persistent CTAs (kSortBlocks per SM) take tiles in ticket order.  A CTA
-// takes its next ticket while it counts the current tile and, once the
-// current keys are in registers, has the bulk-copy engine bring the next
-// whole tile into shared memory, so the loads of one tile overlap the
-// ranking and scatter of the previous one.  Holding the next ticket early
-// cannot stall anyone: a tile waits only on tiles of lower tickets, which
-// are all held by running CTAs that finish them without waiting on it.
 template <int MODE>
-__global__ void __launch_bounds__(kSortThreads, kSortBlocks)
+__global__ void __launch_bounds__(kSortThreads, 4)
 k_radix_pass(const uint64_t *__restrict__ in, void *__restrict__ out, uint32_t n_keys_bound,
              const uint32_t *__restrict__ n_keys_dev, int shift, uint32_t col_mask,
              uint32_t *__restrict__ row_out, int owner_shift, int32_t *outdeg,
              const uint32_t *__restrict__ hist, unsigned long long *__restrict__ status,
              uint32_t *ticket, Ctrl *ctrl) {
   constexpr int WARPS = kSortThreads / 32, TILE = kSortTile;
-  extern __shared__ __align__(128) unsigned char radix_smem[];
-  RadixShared &S = *reinterpret_cast<RadixShared *>(radix_smem);
+  __shared__ RadixShared S;
   const int tid = threadIdx.x;
-  const uint32_t n_keys = n_keys_dev ? *n_keys_dev : n_keys_bound;
-  const uint32_t tiles = (n_keys + TILE - 1) / TILE;
-  const uint32_t full_tiles = n_keys / TILE;
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&S.bar)));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    S.tile = atomicAdd(ticket, 1u);
     S.abort = aborted(ctrl) ? 1u : 0u;
-    S.next = atomicAdd(ticket, 1u);
   }
+  for (int i = tid; i < WARPS * 256; i += kSortThreads) (&S.whist[0][0])[i] = 0;
   __syncthreads();
-  uint32_t t = S.next;
-  if (S.abort) {  // an earlier wait of this call ran out: poison every tile taken
-    while (t < tiles) {
-      st_volatile_u64(status + (size_t)t * 256 + tid, kFlagPoison);
-      __syncthreads();
-      if (tid == 0) S.next = atomicAdd(ticket, 1u);
-      __syncthreads();
-      t = S.next;
-    }
+  const uint32_t tile = S.tile;
+  if (S.abort) {  // an earlier wait of this call ran out: the input is not complete
+    st_volatile_u64(status + (size_t)tile * 256 + tid, kFlagPoison);
     return;
   }
+  const uint32_t n_keys = n_keys_dev ? *n_keys_dev : n_keys_bound;
+  const uint32_t tile_base = tile * (uint32_t)TILE;
+  if (tile_base >= n_keys) return;  // uniform for the block
+
   // global start of every digit: exclusive scan of the pass histogram
   uint32_t dummy;
   const uint32_t gofs = scan256_exclusive(hist[tid], S.scratch, &dummy);
-  bool bulk = t < full_tiles;
-  if (tid == 0 && bulk) bulk_load_tile(S, in, t);
-  uint32_t parity = 0;
-  while (t < tiles) {
-    for (int i = tid; i < WARPS * 256; i += kSortThreads) (&S.whist[0][0])[i] = 0;
-    if (tid == 0) {
-      S.abort = 0u;
-      S.next = atomicAdd(ticket, 1u);
-    }
-    bool landed = true;
-    if (bulk) {
-      landed = bulk_wait(S, parity);
-      parity ^= 1u;
-    }
-    __syncthreads();
-    const uint32_t next = S.next;
-    const bool next_bulk = next < full_tiles;
-    if (__syncthreads_or(!landed)) {  // the copy did not arrive: give up the pass
-      if (tid == 0) atomicOr(&ctrl->err, kErrTimeout);
-      st_volatile_u64(status + (size_t)t * 256 + tid, kFlagPoison);
-      if (next < tiles) st_volatile_u64(status + (size_t)next * 256 + tid, kFlagPoison);
-      break;
-    }
-    if (bulk)
-      radix_tile<MODE, true>(S, in, out, n_keys, t, gofs, shift, col_mask, row_out, owner_shift,
-                             outdeg, status, ctrl, next, next_bulk);
-    else
-      radix_tile<MODE, false>(S, in, out, n_keys, t, gofs, shift, col_mask, row_out,
-                              owner_shift, outdeg, status, ctrl, next, next_bulk);
-    __syncthreads();  // the scatter has read S.keys and S.gbase
-    t = next;
-    bulk = next_bulk;
-  }
+  if (n_keys - tile_base >= (uint32_t)TILE)
+    radix_tile<MODE, true>(S, in, out, n_keys, tile, gofs, shift, col_mask, row_out, owner_shift,
+                           outdeg, status, ctrl);
+  else
+    radix_tile<MODE, false>(S, in, out, n_keys, tile, gofs, shift, col_mask, row_out,
+                            owner_shift, outdeg, status, ctrl);
 }
 
 // ---------------------------------------------------------------------------
@@ -874,56 +786,32 @@ void launch_canon(const int32_t *src, const int32_t *dst, uint32_t m_in, int32_t
   note_launch();
 }
 
-template <int MODE>
-cudaError_t radix_attr() {
-  static bool done[64] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64 || done[dev]) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(
-      k_radix_pass<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(RadixShared));
-  if (e == cudaSuccess) done[dev] = true;
-  return e;
-}
-
-cudaError_t prepare_radix_kernels() {
-  cudaError_t e = radix_attr<kOutKeys>();
-  if (e == cudaSuccess) e = radix_attr<kOutColRow>();
-  if (e == cudaSuccess) e = radix_attr<kOutRank>();
-  if (e == cudaSuccess) e = radix_attr<kOutKeysDeg>();
-  if (e == cudaSuccess) e = radix_attr<kOutPartSkip>();
-  return e;
-}
-
 void launch_radix_pass(const uint64_t *in, void *out, RadixOut mode, uint32_t *row_out,
                        int32_t *outdeg, uint32_t n_keys_bound, const uint32_t *n_keys_dev,
                        int shift, uint32_t col_mask, int owner_shift, const uint32_t *hist,
                        unsigned long long *status, uint32_t *ticket, Ctrl *ctrl,
                        cudaStream_t st) {
-  prepare_radix_kernels();
-  const uint32_t tiles = max(1u, (n_keys_bound + kSortTile - 1) / kSortTile);
-  const uint32_t grid = min(tiles, (uint32_t)num_sms() * kSortBlocks);
-  const size_t smem = sizeof(RadixShared);
+  const uint32_t grid = max(1u, (n_keys_bound + kSortTile - 1) / kSortTile);
   if (mode == kOutPartSkip)
-    k_radix_pass<kOutPartSkip><<<grid, kSortThreads, smem, st>>>(
+    k_radix_pass<kOutPartSkip><<<grid, kSortThreads, 0, st>>>(
         in, out, n_keys_bound, n_keys_dev, shift, col_mask, row_out, owner_shift, outdeg, hist,
         status, ticket, ctrl);
   else if (mode == kOutColRow)
-    k_radix_pass<kOutColRow><<<grid, kSortThreads, smem, st>>>(
+    k_radix_pass<kOutColRow><<<grid, kSortThreads, 0, st>>>(
         in, out, n_keys_bound, n_keys_dev, shift, col_mask, row_out, owner_shift, outdeg, hist,
         status, ticket, ctrl);
   else if (mode == kOutRank)
-    k_radix_pass<kOutRank><<<grid, kSortThreads, smem, st>>>(in, out, n_keys_bound, n_keys_dev,
-                                                             shift, col_mask, nullptr, 0, nullptr,
-                                                             hist, status, ticket, ctrl);
+    k_radix_pass<kOutRank><<<grid, kSortThreads, 0, st>>>(in, out, n_keys_bound, n_keys_dev,
+                                                          shift, col_mask, nullptr, 0, nullptr,
+                                                          hist, status, ticket, ctrl);
   else if (mode == kOutKeysDeg)
-    k_radix_pass<kOutKeysDeg><<<grid, kSortThreads, smem, st>>>(
+    k_radix_pass<kOutKeysDeg><<<grid, kSortThreads, 0, st>>>(
         in, out, n_keys_bound, n_keys_dev, shift, col_mask, nullptr, owner_shift, outdeg, hist,
         status, ticket, ctrl);
   else
-    k_radix_pass<kOutKeys><<<grid, kSortThreads, smem, st>>>(in, out, n_keys_bound, n_keys_dev,
-                                                             shift, col_mask, nullptr, 0, nullptr,
-                                                             hist, status, ticket, ctrl);
+    k_radix_pass<kOutKeys><<<grid, kSortThreads, 0, st>>>(in, out, n_keys_bound, n_keys_dev,
+                                                          shift, col_mask, nullptr, 0, nullptr,
+                                                          hist, status, ticket, ctrl);
   note_launch();
 }
 

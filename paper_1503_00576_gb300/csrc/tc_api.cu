@@ -772,7 +772,6 @@ void engine_release(tc_engine *e) {
 tc_status engine_build(tc_engine *e) {
   TC_CUDA(cudaGetDevice(&e->device), "current device");
   TC_CUDA(prepare_count_kernels(), "count kernel attributes");
-  TC_CUDA(prepare_radix_kernels(), "radix kernel attributes");
   TC_CUDA(cudaStreamCreateWithFlags(&e->st, cudaStreamNonBlocking), "stream");
   e->L = make_layout(e->max_pairs, e->max_vertices);
   e->R = batch_region(e->max_graphs);

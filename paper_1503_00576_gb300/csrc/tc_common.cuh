@@ -276,9 +276,6 @@ void launch_radix_pass(const uint64_t *in, void *out, RadixOut mode, uint32_t *r
                        int shift, uint32_t col_mask, int owner_shift, const uint32_t *hist,
                        unsigned long long *status, uint32_t *ticket, Ctrl *ctrl,
                        cudaStream_t st);
-// Sets the radix kernels' shared-memory attribute for the current device
-// (done lazily otherwise; needed before capturing a CUDA graph).
-cudaError_t prepare_radix_kernels();
 // Keys deg(v) << b | v for every vertex, with the digit histograms of the
 // degree field (the rank sort).
 void launch_rank_keys(const int32_t *deg, int32_t n, int b, int passes, uint64_t *vkeys,
