@@ -186,7 +186,7 @@ def measured_peaks() -> dict:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("preprocess.cu", "group.cu", "count.cu", "tc_common.cuh"):
+    for name in ("preprocess.cu", "group.cu", "count.cu", "hub.cu", "tc_common.cuh"):
         with open(os.path.join(ROOT, "paper_1503_00576_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
