@@ -94,7 +94,9 @@ tc_status tc_count_per_vertex(const int32_t *src, const int32_t *dst, int64_t m,
  * dealing depends on the graph alone, so separate calls agree on it).
  * Summing total_out over the parts gives T,
  * and summing t_out element-wise gives the per-vertex counts; deg_out is
- * complete in every part.  parts = 1 is tc_count / tc_count_per_vertex.
+ * complete in every part.  The dense hub block (tc_tuning), if a graph uses
+ * it, is counted by part 0 alone.  parts = 1 is tc_count /
+ * tc_count_per_vertex.
  *   part, parts  0 <= part < parts, else TC_ERR_INVALID_ARG
  *   t_out        device int64[n], this part's share of t (required when n > 0)
  *   deg_out      device int32[n], written if not NULL

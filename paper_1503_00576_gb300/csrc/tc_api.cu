@@ -385,7 +385,9 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   if (work_stats) launch_work(off, goff, part, pskip, n, ctrl, st, shard, shards);
 
   pt.start(TC_PHASE_COUNT);
-  if (hub) {
+  // the dense block's triangles belong to the first share alone (every share
+  // leaves the block's edges off its hash path)
+  if (hub && shard == 0) {
     TC_CUDA(launch_hub_count(off, voff, col4, n, H, ws + L.hub, ctrl,
                              t_out ? t_rank : nullptr, st),
             "dense hub block");

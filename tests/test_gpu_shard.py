@@ -79,6 +79,30 @@ def test_per_vertex_shares_add_up_to_the_oracle(tc):
     assert np.array_equal(acc, want["t"])
 
 
+@pytest.mark.parametrize("parts", [2, 3])
+def test_shares_add_up_with_the_dense_hub_block(tc, parts):
+    """A graph of 2^17 vertices with the dense hub block forced on: the
+    block is counted by part 0 alone and every part leaves its edges off
+    the hash path, so the shares of T and of every t(v) still add up to the
+    oracle's."""
+    src, dst = graphgen.rmat(17, 32 << 17, 24)
+    n = 1 << 17
+    want = oracle.forward(src, dst, n)
+    s, d = dev(src), dev(dst)
+    tc.tc_set_tuning({"hub_min_edges": 0})
+    try:
+        assert sum(tc.tc_count_part(s, d, n, p, parts) for p in range(parts)) == want["T"]
+        acc = np.zeros(n, np.int64)
+        total = 0
+        for p in range(parts):
+            T, t, deg = tc.tc_count_per_vertex_part(s, d, n, p, parts)
+            total += T
+            acc += t.cpu().numpy()
+        assert total == want["T"] and np.array_equal(acc, want["t"])
+    finally:
+        tc.tc_set_tuning(None)
+
+
 def test_shares_of_a_batchless_empty_graph(tc):
     import torch
 
