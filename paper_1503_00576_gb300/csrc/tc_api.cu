@@ -921,7 +921,8 @@ tc_status tc_count_noalloc(const int32_t *src, const int32_t *dst, int64_t m, in
     *total_out = 0;
     return set_status(TC_OK);
   }
-  const Layout L = make_layout(m, n, true, current_tuning().hub_vertices);
+  // no dense hub block here: its matrix alone would not fit the scratch
+  const Layout L = make_layout(m, n);
   if (L.total > (size_t)TC_NOALLOC_SCRATCH_BYTES)
     return set_status(TC_ERR_OVERFLOW,
                       "m=%lld, n=%d needs %zu bytes of scratch; the static scratch holds %zu",
