@@ -589,6 +589,8 @@ def run_ours(args, world, rank, local, pg):
         "counting_work": {"lookups": work["lookups"], "inserts": work["inserts"],
                           "merge_work_W": work["merge_work"],
                           "max_out_degree": work["max_out_degree"],
+                          "dense_hub_vertices": work["dense_vertices"],
+                          "dense_hub_triangles": work["dense_triangles"],
                           "hub_lookup_share": {str(k): round(v / max(work["lookups"], 1), 4)
                                                for k, v in work["hub_lookups"].items()}},
     }

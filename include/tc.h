@@ -272,6 +272,10 @@ tc_status tc_engine_destroy(tc_engine *engine);
  *                  edges, so these edges' triangles lie wholly in H_i and a
  *                  dense count of the block A_{H_i H_i} (the matrix methods
  *                  of Sec. VI) could replace exactly this share of lookups
+ *   dense_vertices the size of the hub set this run counted on the tensor
+ *                  cores (its highest-ranked vertices; 0: none, see tc_tuning)
+ *   dense_triangles the triangles counted there (all three vertices in it);
+ *                  the hash intersections counted triangles - dense_triangles
  * Same arguments and errors as tc_count; synchronises `stream`.
  */
 typedef struct tc_work {
@@ -283,6 +287,9 @@ typedef struct tc_work {
   int32_t max_out_degree;
   int32_t vertices;
   int64_t hub_lookups[4];
+  uint64_t dense_triangles;
+  int32_t dense_vertices;
+  int32_t pad_;
 } tc_work;
 tc_status tc_count_work(const int32_t *src, const int32_t *dst, int64_t m, int32_t n,
                         tc_stream_t stream, tc_work *out);

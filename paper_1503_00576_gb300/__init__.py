@@ -62,7 +62,9 @@ class Work(ctypes.Structure):
     _fields_ = [("edges", ctypes.c_int64), ("lookups", ctypes.c_int64),
                 ("inserts", ctypes.c_int64), ("merge_work", ctypes.c_int64),
                 ("triangles", ctypes.c_uint64), ("max_out_degree", ctypes.c_int32),
-                ("vertices", ctypes.c_int32), ("hub_lookups", ctypes.c_int64 * 4)]
+                ("vertices", ctypes.c_int32), ("hub_lookups", ctypes.c_int64 * 4),
+                ("dense_triangles", ctypes.c_uint64), ("dense_vertices", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
 
 
 class Tuning(ctypes.Structure):
@@ -530,7 +532,7 @@ def tc_count_work(src, dst, n: int, stream=None, part: int = 0, parts: int = 1) 
         rc = lib.tc_count_work_part(src.data_ptr(), dst.data_ptr(), src.numel(), n, part, parts,
                                     _stream_of(stream, dev), ctypes.byref(w))
     _check(rc)
-    out = {f: int(getattr(w, f)) for f, _ in w._fields_ if f != "hub_lookups"}
+    out = {f: int(getattr(w, f)) for f, _ in w._fields_ if f not in ("hub_lookups", "pad_")}
     out["hub_lookups"] = {1 << (12 + i): int(w.hub_lookups[i]) for i in range(4)}
     return out
 

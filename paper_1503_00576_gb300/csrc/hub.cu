@@ -458,6 +458,7 @@ k_hub_finish(const uint32_t *__restrict__ r, Ctrl *ctrl, int64_t *t) {
     for (int w = 0; w < (int)(blockDim.x / 32); ++w) all += s_sum[w];
     if (s_odd || all % 6ull) atomicOr(&ctrl->err, kErrInternal);
     ctrl->total += all / 6ull;
+    ctrl->hub_triangles = all / 6ull;
   }
 }
 

@@ -1115,6 +1115,8 @@ tc_status tc_count_work_part(const int32_t *src, const int32_t *dst, int64_t m, 
   out->merge_work = (int64_t)h->work[2];
   out->max_out_degree = (int32_t)h->work[3];
   for (int k = 0; k < kHubSizes; ++k) out->hub_lookups[k] = (int64_t)h->work[4 + k];
+  out->dense_vertices = h->hub_on ? (int32_t)h->hub_size : 0;
+  out->dense_triangles = h->hub_triangles;
   return set_status(TC_OK);
 }
 

@@ -78,7 +78,8 @@ struct Ctrl {
   uint32_t hub_on;                 // the hub block is counted densely (hub.cu)
   uint32_t hub_lo;                 // its first rank
   uint32_t hub_size;               // its number of vertices (hub_lo + hub_size = n)
-  uint32_t pad_[3];
+  uint32_t pad_[1];
+  unsigned long long hub_triangles;  // triangles the dense block counted
   unsigned long long hub_est[4];   // hash lookups inside each candidate hub set (hub.cu)
   // work of the counting phase (filled only when asked for; see launch_work):
   // hash lookups, hash inserts, merge work W, max out-degree, then the

@@ -92,6 +92,53 @@ def test_dense_block_takes_the_hub_edges_off_the_hash_path(tc, graph):
     assert on["triangles"] == off["triangles"] == want["T"]
 
 
+def triangles_among_top_ranks(src, dst, n, H):
+    """Triangles with all three vertices among the H vertices highest in the
+    (degree, id) order of the cleaned graph: scipy on the induced subgraph."""
+    import scipy.sparse as sp
+
+    s = np.asarray(src, np.int64)
+    d = np.asarray(dst, np.int64)
+    keep = s != d
+    a, b = np.minimum(s, d)[keep], np.maximum(s, d)[keep]
+    key = np.unique(a * n + b)
+    a, b = key // n, key % n
+    deg = np.bincount(a, minlength=n) + np.bincount(b, minlength=n)
+    top = np.zeros(n, bool)
+    top[np.lexsort((np.arange(n), deg))[n - H:]] = True
+    idx = np.full(n, -1, np.int64)
+    idx[top] = np.arange(H)
+    inside = top[a] & top[b]
+    x, y = idx[a[inside]], idx[b[inside]]
+    A = sp.coo_matrix((np.ones(len(x)), (x, y)), shape=(H, H)).tocsr()
+    A = A + A.T
+    return int(round((A @ A).multiply(A).sum())) // 6
+
+
+def test_dense_triangles_match_the_top_ranks(tc, graph):
+    """Forced on, the block covers the 2^14 highest-ranked vertices and
+    counts exactly the triangles lying wholly among them."""
+    src, dst, n, want = graph
+    try:
+        tc.tc_set_tuning({"hub_min_edges": 0})
+        w = tc.tc_count_work(dev(src), dev(dst), n)
+    finally:
+        tc.tc_set_tuning(None)
+    assert w["dense_vertices"] == 1 << 14
+    assert w["dense_triangles"] == triangles_among_top_ranks(src, dst, n, 1 << 14)
+    assert w["triangles"] == want["T"]
+
+
+def test_cost_model_keeps_it_off_without_hubs(tc):
+    """A random geometric graph of 2^17 vertices has no hubs: the estimated
+    saving never pays for the product, so the block stays off."""
+    n = 1 << 17
+    src, dst = graphgen.rgg(n, graphgen.rgg_radius(n, 32.0), 54)
+    w = tc.tc_count_work(dev(src), dev(dst), n)
+    assert w["dense_vertices"] == 0 and w["dense_triangles"] == 0
+    assert w["triangles"] == oracle.forward(src, dst, n, per_vertex=False)["T"]
+
+
 def test_small_graphs_never_use_it(tc):
     """Below 2^17 vertices the layout has no hub block: forcing the knob
     changes nothing."""

@@ -75,7 +75,7 @@ def expected_work(src, dst, n):
         hub[size] = int(streamed[inside].sum())
     return {"edges": len(key), "lookups": int(lookups), "inserts": int(inserts),
             "merge_work": int(W), "max_out_degree": int(dp.max()) if n else 0,
-            "hub_lookups": hub}
+            "hub_lookups": hub, "dense_vertices": 0, "dense_triangles": 0}
 
 
 @pytest.mark.parametrize("case", ["rmat12", "er", "k9", "rgg", "rmat16"])
