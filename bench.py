@@ -5,7 +5,8 @@
                     [--workload rmat24|rmat20|rgg4m|er16k]
 
 One step = the whole path (validation, cleaning, degree-ordered orientation,
-two LSD radix sorts, node array, counting with per-vertex counts) over one
+an LSD radix sort by owner, node array, per-list sorts that drop repeated
+edges, partner groups, counting with per-vertex counts) over one
 graph whose edge array is already resident in HBM.  The default workload is
 the R-MAT graph of scale 24 with 180,000,000 distinct undirected edges
 (a=.57, b=.19, c=.19, d=.05, seed 1004), whose per-vertex counts feed the
@@ -42,9 +43,9 @@ METRIC = "input edges/s"
 UNIT = "edges/s"
 CPU_SAMPLE_PAIRS = 24_000_000      # cpu_baseline: first pairs of the workload
 REF_SAMPLE_PAIRS = 6_000_000       # reference arm: per step
-KERNEL_OF_PHASE = {"canon": "k_canon", "sort1": "k_radix_pass", "degree": "k_unique_degree",
+KERNEL_OF_PHASE = {"canon": "k_canon", "lists": "k_sort_lists",
                    "rank": "k_rank_keys+k_radix_pass",
-                   "orient": "k_orient", "sort2": "k_radix_pass", "offsets": "k_offsets",
+                   "orient": "k_orient", "sort": "k_radix_pass", "offsets": "k_offsets",
                    "groups": "k_group_keys+k_radix_pass+k_offsets", "count": "k_count"}
 
 
@@ -221,7 +222,7 @@ def roofline(prof: dict, steps: int, m_in: int, m: int, n: int, workload: str,
     partner ids (4m), both offset arrays (8(n+1)) and, per vertex, t[] in
     rank space written, gathered and written again (28n)."""
     b = max(1, (max(n, 2) - 1).bit_length())
-    passes1, passes2 = (2 * b + 7) // 8, (b + 7) // 8
+    passes2 = (b + 7) // 8
     per_kernel = {}
     for phase, (ms, launches) in prof.items():
         k = KERNEL_OF_PHASE[phase]
@@ -246,9 +247,10 @@ def roofline(prof: dict, steps: int, m_in: int, m: int, n: int, workload: str,
                                          / t / 1e9, 1)}
     elif kernel == "k_radix_pass":
         units = launches
-        total = passes1 * 16 * m_in + (passes2 - 1) * 16 * m + 12 * m
-        bytes_per_launch = total / (passes1 + passes2)
-        how = "8-byte key read + 8-byte key write per key per pass (last pass writes 4 bytes)"
+        total = (passes2 - 1) * 16 * m_in + 12 * m_in
+        bytes_per_launch = total / passes2
+        how = ("sort by owner: 8-byte key read + 8-byte key write per key per pass (the last "
+               "pass writes 4 + 4 bytes)")
     else:
         units = launches
         bytes_per_launch = 16 * m_in

@@ -360,16 +360,15 @@ const char *tc_last_error_detail(void);
  *   tc_phase_name       name of phase i.
  */
 enum {
-  TC_PHASE_CANON = 0,   /* validate ids, drop loops, 64-bit keys, digit histograms */
-  TC_PHASE_SORT1 = 1,   /* LSD radix sort of the undirected keys */
-  TC_PHASE_DEGREE = 2,  /* drop repeats, degree histogram */
-  TC_PHASE_RANK = 3,    /* vertex ranks in (degree, id) order */
-  TC_PHASE_ORIENT = 4,  /* compact + orient from the lower rank + out-degree */
-  TC_PHASE_SORT2 = 5,   /* LSD radix sort by owner, unzip to the column array */
-  TC_PHASE_OFFSETS = 6, /* node array by exclusive scan */
-  TC_PHASE_GROUPS = 7,  /* each forward edge to the endpoint with the longer list */
-  TC_PHASE_COUNT = 8,   /* intersections, reductions, counts back to caller ids */
-  TC_NUM_PHASES = 9
+  TC_PHASE_CANON = 0,   /* validate ids, drop loops, 64-bit keys, degrees */
+  TC_PHASE_RANK = 1,    /* vertex ranks in (degree, id) order */
+  TC_PHASE_ORIENT = 2,  /* compact + orient from the lower rank + owner histograms */
+  TC_PHASE_SORT = 3,    /* LSD radix sort by owner, unzip to the column array */
+  TC_PHASE_OFFSETS = 4, /* node array by exclusive scan */
+  TC_PHASE_LISTS = 5,   /* every forward list sorted, repeated edges dropped */
+  TC_PHASE_GROUPS = 6,  /* each forward edge to the endpoint with the longer list */
+  TC_PHASE_COUNT = 7,   /* intersections, reductions, counts back to caller ids */
+  TC_NUM_PHASES = 8
 };
 uint64_t tc_launch_count(void);
 void tc_profile_enable(int on);

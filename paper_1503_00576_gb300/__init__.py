@@ -43,7 +43,7 @@ TC_ERR_CUDA = 4
 TC_ERR_TIMEOUT = 5
 TC_ERR_OVERFLOW = 6
 TC_COUNT_ERROR = (1 << 64) - 1
-PHASES = ("canon", "sort1", "degree", "rank", "orient", "sort2", "offsets", "groups", "count")
+PHASES = ("canon", "rank", "orient", "sort", "offsets", "lists", "groups", "count")
 
 # Every symbol include/tc.h and include/tc_debug.h declare.
 EXPORTS = ("tc_count", "tc_count_per_vertex", "tc_count_part", "tc_count_per_vertex_part",

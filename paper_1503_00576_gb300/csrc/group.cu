@@ -90,12 +90,39 @@ __device__ __forceinline__ void warp_sort_regs(int32_t (&x)[E]) {
   }
 }
 
-// The warp sorts the list of lane `src` (d entries from col + b) into col4
-// from entry w4, with E keys per lane (32 E >= d), and records its minimum.
+// Where the list sort leaves its results (see launch_sort_lists).
+struct ListOut {
+  int32_t *col4;   // sorted lists, padded with -1 to whole 32-byte blocks
+  int32_t *dlen;   // length of a list that held repeats, after dropping them
+  int32_t *dcorr;  // per rank: repeated edges dropped at that vertex
+  Ctrl *ctrl;
+};
+
+// A repeat of edge (u, x) in the sorted list of u is dropped: it had added
+// one to the degree of both ends.
+__device__ __forceinline__ void drop_repeat(int32_t u, int32_t x, const ListOut &o) {
+  atomicAdd(&o.dcorr[u], 1);
+  atomicAdd(&o.dcorr[x], 1);
+  *(volatile uint32_t *)&o.ctrl->dups = 1u;
+}
+
+// Key e*32 + lane of a warp-striped sorted list repeats the key before it.
+template <int E>
+__device__ __forceinline__ bool warp_repeat(const int32_t (&x)[E], int e, int32_t d) {
+  const int lane = threadIdx.x & 31;
+  int32_t p = __shfl_up_sync(kFull, x[e], 1);
+  const int32_t q = __shfl_sync(kFull, x[e > 0 ? e - 1 : 0], 31);
+  if (lane == 0) p = q;
+  const int i = e * 32 + lane;
+  return i > 0 && i < d && x[e] == p;
+}
+
+// The warp sorts list v (d entries from col + b) into col4 from entry w4,
+// with E keys per lane (32 E >= d), dropping repeated entries.
 template <int E>
 __device__ __forceinline__ void warp_sort_list(const int32_t *__restrict__ col, int32_t b,
-                                               int32_t d, long long w4,
-                                               int32_t *__restrict__ col4, int32_t *lmin_v) {
+                                               int32_t d, long long w4, int32_t v,
+                                               const ListOut &o) {
   const int lane = threadIdx.x & 31;
   int32_t x[E];
 #pragma unroll
@@ -105,12 +132,32 @@ __device__ __forceinline__ void warp_sort_list(const int32_t *__restrict__ col, 
   }
   warp_sort_regs<E>(x);
   const int r8 = (d + 7) & ~7;
+  uint32_t reps = 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) reps |= __ballot_sync(kFull, warp_repeat<E>(x, e, d));
+  if (reps == 0) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int i = e * 32 + lane;
+      if (i < r8) o.col4[w4 + i] = i < d ? x[e] : -1;
+    }
+    return;
+  }
+  // some entry repeats (an edge given more than once): compact the rest
+  const uint32_t lt = (1u << lane) - 1u;
+  int len = 0;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int i = e * 32 + lane;
-    if (i < r8) col4[w4 + i] = i < d ? x[e] : -1;
+    const bool rep = warp_repeat<E>(x, e, d);
+    const bool keep = i < d && !rep;
+    const uint32_t bk = __ballot_sync(kFull, keep);
+    if (keep) o.col4[w4 + len + __popc(bk & lt)] = x[e];
+    if (rep) drop_repeat(v, x[e], o);
+    len += __popc(bk);
   }
-  if (lane == 0) *lmin_v = x[0];
+  for (int i = len + lane; i < r8; i += 32) o.col4[w4 + i] = -1;
+  if (lane == 0) o.dlen[v] = len;
 }
 
 // Bitonic sort of buf[0..P) (P a power of two) by a whole block of G
@@ -138,21 +185,85 @@ __device__ __forceinline__ int pow2_at_least(int x) {
   return p;
 }
 
-// Every forward list into col4, sorted ascending and padded with -1 to
-// whole 32-byte blocks.  Warps take 32 consecutive vertices at a time: a
-// list of up to 8 entries is sorted by its own lane in registers (a sorting
-// network), one of up to kWarpSortMax entries by the warp in registers
-// (bitonic, up to 16 keys per lane); longer lists go to k_sort_long_lists.
+// Exclusive scan of one value per thread over a block of G threads; *total
+// gets the sum.  All threads must call it; s_warp holds G / 32 words.
+template <int G>
+__device__ __forceinline__ uint32_t block_scan(uint32_t x, uint32_t *s_warp, uint32_t *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  uint32_t before = 0, all = 0;
+#pragma unroll
+  for (int w = 0; w < G / 32; ++w) {
+    const uint32_t t = s_warp[w];
+    if (w < warp) before += t;
+    all += t;
+  }
+  __syncthreads();  // s_warp is reused by the next call
+  *total = all;
+  return before + incl - x;
+}
+
+// Copies the sorted list buf[0..d) of vertex v to dst without its repeated
+// entries, padded with -1 up to r8 entries, by a block of G threads (buf in
+// shared or global memory, written before the last barrier).
+template <int G>
+__device__ void cta_unique_copy(const int32_t *buf, int32_t d, int32_t *__restrict__ dst,
+                                int32_t r8, int32_t v, const ListOut &o, uint32_t *s_warp,
+                                int32_t *s_len) {
+  constexpr int PER = 16;  // consecutive entries per thread
+  const int tid = threadIdx.x;
+  int32_t len = 0;  // uniform: entries written so far
+  for (int32_t t0 = 0; t0 < d; t0 += G * PER) {
+    const int32_t j0 = t0 + tid * PER;
+    uint32_t keep = 0, cnt = 0;
+    int32_t prev = (j0 > 0 && j0 < d) ? buf[j0 - 1] : 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int32_t j = j0 + q;
+      if (j < d) {
+        const int32_t x = buf[j];
+        const bool k = j == 0 || x != prev;
+        if (!k) drop_repeat(v, x, o);
+        prev = x;
+        keep |= (uint32_t)k << q;
+        cnt += k;
+      }
+    }
+    uint32_t total;
+    uint32_t pos = (uint32_t)len + block_scan<G>(cnt, s_warp, &total);
+#pragma unroll
+    for (int q = 0; q < PER; ++q)
+      if ((keep >> q) & 1u) dst[pos++] = buf[j0 + q];
+    len += (int32_t)total;
+  }
+  for (int32_t j = len + tid; j < r8; j += G) dst[j] = -1;
+  if (tid == 0) {
+    if (len < d) o.dlen[v] = len;
+    *s_len = len;
+  }
+}
+
+// Every forward list into col4, sorted ascending, without repeated entries
+// and padded with -1 to whole 32-byte blocks.  Warps take 32 consecutive
+// vertices at a time: a list of up to 8 entries is sorted by its own lane in
+// registers (a sorting network), one of up to kWarpSortMax entries by the
+// warp in registers (bitonic, up to 16 keys per lane); longer lists go to
+// k_sort_long_lists_warp and k_sort_long_lists.
 __global__ void __launch_bounds__(kListThreads)
 k_sort_lists(const int32_t *__restrict__ col, const int32_t *__restrict__ off,
-             const int32_t *__restrict__ voff, int32_t n, Ctrl *ctrl, int32_t *__restrict__ col4,
-             int32_t *__restrict__ lmin, int32_t *__restrict__ long_lists) {
+             const int32_t *__restrict__ voff, int32_t n, ListOut o,
+             int32_t *__restrict__ long_lists) {
+  Ctrl *ctrl = o.ctrl;
   if (aborted(ctrl)) return;  // an earlier wait of this call ran out
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t warps = gridDim.x * kListWarps;
-  // lists of the dense hub block need no order: the hash path skips their
-  // streams whole and hashes them as they come
-  const uint32_t unsorted_from = ctrl->hub_on ? ctrl->hub_lo : 0xffffffffu;
   for (uint32_t c = blockIdx.x * kListWarps + warp; c * 32u < (uint32_t)n; c += warps) {
     const uint32_t v = c * 32u + lane;
     int32_t b = 0, d = 0;
@@ -161,32 +272,32 @@ k_sort_lists(const int32_t *__restrict__ col, const int32_t *__restrict__ off,
       b = __ldg(off + v);
       d = __ldg(off + v + 1) - b;
       w4 = 4ll * __ldg(voff + v);
-      if (d == 0) lmin[v] = INT32_MAX;
-    }
-    if (c * 32u >= unsorted_from) {  // a whole chunk of hub lists: copied as they are
-      const uint32_t copy = __ballot_sync(kFull, d > 0);
-      for (uint32_t todo = copy; todo; todo &= todo - 1) {
-        const int src = __ffs(todo) - 1;
-        const int32_t lb = __shfl_sync(kFull, b, src), ld = __shfl_sync(kFull, d, src);
-        const long long lw = __shfl_sync(kFull, w4, src);
-        const int r8 = (ld + 7) & ~7;
-        for (int i = lane; i < r8; i += 32) col4[lw + i] = i < ld ? __ldg(col + lb + i) : -1;
-      }
-      if (d > 0) lmin[v] = INT32_MIN;  // unsorted
-      continue;
     }
     if (d > 0 && d <= 8) {
       int32_t x[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) x[i] = i < d ? __ldg(col + b + i) : INT32_MAX;
       sort8(x);
+      uint32_t reps = 0;  // bit i: entry i repeats entry i - 1
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
-        if (i >= d) x[i] = -1;
-      int4 *dst = reinterpret_cast<int4 *>(col4 + w4);
-      dst[0] = make_int4(x[0], x[1], x[2], x[3]);
-      dst[1] = make_int4(x[4], x[5], x[6], x[7]);
-      lmin[v] = x[0];
+      for (int i = 1; i < 8; ++i) reps |= (uint32_t)(i < d && x[i] == x[i - 1]) << i;
+      if (reps == 0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (i >= d) x[i] = -1;
+        int4 *dst = reinterpret_cast<int4 *>(o.col4 + w4);
+        dst[0] = make_int4(x[0], x[1], x[2], x[3]);
+        dst[1] = make_int4(x[4], x[5], x[6], x[7]);
+      } else {  // an edge given more than once
+        int len = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          if (i < d && ((reps >> i) & 1u)) drop_repeat((int32_t)v, x[i], o);
+          else if (i < d) o.col4[w4 + len++] = x[i];
+        }
+        for (int i = len; i < 8; ++i) o.col4[w4 + i] = -1;
+        o.dlen[v] = len;
+      }
     }
     uint32_t todo = __ballot_sync(kFull, d > 8 && d <= kWarpSortMax);
     while (todo) {
@@ -194,12 +305,12 @@ k_sort_lists(const int32_t *__restrict__ col, const int32_t *__restrict__ off,
       todo &= todo - 1;
       const int32_t lb = __shfl_sync(kFull, b, src), ld = __shfl_sync(kFull, d, src);
       const long long lw = __shfl_sync(kFull, w4, src);
-      int32_t *lm = lmin + c * 32u + src;
-      if (ld <= 32) warp_sort_list<1>(col, lb, ld, lw, col4, lm);
-      else if (ld <= 64) warp_sort_list<2>(col, lb, ld, lw, col4, lm);
-      else if (ld <= 128) warp_sort_list<4>(col, lb, ld, lw, col4, lm);
-      else if (ld <= 256) warp_sort_list<8>(col, lb, ld, lw, col4, lm);
-      else warp_sort_list<16>(col, lb, ld, lw, col4, lm);
+      const int32_t lv = (int32_t)(c * 32u) + src;
+      if (ld <= 32) warp_sort_list<1>(col, lb, ld, lw, lv, o);
+      else if (ld <= 64) warp_sort_list<2>(col, lb, ld, lw, lv, o);
+      else if (ld <= 128) warp_sort_list<4>(col, lb, ld, lw, lv, o);
+      else if (ld <= 256) warp_sort_list<8>(col, lb, ld, lw, lv, o);
+      else warp_sort_list<16>(col, lb, ld, lw, lv, o);
     }
     const bool is_long = d > kWarpSortMax;
     const uint32_t bl = __ballot_sync(kFull, is_long);
@@ -218,8 +329,9 @@ constexpr int kWarpLongMax = 2 * kWarpSortMax;
 
 __global__ void __launch_bounds__(kListThreads)
 k_sort_long_lists_warp(const int32_t *__restrict__ col, const int32_t *__restrict__ off,
-                       const int32_t *__restrict__ voff, Ctrl *ctrl, int32_t *__restrict__ col4,
-                       int32_t *__restrict__ lmin, const int32_t *__restrict__ long_lists) {
+                       const int32_t *__restrict__ voff, ListOut o,
+                       const int32_t *__restrict__ long_lists) {
+  Ctrl *ctrl = o.ctrl;
   if (aborted(ctrl)) return;
   const int lane = threadIdx.x & 31;
   const uint32_t count = ctrl->n_long_lists;
@@ -231,22 +343,43 @@ k_sort_long_lists_warp(const int32_t *__restrict__ col, const int32_t *__restric
     const int32_t v = __ldg(long_lists + i);
     const int32_t b = __ldg(off + v), d = __ldg(off + v + 1) - b;
     if (d > kWarpLongMax) continue;  // the CTA kernel's
-    warp_sort_list<kWarpLongMax / 32>(col, b, d, 4ll * __ldg(voff + v), col4, lmin + v);
+    warp_sort_list<kWarpLongMax / 32>(col, b, d, 4ll * __ldg(voff + v), v, o);
   }
 }
 
-// Lists longer than kWarpLongMax: one CTA each, sorted in shared memory up
-// to kCtaSortMax entries; longer lists are copied unsorted and flagged in
-// lmin (their streams then skip nothing).
+// Number of entries of the sorted a[0..len) below x (lower) or not above x
+// (upper); plain loads (a may have been written by this kernel).
+__device__ __forceinline__ int32_t count_below(const int32_t *a, int32_t len, int32_t x,
+                                               bool or_equal) {
+  int32_t lo = 0, hi = len;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi) >> 1;
+    const int32_t y = a[mid];
+    if (y < x || (or_equal && y == x)) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Lists longer than kWarpLongMax: one CTA each.  Up to kCtaSortMax entries
+// the list is sorted in shared memory; a longer one (only with a dense core
+// of more than kCtaSortMax vertices) is sorted in chunks of kCtaSortMax,
+// which are then merged pairwise in global memory, alternating between the
+// list's own region of the column array and its region of col4 so that the
+// last merge lands in the column array.  Then the repeats are dropped on
+// the way into col4.
 __global__ void __launch_bounds__(kLongListThreads, kLongListBlocks)
-k_sort_long_lists(const int32_t *__restrict__ col, const int32_t *__restrict__ off,
-                  const int32_t *__restrict__ voff, Ctrl *ctrl, int32_t *__restrict__ col4,
-                  int32_t *__restrict__ lmin, const int32_t *__restrict__ long_lists) {
+k_sort_long_lists(int32_t *col, const int32_t *__restrict__ off,
+                  const int32_t *__restrict__ voff, ListOut o,
+                  const int32_t *__restrict__ long_lists) {
+  constexpr int G = kLongListThreads;
   __shared__ int32_t s_buf[kCtaSortMax];
-  __shared__ int32_t s_min[kLongListThreads / 32];
+  __shared__ uint32_t s_warp[G / 32];
   __shared__ uint32_t s_i;
+  __shared__ int32_t s_len;
+  Ctrl *ctrl = o.ctrl;
   if (aborted(ctrl)) return;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const uint32_t count = ctrl->n_long_lists;
   for (;;) {
     if (tid == 0) s_i = atomicAdd(&ctrl->next_long_list, 1u);
@@ -256,34 +389,78 @@ k_sort_long_lists(const int32_t *__restrict__ col, const int32_t *__restrict__ o
     const int32_t v = __ldg(long_lists + i);
     const int32_t b = __ldg(off + v), d = __ldg(off + v + 1) - b;
     if (d > kWarpLongMax) {  // shorter lists are the warp kernel's (uniform for the block)
-      int32_t *dst = col4 + 4ll * __ldg(voff + v);
+      int32_t *dst = o.col4 + 4ll * __ldg(voff + v);
       const int r8 = (d + 7) & ~7;
       if (d <= kCtaSortMax) {
         const int P = pow2_at_least(d);
-        for (int j = tid; j < P; j += kLongListThreads) s_buf[j] = j < d ? __ldg(col + b + j) : INT32_MAX;
+        for (int j = tid; j < P; j += G) s_buf[j] = j < d ? col[b + j] : INT32_MAX;
         __syncthreads();
-        bitonic_smem<kLongListThreads>(s_buf, P, tid);
-        for (int j = tid; j < r8; j += kLongListThreads) dst[j] = j < d ? s_buf[j] : -1;
-        if (tid == 0) lmin[v] = s_buf[0];
+        bitonic_smem<G>(s_buf, P, tid);
+        cta_unique_copy<G>(s_buf, d, dst, r8, v, o, s_warp, &s_len);
       } else {
-        int32_t mn = INT32_MAX;
-        for (int j = tid; j < r8; j += kLongListThreads) {
-          const int32_t x = j < d ? __ldg(col + b + j) : -1;
-          dst[j] = x;
-          if (j < d) mn = min(mn, x);
+        int32_t *A = col + b;  // the list's region of the column array: d entries
+        int32_t *B = dst;      // its region of col4: r8 >= d entries
+        const int32_t chunks = (d + kCtaSortMax - 1) / kCtaSortMax;
+        int levels = 0;
+        while ((1 << levels) < chunks) ++levels;
+        int32_t *src = (levels & 1) ? B : A;
+        for (int32_t c0 = 0; c0 < d; c0 += kCtaSortMax) {
+          const int32_t len = min(kCtaSortMax, d - c0);
+          for (int j = tid; j < kCtaSortMax; j += G) s_buf[j] = j < len ? A[c0 + j] : INT32_MAX;
+          __syncthreads();
+          bitonic_smem<G>(s_buf, kCtaSortMax, tid);
+          for (int j = tid; j < len; j += G) src[c0 + j] = s_buf[j];
+          __syncthreads();
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(kFull, mn, o));
-        if (lane == 0) s_min[warp] = mn;
-        __syncthreads();
-        if (tid == 0) {
-          for (int w = 1; w < kLongListThreads / 32; ++w) mn = min(mn, s_min[w]);
-          lmin[v] = -1 - mn;  // unsorted
+        int32_t *to = src == A ? B : A;
+        for (int32_t w = kCtaSortMax; w < d; w <<= 1) {
+          // runs [s0, s0 + w) and [s0 + w, s0 + 2w) merged into to[s0 ..):
+          // an entry's place is its place in its run plus the entries of the
+          // other run before it (ties: the first run's entries first)
+          for (int32_t j = tid; j < d; j += G) {
+            const int32_t s0 = j / (2 * w) * (2 * w);
+            const int32_t am = min(s0 + w, d), be = min(s0 + 2 * w, d);
+            const int32_t x = src[j];
+            const int32_t at = j < am ? (j - s0) + count_below(src + am, be - am, x, false)
+                                      : (j - am) + count_below(src + s0, am - s0, x, true);
+            to[s0 + at] = x;
+          }
+          __syncthreads();
+          int32_t *t = src;
+          src = to;
+          to = t;
         }
+        cta_unique_copy<G>(A, d, B, r8, v, o, s_warp, &s_len);
       }
     }
     __syncthreads();  // s_buf and s_i are reused
   }
+}
+
+// The row array again after repeats were dropped: row[off[v] + i] = v (off:
+// the recounted node array).  One warp per vertex; only when some list held
+// a repeat.
+__global__ void __launch_bounds__(kListThreads)
+k_fix_rows(const int32_t *__restrict__ off, int32_t n, const Ctrl *ctrl,
+           int32_t *__restrict__ row) {
+  if (aborted(ctrl) || *(volatile const uint32_t *)&ctrl->dups == 0u) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * kListWarps;
+  for (uint32_t v = (blockIdx.x * kListThreads + threadIdx.x) >> 5; v < (uint32_t)n; v += warps) {
+    const int32_t b = __ldg(off + v), e = __ldg(off + v + 1);
+    for (int32_t i = b + lane; i < e; i += 32) row[i] = (int32_t)v;
+  }
+}
+
+// The degrees without repeats: deg[v] -= dcorr[rank[v]] (caller ids); only
+// when some list held a repeat.
+__global__ void __launch_bounds__(kListThreads)
+k_fix_degree(const int32_t *__restrict__ dcorr, const int32_t *__restrict__ rank, int32_t n,
+             const Ctrl *ctrl, int32_t *__restrict__ deg) {
+  if (aborted(ctrl) || *(volatile const uint32_t *)&ctrl->dups == 0u) return;
+  const uint32_t stride = gridDim.x * kListThreads;
+  for (uint32_t v = blockIdx.x * kListThreads + threadIdx.x; v < (uint32_t)n; v += stride)
+    deg[v] -= __ldg(dcorr + __ldg(rank + v));
 }
 
 // heavy_ratio_pct = 100: the longer list is always the one hashed; larger
@@ -300,7 +477,8 @@ __device__ __forceinline__ void split_edge(int32_t u, int32_t v, int64_t du, int
 }
 
 // One pass over the forward edges in owner order (row[e] = u; the sorted
-// list N+(u) of col4 holds v at position i = e - off[u]): the group key of
+// list N+(u) of col4 holds v at position i = e - off[u]; row and off are
+// those left after the list sort dropped repeated edges): the group key of
 // every edge with the digit histograms of its h field.  When the longer
 // list is v's (h = v), the intersection streams N+(u), whose entries before
 // position i are all below v; N+(h) holds only ids above h = v, so those
@@ -311,7 +489,7 @@ __device__ __forceinline__ void split_edge(int32_t u, int32_t v, int64_t du, int
 __global__ void __launch_bounds__(kGroupThreads)
 k_group_keys(const int32_t *__restrict__ row, const int32_t *__restrict__ col4,
              const int32_t *__restrict__ off, const int32_t *__restrict__ voff,
-             const int32_t *__restrict__ lmin, int b, int passes, int32_t heavy_ratio_pct,
+             int b, int passes, int32_t heavy_ratio_pct,
              const Ctrl *__restrict__ ctrl, uint64_t *__restrict__ gkeys,
              uint32_t *__restrict__ hist) {
   __shared__ uint32_t s_hist[kMaxGroupPasses * 256];
@@ -328,7 +506,6 @@ k_group_keys(const int32_t *__restrict__ row, const int32_t *__restrict__ col4,
   for (uint32_t e0 = blockIdx.x * kGroupThreads + threadIdx.x; e0 < m;
        e0 += kGroupUnroll * stride) {
     int32_t u[kGroupUnroll], ub[kGroupUnroll], ue[kGroupUnroll], uw[kGroupUnroll];
-    int32_t um[kGroupUnroll];
 #pragma unroll
     for (int q = 0; q < kGroupUnroll; ++q) {
       const uint32_t e = e0 + q * stride;
@@ -339,7 +516,6 @@ k_group_keys(const int32_t *__restrict__ row, const int32_t *__restrict__ col4,
       ub[q] = __ldg(off + u[q]);
       ue[q] = __ldg(off + u[q] + 1);
       uw[q] = __ldg(voff + u[q]);
-      um[q] = __ldg(lmin + u[q]);
     }
     int32_t v[kGroupUnroll], vd[kGroupUnroll];
 #pragma unroll
@@ -355,11 +531,9 @@ k_group_keys(const int32_t *__restrict__ row, const int32_t *__restrict__ col4,
       if (e >= m) break;
       int32_t h, l;
       split_edge(u[q], v[q], ue[q] - ub[q], vd[q], heavy_ratio_pct, h, l);
-      // the list of u is sorted unless it was too long to sort (um < 0); an
-      // edge inside the dense hub block (owner u, hence v, of rank >=
+      // an edge inside the dense hub block (owner u, hence v, of rank >=
       // hub_lo) is left to it: its stream is skipped whole
-      uint64_t skip = (carry_skip && h == v[q] && um[q] >= 0)
-                          ? (uint64_t)(((int32_t)e - ub[q]) >> 3) : 0ull;
+      uint64_t skip = (carry_skip && h == v[q]) ? (uint64_t)(((int32_t)e - ub[q]) >> 3) : 0ull;
       if (hub_on && u[q] >= hub_lo) skip = kSkipAll;
       gkeys[e] = (skip << kSkipShift) | ((uint64_t)(uint32_t)h << b) | (uint32_t)l;
       for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p * 256 + ((h >> (8 * p)) & 255)], 1u);
@@ -441,30 +615,42 @@ uint32_t group_grid(uint32_t m_bound) {
 
 }  // namespace
 
-void launch_sort_lists(const int32_t *col, const int32_t *off, const int32_t *voff, int32_t n,
-                       Ctrl *ctrl, int32_t *col4, int32_t *lmin, int32_t *long_lists,
-                       cudaStream_t st) {
+void launch_sort_lists(int32_t *col, const int32_t *off, const int32_t *voff, int32_t n,
+                       Ctrl *ctrl, int32_t *col4, int32_t *long_lists, int32_t *dlen,
+                       int32_t *dcorr, cudaStream_t st) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   sms = sms > 0 ? sms : 1;
+  const ListOut o{col4, dlen, dcorr, ctrl};
   const uint32_t chunks = ((uint32_t)n + 31u) / 32u;
   const uint32_t grid = max(1u, min((chunks + kListWarps - 1) / kListWarps, (uint32_t)sms * 8u));
-  k_sort_lists<<<grid, kListThreads, 0, st>>>(col, off, voff, n, ctrl, col4, lmin, long_lists);
-  k_sort_long_lists_warp<<<sms * 4, kListThreads, 0, st>>>(col, off, voff, ctrl, col4, lmin,
-                                                            long_lists);
-  k_sort_long_lists<<<sms * kLongListBlocks, kLongListThreads, 0, st>>>(col, off, voff, ctrl,
-                                                                        col4, lmin, long_lists);
+  k_sort_lists<<<grid, kListThreads, 0, st>>>(col, off, voff, n, o, long_lists);
+  k_sort_long_lists_warp<<<sms * 4, kListThreads, 0, st>>>(col, off, voff, o, long_lists);
+  k_sort_long_lists<<<sms * kLongListBlocks, kLongListThreads, 0, st>>>(col, off, voff, o,
+                                                                        long_lists);
   note_launch();
   note_launch();
   note_launch();
 }
 
+void launch_fix_repeats(const int32_t *off, int32_t n, const int32_t *dcorr, const int32_t *rank,
+                        Ctrl *ctrl, int32_t *row, int32_t *deg, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint32_t grid = (uint32_t)(sms > 0 ? sms : 1) * 8u;
+  k_fix_rows<<<grid, kListThreads, 0, st>>>(off, n, ctrl, row);
+  k_fix_degree<<<grid, kListThreads, 0, st>>>(dcorr, rank, n, ctrl, deg);
+  note_launch();
+  note_launch();
+}
+
 void launch_group_keys(const int32_t *row, const int32_t *col4, const int32_t *off,
-                       const int32_t *voff, const int32_t *lmin, uint32_t m_bound, int b,
+                       const int32_t *voff, uint32_t m_bound, int b,
                        int passes, int32_t heavy_ratio_pct, Ctrl *ctrl, uint64_t *gkeys,
                        uint32_t *hist, cudaStream_t st) {
-  k_group_keys<<<group_grid(m_bound), kGroupThreads, 0, st>>>(row, col4, off, voff, lmin, b,
+  k_group_keys<<<group_grid(m_bound), kGroupThreads, 0, st>>>(row, col4, off, voff, b,
                                                               passes, heavy_ratio_pct, ctrl,
                                                               gkeys, hist);
   note_launch();

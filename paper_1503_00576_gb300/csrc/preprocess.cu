@@ -3,42 +3,40 @@
 // Sec. III-B of the paper builds, from an edge array, the sorted forward
 // adjacency lists: sort the edges (as 64-bit integers, Sec. III-D), build the
 // node array, mark and remove backward edges, unzip, rebuild the node array.
-// Here the same result is reached in this order, each step one kernel:
+// Here the same lists are reached in this order, each step one kernel:
 //
 //   canon          validate ids (Sec. III-B computes n = max id + 1; here n
 //                  is given and any id >= n is an error), drop self-loops,
 //                  write the undirected key min(u,v) << b | max(u,v) with
-//                  b = bits of n, and histogram every 8-bit digit of every
-//                  key for all radix passes at once.
-//   radix pass     one stable LSD pass (onesweep: local ranking by warp
-//                  multisplit, decoupled look-back across tiles for the
-//                  global digit offsets, shared-memory staging so that the
-//                  scatter writes runs of equal digits contiguously).
-//   unique+degree  after sort 1, equal keys are adjacent: the first of each
-//                  run is a distinct edge; degree histogram of those (the
-//                  higher endpoints are counted for every key by the sort-1
-//                  pass after which the keys are in their order, one atomic
-//                  per run, and repeated keys take their count back here).
+//                  b = bits of n, and add one to the degree of both ends
+//                  (a global atomic each).  An edge given more than once is
+//                  counted as often as it is given; the list sort drops
+//                  the repeats later and takes their counts back.
 //   rank keys      the (degree, id) order of Sec. II-B as a permutation:
 //                  a stable radix sort of deg(v) << b | v whose last pass
 //                  scatters rank[v]; the rest of the pipeline runs on ranks.
-//   orient         compact the distinct edges (tile scan + look-back) and
-//                  emit each as owner << b | neighbour in rank space, the
-//                  owner being the endpoint of lower rank -- marking and
-//                  removing backward edges of Sec. III-B in one pass; also
-//                  the digit histograms of the owner field.
-//   radix passes   stable LSD passes over the owner bits only.  Sort 1 left
-//                  the keys ordered by (min, max); every entry of a forward
-//                  list that came from a flipped edge has a smaller id than
-//                  the owner and precedes, in that order, all entries of the
-//                  owner's own run, so a stable sort by owner alone leaves
-//                  each list sorted by neighbour id.  The last pass writes
-//                  the neighbour (the column array: the "unzip"), the owner
-//                  (the row array) and counts the out-degrees.
+//                  Any total order of the vertices counts every triangle
+//                  exactly once (from its lowest vertex), so the repeats in
+//                  these degrees change how the work is split, never a
+//                  count; without repeats the order is the paper's.
+//   orient         compact the keys (dropping self-loops; tile scan +
+//                  look-back) and emit each as owner << b | neighbour in
+//                  rank space, the owner being the endpoint of lower rank --
+//                  marking and removing backward edges of Sec. III-B in one
+//                  pass; also the digit histograms of the owner field.
+//   radix passes   stable LSD passes over the owner bits only.  The last
+//                  pass writes the neighbour (the column array: the
+//                  "unzip"), the owner (the row array) and counts the
+//                  out-degrees.
 //   offsets        exclusive scan of the out-degrees = node array (CSR
 //                  offsets).  The last sort pass also wrote the row of
 //                  every entry, so (row[], col[]) is the paper's unzipped
 //                  structure-of-arrays edge array.
+//
+// The paper sorts all 2m keys first (which also brings repeated edges
+// together); here no global sort of the undirected keys is needed: each
+// forward list is sorted on its own afterwards (group.cu), which is where
+// repeated edges meet and are dropped.
 #include <cstdio>
 
 #include "tc_common.cuh"
@@ -185,18 +183,15 @@ __device__ __forceinline__ void publish_aggregate(unsigned long long *status, ui
 }
 
 // ---------------------------------------------------------------------------
-// canon: validate, drop loops, undirected 64-bit keys, digit histograms
+// canon: validate, drop loops, undirected 64-bit keys, degrees
 // ---------------------------------------------------------------------------
 constexpr int kCanonThreads = 256;
 constexpr int kCanonUnroll = 4;
 
 __global__ void __launch_bounds__(kCanonThreads)
 k_canon(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, uint32_t m_in,
-        int32_t n, int b, int passes, const BatchDesc *__restrict__ batch,
-        uint64_t *__restrict__ keys, uint32_t *__restrict__ hist, Ctrl *ctrl) {
-  __shared__ uint32_t sh[kMaxSort1Passes * 256];
-  for (int i = threadIdx.x; i < passes * 256; i += kCanonThreads) sh[i] = 0;
-  __syncthreads();
+        int32_t n, int b, const BatchDesc *__restrict__ batch, uint64_t *__restrict__ keys,
+        int32_t *__restrict__ deg, Ctrl *ctrl) {
   const uint64_t sentinel = (1ull << (2 * b)) - 1;  // > every valid key; 2b <= 62
   // batch: graph g owns pairs [eo[g], eo[g+1]) and union ids from vo[g]
   int32_t ng = 0;
@@ -250,14 +245,13 @@ k_canon(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, uint32
       } else {
         const uint32_t lo = (uint32_t)(min(u, v) + shift), hi = (uint32_t)(max(u, v) + shift);
         key = ((uint64_t)lo << b) | hi;
+        atomicAdd(&deg[lo], 1);
+        atomicAdd(&deg[hi], 1);
       }
       keys[i] = key;
-      for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * 256 + ((key >> (8 * p)) & 255)], 1u);
     }
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctrl->err, kErrIdRange);
-  for (int i = threadIdx.x; i < passes * 256; i += kCanonThreads)
-    if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -290,15 +284,6 @@ __device__ __forceinline__ void radix_out(uint64_t key, uint32_t pos, void *__re
     if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&outdeg[owner], __popc(peers));
   } else if (MODE == kOutRank) {
     ((uint32_t *)out)[(uint32_t)key & col_mask] = pos;
-  } else if (MODE == kOutKeysDeg) {
-    // the staged tile is in order of the low field: equal higher endpoints
-    // sit in runs, one atomic per run (owner_shift holds b: the sentinel
-    // 2^(2b) - 1 counts nothing)
-    ((uint64_t *)out)[pos] = key;
-    const bool real = key != (1ull << (2 * owner_shift)) - 1;
-    const uint32_t hi = (uint32_t)key & col_mask;
-    const uint32_t peers = __match_any_sync(active, real ? hi : 0xffffffffu);
-    if (real && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&outdeg[hi], __popc(peers));
   } else {
     ((uint64_t *)out)[pos] = key;
   }
@@ -483,48 +468,6 @@ k_radix_pass(const uint64_t *__restrict__ in, void *__restrict__ out, uint32_t n
 }
 
 // ---------------------------------------------------------------------------
-// distinct edges after sort 1 and their degree histogram
-// ---------------------------------------------------------------------------
-constexpr int kDegThreads = 256;
-constexpr int kDegUnroll = 8;
-
-__global__ void __launch_bounds__(kDegThreads)
-k_unique_degree(const uint64_t *__restrict__ keys, const Ctrl *__restrict__ ctrl, int b,
-                int32_t *deg) {
-  if (aborted(ctrl)) return;
-  const uint32_t m_in = ctrl->m_in;
-  const uint64_t sentinel = (1ull << (2 * b)) - 1;
-  const uint64_t mask = (1ull << b) - 1;
-  const uint32_t stride = gridDim.x * kDegThreads;
-  const int lane = threadIdx.x & 31;
-  // kDegUnroll keys per thread per round, their loads issued together (the
-  // kernel is latency-bound otherwise); a round is uniform per warp
-  for (uint32_t i0 = blockIdx.x * kDegThreads + (threadIdx.x & ~31u); i0 < m_in;
-       i0 += kDegUnroll * stride) {
-    uint64_t key[kDegUnroll], prev[kDegUnroll];
-#pragma unroll
-    for (int q = 0; q < kDegUnroll; ++q) {
-      const uint32_t i = i0 + q * stride + lane;
-      key[q] = i < m_in ? __ldg(keys + i) : sentinel;
-      prev[q] = (i < m_in && i > 0) ? __ldg(keys + i - 1) : ~0ull;
-    }
-#pragma unroll
-    for (int q = 0; q < kDegUnroll; ++q) {
-      const bool first = key[q] != sentinel && prev[q] != key[q];
-      const uint32_t firsts = __ballot_sync(kFull, first);
-      // sorted keys: neighbouring lanes usually share the lower endpoint,
-      // so that side takes one atomic per run
-      const uint32_t a = (uint32_t)(key[q] >> b);
-      const uint32_t peers = __match_any_sync(kFull, first ? a : 0xffffffffu) & firsts;
-      if (first && lane == __ffs(peers) - 1) atomicAdd(&deg[a], __popc(peers));
-      // the higher endpoint was counted for every key by the sort pass that
-      // grouped the keys by it; a repeated key takes its count back
-      if (!first && key[q] != sentinel) atomicAdd(&deg[(uint32_t)(key[q] & mask)], -1);
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
 // rank keys: the order of Sec. II-B as a permutation.  Vertex v gets the key
 // deg(v) << b | v; a stable LSD sort over the degree bits leaves the keys in
 // (degree, id) order, and its last pass scatters rank[v] = position.  From
@@ -550,7 +493,7 @@ k_rank_keys(const int32_t *__restrict__ deg, int32_t n, int b, int passes,
 }
 
 // ---------------------------------------------------------------------------
-// orient: compact distinct edges, orient by rank (= (degree, id) order)
+// orient: compact the keys, orient by rank (= (degree, id) order)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kOrientThreads, 4)
 k_orient(const uint64_t *__restrict__ keys, int b,
@@ -596,14 +539,12 @@ k_orient(const uint64_t *__restrict__ keys, int b,
   const uint32_t first = (uint32_t)tid * KPT;  // this thread's keys, within the tile
   uint64_t k[KPT];
   uint32_t flags = 0, cnt = 0;
-  uint64_t prev;
-  if (first > 0) prev = s_buf[swz(first - 1)];
-  else prev = tile_base > 0 ? __ldg(keys + tile_base - 1) : ~0ull;  // ~0 differs from every key
+  // every key but the sentinel is kept, repeats included: the list sort
+  // drops those (and takes back the degrees they added)
 #pragma unroll
   for (int i = 0; i < KPT; ++i) {
     k[i] = s_buf[swz(first + i)];
-    const bool keep = k[i] != sentinel && k[i] != prev;
-    prev = k[i];
+    const bool keep = k[i] != sentinel;
     flags |= (uint32_t)keep << i;
     cnt += keep;
   }
@@ -668,7 +609,7 @@ k_orient(const uint64_t *__restrict__ keys, int b,
 // >= 2 entries in the hashed list) by the length of the hashed list: one
 // warp, or a whole CTA.
 // ---------------------------------------------------------------------------
-enum { kScanPlain = 0, kScanGroups = 1, kScanWords = 2 };
+enum { kScanPlain = 0, kScanGroups = 1, kScanWords = 2, kScanRecount = 3 };
 
 template <int KIND>
 __global__ void __launch_bounds__(kScanThreads)
@@ -681,6 +622,9 @@ k_offsets(const int32_t *__restrict__ counts, int32_t n, int32_t *__restrict__ o
   __shared__ uint32_t s_scratch[32];
   __shared__ uint32_t s_tile, s_excl, s_abort;
   const int tid = threadIdx.x, lane = tid & 31;
+  // the recount of the node array is needed only when a list held repeats
+  // (uniform for the grid: set by the list sort, before this launch)
+  if (KIND == kScanRecount && *(volatile const uint32_t *)&ctrl->dups == 0u) return;
   if (tid == 0) {
     s_tile = atomicAdd(ticket, 1u);
     s_abort = aborted(ctrl) ? 1u : 0u;
@@ -721,6 +665,7 @@ k_offsets(const int32_t *__restrict__ counts, int32_t n, int32_t *__restrict__ o
   for (int i = 0; i < IPT; ++i) {
     const uint32_t v = first + i;
     if (v < items) off[v] = (int32_t)run;
+    if (KIND == kScanRecount && v == (uint32_t)n) ctrl->m = run;  // edges left
     run += (uint32_t)d[i];
   }
   if constexpr (KIND == kScanGroups) {
@@ -776,13 +721,12 @@ cudaError_t set_wait_hooks(uint32_t spin_limit, uint32_t unpublished_tile) {
 }
 
 void launch_canon(const int32_t *src, const int32_t *dst, uint32_t m_in, int32_t n, int b,
-                  int passes, const BatchDesc *batch, uint64_t *keys, uint32_t *hist,
-                  Ctrl *ctrl, cudaStream_t st) {
+                  const BatchDesc *batch, uint64_t *keys, int32_t *deg, Ctrl *ctrl,
+                  cudaStream_t st) {
   const uint32_t want = (m_in + kCanonThreads * 8 - 1) / (kCanonThreads * 8);
   const uint32_t cap = (uint32_t)num_sms() * 8;
   const uint32_t grid = max(1u, min(want, cap));
-  k_canon<<<grid, kCanonThreads, 0, st>>>(src, dst, m_in, n, b, passes, batch, keys, hist,
-                                          ctrl);
+  k_canon<<<grid, kCanonThreads, 0, st>>>(src, dst, m_in, n, b, batch, keys, deg, ctrl);
   note_launch();
 }
 
@@ -804,10 +748,6 @@ void launch_radix_pass(const uint64_t *in, void *out, RadixOut mode, uint32_t *r
     k_radix_pass<kOutRank><<<grid, kSortThreads, 0, st>>>(in, out, n_keys_bound, n_keys_dev,
                                                           shift, col_mask, nullptr, 0, nullptr,
                                                           hist, status, ticket, ctrl);
-  else if (mode == kOutKeysDeg)
-    k_radix_pass<kOutKeysDeg><<<grid, kSortThreads, 0, st>>>(
-        in, out, n_keys_bound, n_keys_dev, shift, col_mask, nullptr, owner_shift, outdeg, hist,
-        status, ticket, ctrl);
   else
     k_radix_pass<kOutKeys><<<grid, kSortThreads, 0, st>>>(in, out, n_keys_bound, n_keys_dev,
                                                           shift, col_mask, nullptr, 0, nullptr,
@@ -820,14 +760,6 @@ void launch_rank_keys(const int32_t *deg, int32_t n, int b, int passes, uint64_t
   const uint32_t want = ((uint32_t)n + kCanonThreads * 8 - 1) / (kCanonThreads * 8);
   const uint32_t grid = max(1u, min(want, (uint32_t)num_sms() * 8));
   k_rank_keys<<<grid, kCanonThreads, 0, st>>>(deg, n, b, passes, vkeys, hist);
-  note_launch();
-}
-
-void launch_unique_degree(const uint64_t *keys, uint32_t m_in, const Ctrl *ctrl, int b,
-                          int32_t *deg, cudaStream_t st) {
-  const uint32_t want = (m_in + kDegThreads * 8 - 1) / (kDegThreads * 8);
-  const uint32_t grid = max(1u, min(want, (uint32_t)num_sms() * 8));
-  k_unique_degree<<<grid, kDegThreads, 0, st>>>(keys, ctrl, b, deg);
   note_launch();
 }
 
@@ -855,6 +787,16 @@ void launch_offsets(const int32_t *counts, int32_t n, int32_t *off, const int32_
     k_offsets<kScanPlain><<<grid, kScanThreads, 0, st>>>(counts, n, off, nullptr, nullptr,
                                                          nullptr, nullptr, tune, status, ticket,
                                                          ctrl, 0u, 1u);
+  note_launch();
+}
+
+void launch_recount(const int32_t *counts, int32_t n, int32_t *off, unsigned long long *status,
+                    uint32_t *ticket, Ctrl *ctrl, cudaStream_t st) {
+  const uint32_t items = (uint32_t)n + 1;
+  const uint32_t grid = max(1u, (items + kScanTile - 1) / kScanTile);
+  k_offsets<kScanRecount><<<grid, kScanThreads, 0, st>>>(counts, n, off, nullptr, nullptr,
+                                                         nullptr, nullptr, kDefaultTuning, status,
+                                                         ticket, ctrl, 0u, 1u);
   note_launch();
 }
 

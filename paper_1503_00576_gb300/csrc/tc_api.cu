@@ -86,8 +86,8 @@ std::mutex g_prof_mu;
 double g_prof_ms[TC_NUM_PHASES];
 uint64_t g_prof_launches[TC_NUM_PHASES];
 
-const char *const kPhaseNames[TC_NUM_PHASES] = {"canon", "sort1",   "degree", "rank", "orient",
-                                                "sort2", "offsets", "groups", "count"};
+const char *const kPhaseNames[TC_NUM_PHASES] = {"canon",   "rank",  "orient", "sort",
+                                                "offsets", "lists", "groups", "count"};
 
 // Events around each phase of one call, folded into the global totals after
 // the call has synchronised its stream.
@@ -198,9 +198,8 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
                        int32_t shard = 0, int32_t shards = 1) {
   const uint32_t m = (uint32_t)m_in;
   const int b = id_bits(n);
-  // radix passes: undirected keys (2b bits), rank keys (degree bits < 2^b),
-  // oriented keys (owner bits)
-  const int passes1 = (2 * b + 7) / 8, passes_r = (b + 7) / 8, passes2 = (b + 7) / 8;
+  // radix passes: rank keys (degree bits < 2^b), oriented keys (owner bits)
+  const int passes_r = (b + 7) / 8, passes2 = (b + 7) / 8;
   const int passes3 = (b + 7) / 8;  // group keys: the h field
   Ctrl *ctrl = reinterpret_cast<Ctrl *>(ws + L.ctrl);
   uint32_t *hist = reinterpret_cast<uint32_t *>(ws + L.hist);
@@ -209,6 +208,7 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   auto *st_scan = reinterpret_cast<unsigned long long *>(ws + L.st_scan);
   auto *st_scan2 = reinterpret_cast<unsigned long long *>(ws + L.st_scan2);
   auto *st_scan3 = reinterpret_cast<unsigned long long *>(ws + L.st_scan3);
+  auto *st_scan4 = reinterpret_cast<unsigned long long *>(ws + L.st_scan4);
   uint64_t *keys_a = reinterpret_cast<uint64_t *>(ws + L.keys_a);
   uint64_t *keys_b = reinterpret_cast<uint64_t *>(ws + L.keys_b);
   uint64_t *vkeys_a = reinterpret_cast<uint64_t *>(ws + L.vkeys_a);
@@ -223,15 +223,16 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   int32_t *cta_groups = reinterpret_cast<int32_t *>(ws + L.cta_groups);
   int32_t *big_groups = reinterpret_cast<int32_t *>(ws + L.big_groups);
   int32_t *rank = reinterpret_cast<int32_t *>(ws + L.rank);
-  // smallest entry of every forward list (the rank keys are free by then)
-  int32_t *lmin = reinterpret_cast<int32_t *>(ws + L.vkeys_b);
+  // per rank: repeated edges dropped by the list sort (the rank keys are
+  // free by then)
+  int32_t *dcorr = reinterpret_cast<int32_t *>(ws + L.vkeys_a);
   // per-vertex counts, or per-group totals of a batch, in rank space
   int64_t *t_rank = (t_out || batch) ? reinterpret_cast<int64_t *>(ws + L.t_rank) : nullptr;
   // group totals back in union ids (the rank keys are free by then)
   int64_t *tg_union = reinterpret_cast<int64_t *>(ws + L.vkeys_a);
   const size_t words = L.st_sort_words_per_pass;
   // look-back status and tile tickets: one slot per radix pass, in the order
-  // the passes run (sort 1, rank sort, sort 2)
+  // the passes run (rank sort, sort by owner, group sort)
   int slot = 0;
   auto next_pass = [&](unsigned long long **status, uint32_t **ticket) {
     *status = st_sort + words * (size_t)slot;
@@ -248,32 +249,11 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   TC_CUDA(cudaMemsetAsync(outdeg, 0, sizeof(int32_t) * (size_t)n, st), "memset outdeg");
   if (t_rank) TC_CUDA(cudaMemsetAsync(t_rank, 0, sizeof(int64_t) * (size_t)n, st), "memset t");
 
+  // undirected keys and the degrees (repeated edges counted as often as
+  // they are given; the list sort takes them back)
   pt.start(TC_PHASE_CANON);
-  launch_canon(src, dst, m, n, b, passes1, batch ? batch->desc : nullptr, keys_a, hist, ctrl, st);
+  launch_canon(src, dst, m, n, b, batch ? batch->desc : nullptr, keys_a, deg, ctrl, st);
   pt.stop(TC_PHASE_CANON);
-
-  pt.start(TC_PHASE_SORT1);
-  uint64_t *in = keys_a, *out = keys_b;
-  const uint32_t id_mask1 = (uint32_t)((1ull << b) - 1);
-  for (int p = 0; p < passes1; ++p) {
-    unsigned long long *status;
-    uint32_t *ticket;
-    next_pass(&status, &ticket);
-    // after pass hi_pass the keys are in order of their higher endpoint
-    // (the low b bits): that pass also counts it into deg
-    const bool hi_pass = p == (b + 7) / 8 - 1;
-    launch_radix_pass(in, out, hi_pass ? kOutKeysDeg : kOutKeys, nullptr, hi_pass ? deg : nullptr,
-                      m, &ctrl->m_in, 8 * p, hi_pass ? id_mask1 : 0u, hi_pass ? b : 0,
-                      hist + 256 * p, status, ticket, ctrl, st);
-    uint64_t *x = in;
-    in = out;
-    out = x;
-  }
-  pt.stop(TC_PHASE_SORT1);
-
-  pt.start(TC_PHASE_DEGREE);
-  launch_unique_degree(in, m, ctrl, b, deg, st);
-  pt.stop(TC_PHASE_DEGREE);
 
   // rank of every vertex in the (degree, id) order
   pt.start(TC_PHASE_RANK);
@@ -297,15 +277,12 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   pt.stop(TC_PHASE_RANK);
 
   pt.start(TC_PHASE_ORIENT);
-  launch_orient(in, m, b, rank, out, hist + 256 * kSort2Slot, passes2, st_orient, ctrl, st);
+  launch_orient(keys_a, m, b, rank, keys_b, hist + 256 * kSort2Slot, passes2, st_orient, ctrl,
+                st);
   pt.stop(TC_PHASE_ORIENT);
 
-  pt.start(TC_PHASE_SORT2);
-  {
-    uint64_t *x = in;
-    in = out;
-    out = x;
-  }
+  pt.start(TC_PHASE_SORT);
+  uint64_t *in = keys_b, *out = keys_a;
   // the last pass writes the column array to `out` (first 4m bytes) and the
   // row array to the second half of the same buffer
   for (int p = 0; p < passes2; ++p) {
@@ -323,9 +300,9 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
       out = x;
     }
   }
-  const int32_t *col = reinterpret_cast<const int32_t *>(out);
-  const int32_t *row = reinterpret_cast<const int32_t *>(out) + m;
-  pt.stop(TC_PHASE_SORT2);
+  int32_t *col = reinterpret_cast<int32_t *>(out);
+  int32_t *row = reinterpret_cast<int32_t *>(out) + m;
+  pt.stop(TC_PHASE_SORT);
 
   pt.start(TC_PHASE_OFFSETS);
   launch_offsets(outdeg, n, off, nullptr, nullptr, nullptr, nullptr, tune, st_scan,
@@ -338,17 +315,26 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   if (hub) launch_hub_decide(off, col, n, H, tune.hub_min_edges, t_out != nullptr, ctrl, st);
   pt.stop(TC_PHASE_OFFSETS);
 
+  // every forward list sorted into the padded column array col4 (the
+  // warp-group list is free scratch until the binning), repeated edges
+  // dropped: their lists' new lengths overwrite the out-degrees, and only if
+  // there were any, the node array, the edge count, the row array and the
+  // degrees are made right again
+  pt.start(TC_PHASE_LISTS);
+  TC_CUDA(cudaMemsetAsync(dcorr, 0, sizeof(int32_t) * (size_t)n, st), "memset repeats");
+  launch_sort_lists(col, off, voff, n, ctrl, col4, warp_groups, outdeg, dcorr, st);
+  launch_recount(outdeg, n, off, st_scan4, &ctrl->tile_ticket[kTicketRecount], ctrl, st);
+  launch_fix_repeats(off, n, dcorr, rank, ctrl, row, deg, st);
+  pt.stop(TC_PHASE_LISTS);
+
   // partner groups: each forward edge goes to the endpoint with the longer
-  // forward list.  First every list is sorted into the padded column array
-  // col4 (lmin: each list's smallest entry; the warp-group list is free
-  // scratch until the binning).  Group keys, read from the sorted lists, go
-  // to `in` (sort 2's input, free now); a radix sort over the group bits
-  // then gathers every group's partners, its last pass counting the group
-  // sizes into gcnt (the out-degree array's space) and writing the skipped
-  // blocks of each partner's stream beside the partner array.
+  // forward list.  Group keys, read from the sorted lists, go to `in` (the
+  // owner sort's input, free now); a radix sort over the group bits then
+  // gathers every group's partners, its last pass counting the group sizes
+  // into gcnt (the out-degree array's space) and writing the skipped blocks
+  // of each partner's stream beside the partner array.
   pt.start(TC_PHASE_GROUPS);
-  launch_sort_lists(col, off, voff, n, ctrl, col4, lmin, warp_groups, st);
-  launch_group_keys(row, col4, off, voff, lmin, m, b, passes3, tune.heavy_ratio_pct, ctrl, in,
+  launch_group_keys(row, col4, off, voff, m, b, passes3, tune.heavy_ratio_pct, ctrl, in,
                     hist + 256 * kGroupSlot, st);
   int32_t *gcnt = outdeg;
   TC_CUDA(cudaMemsetAsync(gcnt, 0, sizeof(int32_t) * (size_t)n, st), "memset groups");

@@ -22,9 +22,11 @@ enum : uint32_t { kErrIdRange = 1u, kErrTimeout = 2u, kErrInternal = 4u };
 constexpr uint32_t kSpinLimit = 1u << 24;
 
 // Sorted forward lists (the padded column array col4).  Lists of up to
-// kWarpSortMax entries are sorted by one warp, up to kCtaSortMax by a CTA;
-// longer ones (never met in the workloads: they need a dense core of more
-// than 8192 vertices) stay unsorted and are flagged in lmin (below).
+// kWarpSortMax entries are sorted by one warp, up to kCtaSortMax by a CTA in
+// shared memory; longer ones (never met in the workloads: they need a dense
+// core of more than 8192 vertices) by a CTA in sorted chunks of kCtaSortMax
+// merged in global memory.  Every list is sorted, and repeated entries (an
+// edge given more than once) are dropped there.
 constexpr int kWarpSortMax = 512;
 constexpr int kCtaSortMax = 8192;
 // Group keys carry, above the 2b bits of h and l, the number of leading
@@ -44,15 +46,14 @@ constexpr int32_t kHubMaxSize = 1 << 15;  // largest allowed (a multiple of 128)
 constexpr int32_t kHubMinVertices = 1 << 17;
 constexpr int64_t kHubMinEdges = 1 << 21;
 
-constexpr int kMaxSort1Passes = 8;  // 2 * 31 id bits / 8-bit digits
 constexpr int kMaxSort2Passes = 4;  // 31 owner bits / 8-bit digits
 constexpr int kMaxRankPasses = 4;   // 31 degree bits / 8-bit digits
 constexpr int kMaxGroupPasses = 4;  // 31 group bits / 8-bit digits
-constexpr int kMaxPasses = kMaxSort1Passes + kMaxSort2Passes + kMaxRankPasses + kMaxGroupPasses;
+constexpr int kMaxPasses = kMaxSort2Passes + kMaxRankPasses + kMaxGroupPasses;
 // First histogram slot of each sort.
-constexpr int kSort2Slot = kMaxSort1Passes;
-constexpr int kRankSlot = kMaxSort1Passes + kMaxSort2Passes;
-constexpr int kGroupSlot = kMaxSort1Passes + kMaxSort2Passes + kMaxRankPasses;
+constexpr int kSort2Slot = 0;
+constexpr int kRankSlot = kMaxSort2Passes;
+constexpr int kGroupSlot = kMaxSort2Passes + kMaxRankPasses;
 
 // Hub sets of the work instrumentation: the 2^(kHubLog2Min + i) highest
 // ranks, i < kHubSizes.
@@ -62,7 +63,8 @@ constexpr int kHubLog2Min = 12;
 // Control block: zeroed at the start of every call.
 struct Ctrl {
   uint32_t err;                    // kErr* bits
-  uint32_t m;                      // distinct undirected edges (set by orient)
+  uint32_t m;                      // oriented edges: set by orient (repeats included), then,
+                                   //   if any list held repeats, by the recount of its node array
   uint32_t tile_ticket[24];        // per look-back kernel: next tile to hand out
   uint32_t n_warp_groups;          // partner groups counted by one warp each
   uint32_t n_cta_groups;           // ... by a 256-thread CTA each
@@ -78,7 +80,7 @@ struct Ctrl {
   uint32_t hub_on;                 // the hub block is counted densely (hub.cu)
   uint32_t hub_lo;                 // its first rank
   uint32_t hub_size;               // its number of vertices (hub_lo + hub_size = n)
-  uint32_t pad_[1];
+  uint32_t dups;                   // some forward list held a repeated edge (set by the list sort)
   unsigned long long hub_triangles;  // triangles the dense block counted
   unsigned long long hub_est[4];   // hash lookups inside each candidate hub set (hub.cu)
   // work of the counting phase (filled only when asked for; see launch_work):
@@ -94,9 +96,10 @@ enum {
   kTicketOrient = kMaxPasses,
   kTicketScan = kMaxPasses + 1,
   kTicketGroupScan = kMaxPasses + 2,
-  kTicketVecScan = kMaxPasses + 3
+  kTicketVecScan = kMaxPasses + 3,
+  kTicketRecount = kMaxPasses + 4
 };
-static_assert(kTicketVecScan < 24, "ticket slots");
+static_assert(kTicketRecount < 24, "ticket slots");
 
 // Look-back status words: value in the low 62 bits, flag in the top 2.
 constexpr unsigned long long kFlagAggregate = 1ull << 62;
@@ -111,10 +114,6 @@ __device__ __forceinline__ bool aborted(const Ctrl *ctrl) {
   return (*(const volatile uint32_t *)&ctrl->err & kErrTimeout) != 0u;
 }
 
-// lmin[v] describes forward list v: its smallest entry if the list is
-// sorted, -1 - (its smallest entry) if it was left unsorted, INT32_MAX if
-// it is empty.
-__device__ __forceinline__ int32_t list_min(int32_t lm) { return lm >= 0 ? lm : -1 - lm; }
 #endif
 
 // Partner groups whose hashed forward list has at most kWarpMaxRow entries
@@ -151,7 +150,7 @@ struct BatchDesc {
 // Workspace layout for an input of m_in pairs and n vertices.  All offsets
 // are 256-byte aligned.
 struct Layout {
-  size_t ctrl, hist, st_sort, st_orient, st_scan, st_scan2, st_scan3;
+  size_t ctrl, hist, st_sort, st_orient, st_scan, st_scan2, st_scan3, st_scan4;
   size_t keys_a, keys_b, deg, outdeg, off, voff, goff, warp_groups, cta_groups, big_groups;
   size_t col4;
   size_t rank, vkeys_a, vkeys_b, t_rank;
@@ -185,10 +184,9 @@ inline int id_bits(int32_t n) {
   return b;
 }
 
-// Radix passes of one run over ids of b bits: the undirected keys (2b
-// bits), the rank keys (degree < 2^b), the oriented keys (owner bits) and
-// the group keys (group bits).
-inline int radix_passes(int b) { return (2 * b + 7) / 8 + 3 * ((b + 7) / 8); }
+// Radix passes of one run over ids of b bits: the rank keys (degree <
+// 2^b), the oriented keys (owner bits) and the group keys (group bits).
+inline int radix_passes(int b) { return 3 * ((b + 7) / 8); }
 
 // Whether a single-graph run of n vertices has the dense hub block.
 inline bool hub_enabled(int32_t n, int b) { return n >= kHubMinVertices && 2 * b <= kSkipShift; }
@@ -219,6 +217,7 @@ inline Layout make_layout(int64_t m_in, int32_t n, bool with_hub = false,
   L.st_scan = take(sizeof(unsigned long long) * L.scan_tiles);
   L.st_scan2 = take(sizeof(unsigned long long) * L.scan_tiles);
   L.st_scan3 = take(sizeof(unsigned long long) * L.scan_tiles);
+  L.st_scan4 = take(sizeof(unsigned long long) * L.scan_tiles);
   L.keys_a = take(sizeof(uint64_t) * m);
   L.keys_b = take(sizeof(uint64_t) * m);
   L.deg = take(sizeof(int32_t) * nv);
@@ -256,22 +255,23 @@ void note_launch();
 cudaError_t set_wait_hooks(uint32_t spin_limit, uint32_t unpublished_tile);
 
 // ---- launchers (preprocess.cu) ----
+// Undirected keys min << b | max of the pairs (self-loops and pairs with an
+// id out of range: the sentinel 2^(2b) - 1) and deg[v] += 1 at both ends of
+// every other pair (the degree with repeats; deg must be zero on entry).
 // batch == nullptr: one graph on ids [0, n).  Otherwise ids of pair i are
 // local to its graph, checked against that graph's vertex count, and
 // shifted by the graph's first union id.
 void launch_canon(const int32_t *src, const int32_t *dst, uint32_t m_in, int32_t n, int b,
-                  int passes, const BatchDesc *batch, uint64_t *keys, uint32_t *hist,
-                  Ctrl *ctrl, cudaStream_t st);
+                  const BatchDesc *batch, uint64_t *keys, int32_t *deg, Ctrl *ctrl,
+                  cudaStream_t st);
 // Output of a radix pass: the keys themselves; the column array (low bits,
 // to `out`) plus the row array (key >> owner_shift, to `row_out`) with the
 // out-degrees added to `outdeg`; or the rank scatter rank[low bits] =
 // sorted position (to `out`).
-// kOutKeysDeg: keys out, and deg[key & col_mask] += 1 for every key but the
-// sentinel (the pass after which equal low fields are adjacent).
 // kOutPartSkip: the group sort's last pass: low bits to `out` (partners),
 // key >> kSkipShift to `row_out` (skipped blocks) and the group sizes (the
 // field at owner_shift, under col_mask) added to `outdeg`.
-enum RadixOut { kOutKeys = 0, kOutColRow = 1, kOutRank = 2, kOutKeysDeg = 3, kOutPartSkip = 4 };
+enum RadixOut { kOutKeys = 0, kOutColRow = 1, kOutRank = 2, kOutPartSkip = 4 };
 void launch_radix_pass(const uint64_t *in, void *out, RadixOut mode, uint32_t *row_out,
                        int32_t *outdeg, uint32_t n_keys_bound, const uint32_t *n_keys_dev,
                        int shift, uint32_t col_mask, int owner_shift, const uint32_t *hist,
@@ -281,8 +281,9 @@ void launch_radix_pass(const uint64_t *in, void *out, RadixOut mode, uint32_t *r
 // degree field (the rank sort).
 void launch_rank_keys(const int32_t *deg, int32_t n, int b, int passes, uint64_t *vkeys,
                       uint32_t *hist, cudaStream_t st);
-void launch_unique_degree(const uint64_t *keys, uint32_t m_in, const Ctrl *ctrl, int b,
-                          int32_t *deg, cudaStream_t st);
+// Every non-sentinel key (in any order) as (lower rank) << b | (higher
+// rank), compacted, with the digit histograms of the owner field; sets
+// ctrl->m to the number written.
 void launch_orient(const uint64_t *keys, uint32_t m_in, int b, const int32_t *rank,
                    uint64_t *okeys, uint32_t *hist2, int passes2, unsigned long long *status,
                    Ctrl *ctrl, cudaStream_t st);
@@ -295,6 +296,11 @@ void launch_offsets(const int32_t *counts, int32_t n, int32_t *off, const int32_
                     int32_t *warp_list, int32_t *cta_list, int32_t *big_list, Tuning tune,
                     unsigned long long *status, uint32_t *ticket, Ctrl *ctrl, cudaStream_t st,
                     int32_t shard = 0, int32_t shards = 1);
+// The node array again, from the list lengths left after the list sort
+// dropped repeated edges, and ctrl->m = their sum; nothing (the kernel
+// returns at once) when no list held a repeat.
+void launch_recount(const int32_t *counts, int32_t n, int32_t *off, unsigned long long *status,
+                    uint32_t *ticket, Ctrl *ctrl, cudaStream_t st);
 // Exclusive scan of 2 ceil(counts / 8) -> voff[0..n]: the node array of the
 // padded column array (lists in whole 32-byte blocks), in 16-byte words.
 void launch_word_offsets(const int32_t *counts, int32_t n, int32_t *voff,
@@ -319,18 +325,29 @@ cudaError_t launch_hub_count(const int32_t *off, const int32_t *voff, const int3
 // ---- launchers (group.cu) ----
 // Sorts every forward list (the column array col, grouped by owner, node
 // array off) into the padded column array col4 (list v from 16-byte word
-// voff[v], padded with -1 to whole 32-byte blocks) and writes lmin.
-// long_lists: scratch of n entries.
-void launch_sort_lists(const int32_t *col, const int32_t *off, const int32_t *voff, int32_t n,
-                       Ctrl *ctrl, int32_t *col4, int32_t *lmin, int32_t *long_lists,
-                       cudaStream_t st);
+// voff[v], padded with -1 to whole 32-byte blocks).  A
+// repeated entry (an edge given more than once) is dropped: the list's
+// length goes to dlen[v] (written only for such lists; dlen holds the
+// lengths with repeats on entry), each dropped copy adds one to dcorr at
+// both its ends (rank space; zero on entry) and ctrl->dups is set.
+// long_lists: scratch of n entries; col is scratch for lists longer than
+// kCtaSortMax.
+void launch_sort_lists(int32_t *col, const int32_t *off, const int32_t *voff, int32_t n,
+                       Ctrl *ctrl, int32_t *col4, int32_t *long_lists, int32_t *dlen,
+                       int32_t *dcorr, cudaStream_t st);
+// After the list sort, if some list held repeats: the row array again
+// (row[off[v] + i] = v, from the recounted node array) and the degrees
+// without repeats (deg[v] -= dcorr[rank[v]], caller ids).  Both return at
+// once otherwise.
+void launch_fix_repeats(const int32_t *off, int32_t n, const int32_t *dcorr, const int32_t *rank,
+                        Ctrl *ctrl, int32_t *row, int32_t *deg, cudaStream_t st);
 // Group keys s << kSkipShift | h << b | l of every forward edge (h: the
 // endpoint with the longer forward list, l: the other one, s: the leading
 // blocks of N+(l) the intersection skips, 0 when 2b > kSkipShift), with the
 // digit histograms of the h field for the group sort.  Reads the sorted
-// lists (col4, lmin) in owner order (row).
+// lists (col4) in owner order (row).
 void launch_group_keys(const int32_t *row, const int32_t *col4, const int32_t *off,
-                       const int32_t *voff, const int32_t *lmin, uint32_t m_bound, int b,
+                       const int32_t *voff, uint32_t m_bound, int b,
                        int passes, int32_t heavy_ratio_pct, Ctrl *ctrl, uint64_t *gkeys,
                        uint32_t *hist, cudaStream_t st);
 // Instrumentation: adds the counting phase's work into ctrl->work (from the

@@ -58,9 +58,8 @@ def test_pure_host_entry_points(lib):
     assert lib.tc_status_string(0) == b"ok"
     assert lib.tc_status_string(2) == b"vertex id out of range"
     lib.tc_phase_name.restype = ctypes.c_char_p
-    assert [lib.tc_phase_name(i) for i in range(9)] == [
-        b"canon", b"sort1", b"degree", b"rank", b"orient", b"sort2", b"offsets", b"groups",
-        b"count"]
+    assert [lib.tc_phase_name(i) for i in range(8)] == [
+        b"canon", b"rank", b"orient", b"sort", b"offsets", b"lists", b"groups", b"count"]
     lib.tc_workspace_bytes.restype = ctypes.c_size_t
     lib.tc_workspace_bytes.argtypes = [ctypes.c_int64, ctypes.c_int32]
     small = lib.tc_workspace_bytes(1000, 100)

@@ -3,7 +3,8 @@ highest-ranked vertices) against the CPU oracle.
 
 A single graph of at least 2^17 vertices counts the triangles whose lowest
 vertex lies in the hub set H (the 2^14 vertices highest in the (degree, id)
-order) as a masked 0/1 matrix product on the tensor cores, and leaves the
+order; the degree counts repeated input pairs, which changes the set but
+never a count) as a masked 0/1 matrix product on the tensor cores, and leaves the
 edges inside H out of the hash-set intersections.  The threshold
 hub_min_edges (a tuning knob: counts never depend on it) forces the dense
 block on (0) or off (-1), so the same graph is counted both ways; both must
@@ -94,18 +95,19 @@ def test_dense_block_takes_the_hub_edges_off_the_hash_path(tc, graph):
 
 def triangles_among_top_ranks(src, dst, n, H):
     """Triangles with all three vertices among the H vertices highest in the
-    (degree, id) order of the cleaned graph: scipy on the induced subgraph."""
+    library's (degree, id) order -- the degree counting every non-loop input
+    pair, repeats included -- : scipy on the induced subgraph."""
     import scipy.sparse as sp
 
     s = np.asarray(src, np.int64)
     d = np.asarray(dst, np.int64)
     keep = s != d
     a, b = np.minimum(s, d)[keep], np.maximum(s, d)[keep]
+    dord = np.bincount(a, minlength=n) + np.bincount(b, minlength=n)
     key = np.unique(a * n + b)
     a, b = key // n, key % n
-    deg = np.bincount(a, minlength=n) + np.bincount(b, minlength=n)
     top = np.zeros(n, bool)
-    top[np.lexsort((np.arange(n), deg))[n - H:]] = True
+    top[np.lexsort((np.arange(n), dord))[n - H:]] = True
     idx = np.full(n, -1, np.int64)
     idx[top] = np.arange(H)
     inside = top[a] & top[b]

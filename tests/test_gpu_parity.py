@@ -145,6 +145,28 @@ def test_paper_format_each_edge_twice(tc):
     assert once == twice == oracle.forward(s, d, 5000)["T"]
 
 
+@pytest.mark.parametrize("k", [200, 300, 600, 3000, 8200])
+def test_repeated_edges_in_long_lists(tc, k):
+    """K_k with every edge given in both directions and a third of them a
+    third time, in shuffled order: each forward list holds every entry two
+    or three times before the list sort drops the repeats.  The lists of
+    up to 2k entries take the warp sort (k = 200), the warp sort of up to
+    1024 keys (300), the CTA sort in shared memory (600, 3000) and the
+    chunked sort merged in global memory (8200: lists of up to 24597
+    entries).  T = C(k,3), t(v) = C(k-1,2), deg(v) = k-1."""
+    a, b = (x.astype(np.int32) for x in np.triu_indices(k, 1))
+    rng = np.random.default_rng(k)
+    third = rng.random(len(a)) < 1 / 3
+    s = np.concatenate([a, b, a[third]])
+    d = np.concatenate([b, a, b[third]])
+    order = rng.permutation(len(s))
+    s, d = s[order], d[order]
+    T, t, deg = run_pv(tc, s, d, k)
+    assert T == math.comb(k, 3)
+    assert np.all(t == math.comb(k - 1, 2)) and np.all(deg == k - 1)
+    assert tc.tc_count(dev(s), dev(d), k) == T
+
+
 def test_id_out_of_range(tc):
     s = np.array([0, 1, 5], np.int32)
     d = np.array([1, 2, 0], np.int32)

@@ -1,7 +1,9 @@
-"""Work counters of the counting phase (tc_count_work) against the oracle.
+"""Work counters of the counting phase (tc_count_work) against numpy.
 
-The oracle gives every forward-list length d+(v) (Sec. II-B orientation);
-from it and the cleaned edge set the expected work follows directly:
+The library orders the vertices by (degree counted with repeated input
+pairs, id): without repeats that is the order of Sec. II-B, and any order
+gives the same counts.  From that order and the cleaned edge set numpy
+gives every forward-list length d+(v) and the expected work follows:
 lookups = sum over edges of the streamed (shorter, ties to the non-owner)
 list less its skipped leading blocks, inserts = the hashed lists of the
 partner groups, W = sum over edges of d+(u) + d+(v) = sum over v of
@@ -37,14 +39,18 @@ def expected_work(src, dst, n):
     d = np.asarray(dst, np.int64)
     keep = s != d
     a, b = np.minimum(s, d)[keep], np.maximum(s, d)[keep]
+    # the order's degree counts every non-loop pair, repeats included
+    dord = np.bincount(a, minlength=n) + np.bincount(b, minlength=n)
     key = np.unique(a * n + b)
     a, b = key // n, key % n
     deg = np.bincount(a, minlength=n) + np.bincount(b, minlength=n)
-    dp = oracle.out_degrees(src, dst, n).astype(np.int64)
-    # owner = the endpoint lower in the (degree, id) order
-    a_first = (deg[a] < deg[b]) | ((deg[a] == deg[b]) & (a < b))
+    # owner = the endpoint lower in the (degree with repeats, id) order
+    a_first = (dord[a] < dord[b]) | ((dord[a] == dord[b]) & (a < b))
     u = np.where(a_first, a, b)
     v = np.where(a_first, b, a)
+    dp = np.bincount(u, minlength=n).astype(np.int64)
+    if not (dord > deg).any():  # no repeats: the oracle's orientation
+        assert np.array_equal(dp, oracle.out_degrees(src, dst, n))
     du, dv = dp[u], dp[v]
     h = np.where(dv > du, v, u)  # the longer list is hashed; ties stay at the owner
     l = np.where(dv > du, u, v)
@@ -53,8 +59,8 @@ def expected_work(src, dst, n):
     W = (du + dv).sum()
     assert W == (deg * dp).sum()  # the two forms of the merge work agree
     assert dp.sum() == len(key)
-    # hub sets: the 2^12 .. 2^15 vertices highest in the (degree, id) order
-    order = np.lexsort((np.arange(n), deg))  # ascending degree, then id
+    # hub sets: the 2^12 .. 2^15 vertices highest in the order
+    order = np.lexsort((np.arange(n), dord))  # ascending degree, then id
     rank = np.empty(n, np.int64)
     rank[order] = np.arange(n)
     # sorted forward lists in rank space: N+(u) holds the ranks of u's
