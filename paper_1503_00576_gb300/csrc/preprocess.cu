@@ -186,7 +186,7 @@ __device__ __forceinline__ void publish_aggregate(unsigned long long *status, ui
 // canon: validate, drop loops, undirected 64-bit keys, degrees
 // ---------------------------------------------------------------------------
 constexpr int kCanonThreads = 256;
-constexpr int kCanonUnroll = 4;
+constexpr int kCanonUnroll = 8;
 
 __global__ void __launch_bounds__(kCanonThreads)
 k_canon(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, uint32_t m_in,
@@ -290,8 +290,11 @@ __device__ __forceinline__ void radix_out(uint64_t key, uint32_t pos, void *__re
 }
 
 // One tile of a pass.  FULL: all TILE keys of the tile exist (every tile but
-// the last), so no key needs a bounds test.
-template <int MODE, bool FULL>
+// the last), so no key needs a bounds test.  UNSTABLE: keys of equal digit
+// are ranked in any order (a shared-memory atomic per key instead of the
+// ballots): only for the first pass of a sort whose input order does not
+// matter.
+template <int MODE, bool FULL, bool UNSTABLE>
 __device__ __forceinline__ void radix_tile(RadixShared &S, const uint64_t *__restrict__ in,
                                            void *__restrict__ out, uint32_t n_keys,
                                            uint32_t tile, uint32_t gofs, int shift,
@@ -318,6 +321,10 @@ __device__ __forceinline__ void radix_tile(RadixShared &S, const uint64_t *__res
   for (int i = 0; i < KPT; ++i) {
     const bool valid = FULL || first + 32u * i < n_keys;
     const uint32_t d = (uint32_t)(k[i] >> shift) & 255u;
+    if (UNSTABLE) {
+      pk[i] = valid ? (d << 16) | atomicAdd(&S.whist[warp][d], 1u) : 0u;
+      continue;
+    }
     uint32_t peers = FULL ? kFull : __ballot_sync(kFull, valid);
 #pragma unroll
     for (int bit = 0; bit < 8; ++bit) {
@@ -437,7 +444,7 @@ k_radix_pass(const uint64_t *__restrict__ in, void *__restrict__ out, uint32_t n
              const uint32_t *__restrict__ n_keys_dev, int shift, uint32_t col_mask,
              uint32_t *__restrict__ row_out, int owner_shift, int32_t *outdeg,
              const uint32_t *__restrict__ hist, unsigned long long *__restrict__ status,
-             uint32_t *ticket, Ctrl *ctrl) {
+             uint32_t *ticket, Ctrl *ctrl, int unstable) {
   constexpr int WARPS = kSortThreads / 32, TILE = kSortTile;
   __shared__ RadixShared S;
   const int tid = threadIdx.x;
@@ -459,12 +466,21 @@ k_radix_pass(const uint64_t *__restrict__ in, void *__restrict__ out, uint32_t n
   // global start of every digit: exclusive scan of the pass histogram
   uint32_t dummy;
   const uint32_t gofs = scan256_exclusive(hist[tid], S.scratch, &dummy);
-  if (n_keys - tile_base >= (uint32_t)TILE)
-    radix_tile<MODE, true>(S, in, out, n_keys, tile, gofs, shift, col_mask, row_out, owner_shift,
-                           outdeg, status, ctrl);
-  else
-    radix_tile<MODE, false>(S, in, out, n_keys, tile, gofs, shift, col_mask, row_out,
-                            owner_shift, outdeg, status, ctrl);
+  const bool full = n_keys - tile_base >= (uint32_t)TILE;
+  if (MODE == kOutKeys && unstable) {  // uniform for the grid
+    if (full)
+      radix_tile<MODE, true, true>(S, in, out, n_keys, tile, gofs, shift, col_mask, row_out,
+                                   owner_shift, outdeg, status, ctrl);
+    else
+      radix_tile<MODE, false, true>(S, in, out, n_keys, tile, gofs, shift, col_mask, row_out,
+                                    owner_shift, outdeg, status, ctrl);
+  } else if (full) {
+    radix_tile<MODE, true, false>(S, in, out, n_keys, tile, gofs, shift, col_mask, row_out,
+                                  owner_shift, outdeg, status, ctrl);
+  } else {
+    radix_tile<MODE, false, false>(S, in, out, n_keys, tile, gofs, shift, col_mask, row_out,
+                                   owner_shift, outdeg, status, ctrl);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -723,8 +739,9 @@ cudaError_t set_wait_hooks(uint32_t spin_limit, uint32_t unpublished_tile) {
 void launch_canon(const int32_t *src, const int32_t *dst, uint32_t m_in, int32_t n, int b,
                   const BatchDesc *batch, uint64_t *keys, int32_t *deg, Ctrl *ctrl,
                   cudaStream_t st) {
+  // many pairs in flight: the degree atomics wait on L2
   const uint32_t want = (m_in + kCanonThreads * 8 - 1) / (kCanonThreads * 8);
-  const uint32_t cap = (uint32_t)num_sms() * 8;
+  const uint32_t cap = (uint32_t)num_sms() * 32;
   const uint32_t grid = max(1u, min(want, cap));
   k_canon<<<grid, kCanonThreads, 0, st>>>(src, dst, m_in, n, b, batch, keys, deg, ctrl);
   note_launch();
@@ -734,24 +751,25 @@ void launch_radix_pass(const uint64_t *in, void *out, RadixOut mode, uint32_t *r
                        int32_t *outdeg, uint32_t n_keys_bound, const uint32_t *n_keys_dev,
                        int shift, uint32_t col_mask, int owner_shift, const uint32_t *hist,
                        unsigned long long *status, uint32_t *ticket, Ctrl *ctrl,
-                       cudaStream_t st) {
+                       cudaStream_t st, bool unstable) {
   const uint32_t grid = max(1u, (n_keys_bound + kSortTile - 1) / kSortTile);
   if (mode == kOutPartSkip)
     k_radix_pass<kOutPartSkip><<<grid, kSortThreads, 0, st>>>(
         in, out, n_keys_bound, n_keys_dev, shift, col_mask, row_out, owner_shift, outdeg, hist,
-        status, ticket, ctrl);
+        status, ticket, ctrl, 0);
   else if (mode == kOutColRow)
     k_radix_pass<kOutColRow><<<grid, kSortThreads, 0, st>>>(
         in, out, n_keys_bound, n_keys_dev, shift, col_mask, row_out, owner_shift, outdeg, hist,
-        status, ticket, ctrl);
+        status, ticket, ctrl, 0);
   else if (mode == kOutRank)
     k_radix_pass<kOutRank><<<grid, kSortThreads, 0, st>>>(in, out, n_keys_bound, n_keys_dev,
                                                           shift, col_mask, nullptr, 0, nullptr,
-                                                          hist, status, ticket, ctrl);
+                                                          hist, status, ticket, ctrl, 0);
   else
     k_radix_pass<kOutKeys><<<grid, kSortThreads, 0, st>>>(in, out, n_keys_bound, n_keys_dev,
                                                           shift, col_mask, nullptr, 0, nullptr,
-                                                          hist, status, ticket, ctrl);
+                                                          hist, status, ticket, ctrl,
+                                                          unstable ? 1 : 0);
   note_launch();
 }
 

@@ -284,7 +284,9 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   pt.start(TC_PHASE_SORT);
   uint64_t *in = keys_b, *out = keys_a;
   // the last pass writes the column array to `out` (first 4m bytes) and the
-  // row array to the second half of the same buffer
+  // row array to the second half of the same buffer.  The order within a
+  // list does not matter (each list is sorted on its own later), so the
+  // first pass ranks equal digits in any order.
   for (int p = 0; p < passes2; ++p) {
     unsigned long long *status;
     uint32_t *ticket;
@@ -293,7 +295,7 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
     uint32_t *row_target = last ? reinterpret_cast<uint32_t *>(out) + m : nullptr;
     launch_radix_pass(in, out, last ? kOutColRow : kOutKeys, row_target, last ? outdeg : nullptr,
                       m, &ctrl->m, b + 8 * p, id_mask, b, hist + 256 * (kSort2Slot + p), status,
-                      ticket, ctrl, st);
+                      ticket, ctrl, st, /*unstable=*/p == 0);
     if (!last) {
       uint64_t *x = in;
       in = out;
@@ -346,11 +348,14 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
     next_pass(&status, &ticket);
     const bool last = p == passes3 - 1;
     // the last pass writes the partners l (first half of gout) and the
-    // blocks their streams skip (second half)
+    // blocks their streams skip (second half); the order of a group's
+    // partners does not matter, so the first pass ranks equal digits in
+    // any order
     const RadixOut mode = !last ? kOutKeys : skip_in_key ? kOutPartSkip : kOutColRow;
     uint32_t *skip_target = last && skip_in_key ? reinterpret_cast<uint32_t *>(gout) + m : nullptr;
     launch_radix_pass(gin, gout, mode, skip_target, last ? gcnt : nullptr, m, &ctrl->m, b + 8 * p,
-                      id_mask, b, hist + 256 * (kGroupSlot + p), status, ticket, ctrl, st);
+                      id_mask, b, hist + 256 * (kGroupSlot + p), status, ticket, ctrl, st,
+                      /*unstable=*/p == 0);
     if (!last) {
       uint64_t *x = gin;
       gin = gout;

@@ -272,11 +272,13 @@ void launch_canon(const int32_t *src, const int32_t *dst, uint32_t m_in, int32_t
 // key >> kSkipShift to `row_out` (skipped blocks) and the group sizes (the
 // field at owner_shift, under col_mask) added to `outdeg`.
 enum RadixOut { kOutKeys = 0, kOutColRow = 1, kOutRank = 2, kOutPartSkip = 4 };
+// unstable: keys of equal digit may leave in any order (kOutKeys only; the
+// first pass of a sort whose input order does not matter).
 void launch_radix_pass(const uint64_t *in, void *out, RadixOut mode, uint32_t *row_out,
                        int32_t *outdeg, uint32_t n_keys_bound, const uint32_t *n_keys_dev,
                        int shift, uint32_t col_mask, int owner_shift, const uint32_t *hist,
                        unsigned long long *status, uint32_t *ticket, Ctrl *ctrl,
-                       cudaStream_t st);
+                       cudaStream_t st, bool unstable = false);
 // Keys deg(v) << b | v for every vertex, with the digit histograms of the
 // degree field (the rank sort).
 void launch_rank_keys(const int32_t *deg, int32_t n, int b, int passes, uint64_t *vkeys,
