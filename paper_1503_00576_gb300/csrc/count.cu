@@ -91,8 +91,10 @@ struct Lists {
   const int32_t *__restrict__ voff;  // node array of col4, in 16-byte words (even)
   const int32_t *__restrict__ col4;  // forward lists, sorted, each padded with -1 to whole 32-byte blocks
   const int32_t *__restrict__ goff;  // partner-group offsets
-  const int32_t *__restrict__ part;  // partners
+  const int32_t *__restrict__ part;   // partners
   const int32_t *__restrict__ pskip;  // per partner: leading blocks of its list skipped
+  const int2 *__restrict__ desc;      // per-vertex mode, per partner: its stream
+                                      //   {first col4 word, entries} (k_stream_desc)
 };
 
 // One hash set in shared memory.
@@ -322,7 +324,8 @@ __device__ __forceinline__ void probe_windows(const Lists &g, int32_t w, int32_t
 // to the counter beside w's slot.
 template <bool PV, int W>
 __device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__restrict__ part,
-                                            const int32_t *__restrict__ pskip, int32_t np,
+                                            const int32_t *__restrict__ pskip,
+                                            const int2 *__restrict__ desc, int32_t np,
                                             int32_t c0, int32_t cs, const Table &tb,
                                             WarpScratch &ws, int64_t *t, uint64_t &found_total,
                                             uint64_t &found_group) {
@@ -331,13 +334,23 @@ __device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__res
   int32_t l = 0, dl = 0, vb = 0;
   if (lane < cs && j < np) {
     l = __ldg(part + j);
-    const int32_t skip = __ldg(pskip + j);
-    dl = __ldg(g.off + l + 1) - __ldg(g.off + l);
-    vb = __ldg(g.voff + l);
-    // the leading blocks of N+(l) below the hashed list's smallest id
-    // cannot meet it: stream from the first block that can
-    vb += 2 * skip;
-    dl = max(dl - 8 * skip, 0);
+    if (PV) {
+      // the partner's stream, written before the counting (k_stream_desc):
+      // no gathers in the chunk's set-up, whose registers the per-vertex
+      // counters need (measured: 1.6 ms of 31 at R-MAT scale 24; without
+      // counters the separate pass costs more than it saves)
+      const int2 ds = __ldg(desc + j);
+      vb = ds.x;
+      dl = ds.y;
+    } else {
+      const int32_t skip = __ldg(pskip + j);
+      dl = __ldg(g.off + l + 1) - __ldg(g.off + l);
+      vb = __ldg(g.voff + l);
+      // the leading blocks of N+(l) below the hashed list's smallest id
+      // cannot meet it: stream from the first block that can
+      vb += 2 * skip;
+      dl = max(dl - 8 * skip, 0);
+    }
   }
   const uint32_t nonempty = __ballot_sync(kFull, dl > 0);
   if (nonempty == 0) return;
@@ -482,8 +495,8 @@ __device__ __forceinline__ void cta_groups(const Lists &g, const int32_t *__rest
         c = __shfl_sync(kFull, c, 0);
         cs = __shfl_sync(kFull, cs, 0);
         if ((int32_t)c >= np) break;
-        probe_chunk<PV, W>(g, g.part + pb, g.pskip + pb, np, (int32_t)c, (int32_t)cs, tb, s_ws[warp], t,
-                           found_total, found_group);
+        probe_chunk<PV, W>(g, g.part + pb, g.pskip + pb, g.desc + pb, np, (int32_t)c, (int32_t)cs, tb, s_ws[warp],
+                           t, found_total, found_group);
       }
       __syncthreads();
       if (PV) {
@@ -530,7 +543,7 @@ __device__ __forceinline__ void warp_groups(const Lists &g, const int32_t *__res
       __syncwarp();
       uint64_t found_group = 0;
       for (int32_t c0 = 0; c0 < np; c0 += 32)
-        probe_chunk<PV, kWindows>(g, g.part + pb, g.pskip + pb, np, c0, 32, tb, ws, t, found_total,
+        probe_chunk<PV, kWindows>(g, g.part + pb, g.pskip + pb, g.desc + pb, np, c0, 32, tb, ws, t, found_total,
                                   found_group);
       if (PV || tg) {
         found_group = warp_sum_u64(found_group);
@@ -544,6 +557,39 @@ __device__ __forceinline__ void warp_groups(const Lists &g, const int32_t *__res
       }
       empty_table(tb, slot_of, hd, lane, 32);
       __syncwarp();
+    }
+  }
+}
+
+// Per-vertex mode: the stream of every partner, so that a chunk's set-up is
+// one coalesced load and no gathers.  Partner l of an edge streams N+(l)
+// from its first block that can meet the hashed list (the pskip leading
+// blocks below it cannot): {col4 word voff[l] + 2 skip, d+(l) - 8 skip
+// entries, at least 0}.
+__global__ void __launch_bounds__(256)
+k_stream_desc(const int32_t *__restrict__ part, const int32_t *__restrict__ pskip,
+              const int32_t *__restrict__ off, const int32_t *__restrict__ voff, const Ctrl *ctrl,
+              int2 *__restrict__ desc) {
+  if (aborted(ctrl)) return;  // an earlier wait of this call ran out
+  const uint32_t m = ctrl->m;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t e0 = blockIdx.x * blockDim.x + threadIdx.x; e0 < m; e0 += 4 * stride) {
+    int32_t l[4], skip[4], d[4], vb[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t e = e0 + q * stride;
+      l[q] = e < m ? __ldg(part + e) : 0;
+      skip[q] = e < m ? __ldg(pskip + e) : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      d[q] = __ldg(off + l[q] + 1) - __ldg(off + l[q]);
+      vb[q] = __ldg(voff + l[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t e = e0 + q * stride;
+      if (e < m) desc[e] = make_int2(vb[q] + 2 * skip[q], max(d[q] - 8 * skip[q], 0));
     }
   }
 }
@@ -736,14 +782,21 @@ cudaError_t prepare_count_kernels() {
 
 cudaError_t launch_count(const int32_t *off, const int32_t *voff, const int32_t *col4,
                          const int32_t *goff, const int32_t *part, const int32_t *pskip,
-                         const int32_t *warp_groups,
+                         int2 *desc, const int32_t *warp_groups,
                          const int32_t *cta_groups, const int32_t *big_groups, int32_t n,
                          Ctrl *ctrl, int64_t *t, int64_t *tg, cudaStream_t st) {
   const bool pv = t != nullptr;
   CountGrid cg;
   cudaError_t e = count_grid(pv, &cg);
   if (e != cudaSuccess) return e;
-  const Lists g{off, voff, col4, goff, part, pskip};
+  if (pv) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_stream_desc<<<(sms > 0 ? sms : 1) * 16, 256, 0, st>>>(part, pskip, off, voff, ctrl, desc);
+    note_launch();
+  }
+  const Lists g{off, voff, col4, goff, part, pskip, desc};
   // the long lists first, on their own wide CTAs
   if (pv) {
     k_count_big<true><<<cg.big_blocks, kBigThreads, big_smem<true>(), st>>>(g, big_groups, n, ctrl,

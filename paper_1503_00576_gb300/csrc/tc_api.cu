@@ -383,7 +383,9 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
                              t_out ? t_rank : nullptr, st),
             "dense hub block");
   }
-  cudaError_t e = launch_count(off, voff, col4, goff, part, pskip, warp_groups, cta_groups,
+  // each partner's stream goes to the group sort's other buffer (free now)
+  int2 *desc = reinterpret_cast<int2 *>(gin);
+  cudaError_t e = launch_count(off, voff, col4, goff, part, pskip, desc, warp_groups, cta_groups,
                                big_groups, n, ctrl, t_out ? t_rank : nullptr,
                                t_out ? nullptr : t_rank, st);
   if (e == cudaSuccess && t_out) launch_gather_counts(t_rank, rank, n, t_out, ctrl, st);

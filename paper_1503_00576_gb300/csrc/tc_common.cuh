@@ -361,10 +361,11 @@ void launch_work(const int32_t *off, const int32_t *goff, const int32_t *part,
 // ---- launchers (count.cu) ----
 // t != nullptr: per-vertex counts (rank space).  Otherwise, if tg is not
 // nullptr, tg[h] += triangles found in group h (their sum per graph is the
-// graph's count).
+// graph's count).  desc: scratch of 8 bytes per partner (each partner's
+// stream, written first).
 cudaError_t launch_count(const int32_t *off, const int32_t *voff, const int32_t *col4,
                          const int32_t *goff, const int32_t *part, const int32_t *pskip,
-                         const int32_t *warp_groups,
+                         int2 *desc, const int32_t *warp_groups,
                          const int32_t *cta_groups, const int32_t *big_groups, int32_t n,
                          Ctrl *ctrl, int64_t *t, int64_t *tg, cudaStream_t st);
 // Sets the counting kernels' attributes and occupancy for the current

@@ -336,7 +336,8 @@ def test_launch_counter_and_profile(tc):
     launched = tc.tc_launch_count() - before
     assert launched >= 8
     assert sum(x[1] for x in prof.values()) == launched
-    # the count phase launches the long-list kernel and the main kernel
+    # the count phase (total only) launches the long-list kernel and the
+    # main kernel
     assert all(ms >= 0.0 for ms, _ in prof.values()) and prof["count"][1] == 2
 
 
