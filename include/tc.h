@@ -318,7 +318,7 @@ tc_status tc_count_work_part(const int32_t *src, const int32_t *dst, int64_t m, 
  *   total_out  HOST uint64, receives T
  * Returns TC_ERR_OVERFLOW, with a message stating the bytes needed, when
  * tc_workspace_bytes(m, n) exceeds TC_NOALLOC_SCRATCH_BYTES (about
- * 27 m + 88 n bytes: up to about 1.1 million pairs with n = 2^16).
+ * 24.5 m + 92 n bytes: up to about 1.1 million pairs with n = 2^16).
  *
  * First call on a device: under CUDA's lazy module loading (the default)
  * the array and the library's kernels are loaded onto a device when they
