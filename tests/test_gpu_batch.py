@@ -152,6 +152,31 @@ def test_batch_errors(tc, batch, expected):
     assert len(tc.tc_count_batch(dev(batch.src[:0]), dev(batch.dst[:0]), [0], [])) == 0
 
 
+def test_repeated_edges_in_batch(tc):
+    """Graphs with repeats, reversed copies and self-loops, counted as one
+    union: every graph's repeats meet in its own forward lists (ids of
+    different graphs never share a list) and are dropped there, so each
+    total equals the oracle's on that graph alone."""
+    from graphgen import families as fam
+
+    parts = [fam.random_multigraph(n, m, seed) for n, m, seed in
+             [(40, 900, 1), (300, 6000, 2), (2000, 30000, 3), (7, 200, 4), (1500, 5000, 5)]]
+    # a clique given in both directions, shuffled: its lists hold every entry twice
+    a, b = (x.astype(np.int32) for x in np.triu_indices(120, 1))
+    order = np.random.default_rng(6).permutation(2 * len(a))
+    parts.append((np.concatenate([a, b])[order], np.concatenate([b, a])[order], 120))
+    src = np.concatenate([p[0] for p in parts])
+    dst = np.concatenate([p[1] for p in parts])
+    eo = np.concatenate([[0], np.cumsum([len(p[0]) for p in parts])])
+    vn = [p[2] for p in parts]
+    want = np.array([oracle.forward(*p, per_vertex=False)["T"] for p in parts], np.uint64)
+    assert want[-1] == 120 * 119 * 118 // 6
+    assert np.array_equal(tc.tc_count_batch(dev(src), dev(dst), eo, vn), want)
+    with tc.Engine(len(src) + 100, sum(vn) + 10, len(parts) + 2) as eng:
+        for _ in range(2):
+            assert np.array_equal(eng.count(src, dst, eo, vn), want)
+
+
 def test_empty_and_tiny_graphs_in_batch(tc):
     # graphs with no edges, one edge, a triangle, K5, and isolated vertices
     parts = [([], [], 4), ([0], [1], 2), ([0, 1, 2], [1, 2, 0], 3),
