@@ -95,6 +95,8 @@ struct Lists {
   const int32_t *__restrict__ pskip;  // per partner: leading blocks of its list skipped
   const int2 *__restrict__ desc;      // per-vertex mode, per partner: its stream
                                       //   {first col4 word, entries} (k_stream_desc)
+  const int2 *__restrict__ ldesc;     // per vertex: its list {voff[v], d+(v)}, one
+                                      //   8-byte gather instead of three 4-byte ones
 };
 
 // One hash set in shared memory.
@@ -381,8 +383,9 @@ __device__ __forceinline__ void probe_chunk(const Lists &g, const int32_t *__res
       dl = ds.y;
     } else {
       const int32_t skip = __ldg(pskip + j);
-      dl = __ldg(g.off + l + 1) - __ldg(g.off + l);
-      vb = __ldg(g.voff + l);
+      const int2 ld = __ldg(g.ldesc + l);
+      dl = ld.y;
+      vb = ld.x;
       // the leading blocks of N+(l) below the hashed list's smallest id
       // cannot meet it: stream from the first block that can
       vb += 2 * skip;
@@ -508,8 +511,9 @@ __device__ __forceinline__ void cta_groups(const Lists &g, const int32_t *__rest
     // lists are filled in about ascending rank, and high ranks (high
     // degrees) carry the most work: take them first to shorten the tail
     const int32_t h = __ldg(list + (n_list - 1 - gi));
-    const int32_t hd = __ldg(g.off + h + 1) - __ldg(g.off + h);
-    const int32_t *hl = g.col4 + 4 * (size_t)__ldg(g.voff + h);
+    const int2 hld = __ldg(g.ldesc + h);
+    const int32_t hd = hld.y;
+    const int32_t *hl = g.col4 + 4 * (size_t)hld.x;
     const int32_t pb = __ldg(g.goff + h), np = __ldg(g.goff + h + 1) - pb;
     const int32_t nseg = (hd + SLOTS / 2 - 1) / (SLOTS / 2);
     const int32_t seg_len = (hd + nseg - 1) / nseg;
@@ -572,8 +576,9 @@ __device__ __forceinline__ void warp_groups(const Lists &g, const int32_t *__res
     const uint32_t g1 = min(g0 + (uint32_t)kGroupChunk, n_list);
     for (uint32_t gi = g0; gi < g1; ++gi) {
       const int32_t h = __ldg(list + (n_list - 1 - gi));  // heavy (high-rank) groups first
-      const int32_t hd = __ldg(g.off + h + 1) - __ldg(g.off + h);
-      const int32_t *hl = g.col4 + 4 * (size_t)__ldg(g.voff + h);
+      const int2 hld = __ldg(g.ldesc + h);
+      const int32_t hd = hld.y;
+      const int32_t *hl = g.col4 + 4 * (size_t)hld.x;
       const int32_t pb = __ldg(g.goff + h), np = __ldg(g.goff + h + 1) - pb;
       tb.slots = table_slots(hd, WSLOTS);
       fill_table(hl, hd, tb, slot_of, lane, 32);
@@ -605,13 +610,13 @@ __device__ __forceinline__ void warp_groups(const Lists &g, const int32_t *__res
 // entries, at least 0}.
 __global__ void __launch_bounds__(256)
 k_stream_desc(const int32_t *__restrict__ part, const int32_t *__restrict__ pskip,
-              const int32_t *__restrict__ off, const int32_t *__restrict__ voff, const Ctrl *ctrl,
-              int2 *__restrict__ desc) {
+              const int2 *__restrict__ ldesc, const Ctrl *ctrl, int2 *__restrict__ desc) {
   if (aborted(ctrl)) return;  // an earlier wait of this call ran out
   const uint32_t m = ctrl->m;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t e0 = blockIdx.x * blockDim.x + threadIdx.x; e0 < m; e0 += 4 * stride) {
-    int32_t l[4], skip[4], d[4], vb[4];
+    int32_t l[4], skip[4];
+    int2 ld[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const uint32_t e = e0 + q * stride;
@@ -619,16 +624,24 @@ k_stream_desc(const int32_t *__restrict__ part, const int32_t *__restrict__ pski
       skip[q] = e < m ? __ldg(pskip + e) : 0;
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      d[q] = __ldg(off + l[q] + 1) - __ldg(off + l[q]);
-      vb[q] = __ldg(voff + l[q]);
-    }
+    for (int q = 0; q < 4; ++q) ld[q] = __ldg(ldesc + l[q]);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const uint32_t e = e0 + q * stride;
-      if (e < m) desc[e] = make_int2(vb[q] + 2 * skip[q], max(d[q] - 8 * skip[q], 0));
+      if (e < m) desc[e] = make_int2(ld[q].x + 2 * skip[q], max(ld[q].y - 8 * skip[q], 0));
     }
   }
+}
+
+// ldesc[v] = {voff[v], off[v+1] - off[v]}: each list's first col4 word and
+// length in one record (after the list sort's recount).
+__global__ void __launch_bounds__(256)
+k_list_desc(const int32_t *__restrict__ off, const int32_t *__restrict__ voff, int32_t n,
+            const Ctrl *ctrl, int2 *__restrict__ ldesc) {
+  if (aborted(ctrl)) return;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < (uint32_t)n; v += stride)
+    ldesc[v] = make_int2(__ldg(voff + v), __ldg(off + v + 1) - __ldg(off + v));
 }
 
 // Dynamic shared memory of the counting kernels: the hash table, the slot
@@ -817,7 +830,8 @@ cudaError_t prepare_count_kernels() {
   return e;
 }
 
-cudaError_t launch_count(const int32_t *off, const int32_t *voff, const int32_t *col4,
+cudaError_t launch_count(const int32_t *off, const int32_t *voff, const int2 *ldesc,
+                         const int32_t *col4,
                          const int32_t *goff, const int32_t *part, const int32_t *pskip,
                          int2 *desc, const int32_t *warp_groups,
                          const int32_t *cta_groups, const int32_t *big_groups, int32_t n,
@@ -830,10 +844,10 @@ cudaError_t launch_count(const int32_t *off, const int32_t *voff, const int32_t 
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_stream_desc<<<(sms > 0 ? sms : 1) * 16, 256, 0, st>>>(part, pskip, off, voff, ctrl, desc);
+    k_stream_desc<<<(sms > 0 ? sms : 1) * 16, 256, 0, st>>>(part, pskip, ldesc, ctrl, desc);
     note_launch();
   }
-  const Lists g{off, voff, col4, goff, part, pskip, desc};
+  const Lists g{off, voff, col4, goff, part, pskip, desc, ldesc};
   // the long lists first, on their own wide CTAs
   if (pv) {
     k_count_big<true><<<cg.big_blocks, kBigThreads, big_smem<true>(), st>>>(g, big_groups, n, ctrl,
@@ -851,6 +865,17 @@ cudaError_t launch_count(const int32_t *off, const int32_t *voff, const int32_t 
   note_launch();
   note_launch();
   return cudaGetLastError();
+}
+
+void launch_list_desc(const int32_t *off, const int32_t *voff, int32_t n, const Ctrl *ctrl,
+                      int2 *ldesc, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint32_t want = ((uint32_t)n + 255u) / 256u;
+  const uint32_t grid = max(1u, min(want, (uint32_t)(sms > 0 ? sms : 1) * 8u));
+  k_list_desc<<<grid, 256, 0, st>>>(off, voff, n, ctrl, ldesc);
+  note_launch();
 }
 
 void launch_clustering(const int64_t *t, const int32_t *deg, int32_t n, double *cc,

@@ -226,6 +226,9 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   // per rank: repeated edges dropped by the list sort (the rank keys are
   // free by then)
   int32_t *dcorr = reinterpret_cast<int32_t *>(ws + L.vkeys_a);
+  // per vertex: its list's first col4 word and length (the second rank-key
+  // buffer, free after the rank sort)
+  int2 *ldesc = reinterpret_cast<int2 *>(ws + L.vkeys_b);
   // per-vertex counts, or per-group totals of a batch, in rank space
   int64_t *t_rank = (t_out || batch) ? reinterpret_cast<int64_t *>(ws + L.t_rank) : nullptr;
   // group totals back in union ids (the rank keys are free by then)
@@ -327,6 +330,7 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   launch_sort_lists(col, off, voff, n, ctrl, col4, warp_groups, outdeg, dcorr, st);
   launch_recount(outdeg, n, off, st_scan4, &ctrl->tile_ticket[kTicketRecount], ctrl, st);
   launch_fix_repeats(off, n, dcorr, rank, ctrl, row, deg, st);
+  launch_list_desc(off, voff, n, ctrl, ldesc, st);
   pt.stop(TC_PHASE_LISTS);
 
   // partner groups: each forward edge goes to the endpoint with the longer
@@ -385,7 +389,8 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   }
   // each partner's stream goes to the group sort's other buffer (free now)
   int2 *desc = reinterpret_cast<int2 *>(gin);
-  cudaError_t e = launch_count(off, voff, col4, goff, part, pskip, desc, warp_groups, cta_groups,
+  cudaError_t e = launch_count(off, voff, ldesc, col4, goff, part, pskip, desc, warp_groups,
+                               cta_groups,
                                big_groups, n, ctrl, t_out ? t_rank : nullptr,
                                t_out ? nullptr : t_rank, st);
   if (e == cudaSuccess && t_out) launch_gather_counts(t_rank, rank, n, t_out, ctrl, st);

@@ -363,7 +363,12 @@ void launch_work(const int32_t *off, const int32_t *goff, const int32_t *part,
 // nullptr, tg[h] += triangles found in group h (their sum per graph is the
 // graph's count).  desc: scratch of 8 bytes per partner (each partner's
 // stream, written first).
-cudaError_t launch_count(const int32_t *off, const int32_t *voff, const int32_t *col4,
+// ldesc[v] = {voff[v], off[v+1] - off[v]} for every vertex (the lists' first
+// col4 word and length in one record), for the counting kernels.
+void launch_list_desc(const int32_t *off, const int32_t *voff, int32_t n, const Ctrl *ctrl,
+                      int2 *ldesc, cudaStream_t st);
+cudaError_t launch_count(const int32_t *off, const int32_t *voff, const int2 *ldesc,
+                         const int32_t *col4,
                          const int32_t *goff, const int32_t *part, const int32_t *pskip,
                          int2 *desc, const int32_t *warp_groups,
                          const int32_t *cta_groups, const int32_t *big_groups, int32_t n,
