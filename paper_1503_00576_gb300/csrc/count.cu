@@ -8,7 +8,7 @@
 // longer forward list is N+(h); partners l: their other endpoints):
 //
 //  * N+(h) is staged once in shared memory as an open-addressing hash set
-//    (multiplicative hashing, linear probing, load <= 1/16 where it fits),
+//    (multiplicative hashing, linear probing, load <= 1/32 where it fits),
 //    by one warp when the group is small, else by a whole CTA whose warps
 //    claim chunks of partners from a shared counter;
 //  * the lists N+(l) of a chunk of <= 32 partners are read as one flat
@@ -62,8 +62,9 @@ static_assert(main_slots<true>() / kMainWarps >= 4 * kWarpMaxRow,
 // Hash-set slots.  Ids are < 2^31 - 1, so 0x7fffffff marks an empty slot and
 // bit 31 of an occupied slot records that some key whose home is this slot
 // was displaced further along (linear probing).  A lookup whose home slot is
-// neither the key nor flagged is a miss after one read: at load 1/16 only
-// ~0.2% of the slots are flagged.  The padding id -1 never matches: a slot's
+// neither the key nor flagged is a miss after one read: about a^2 / 2 of the
+// slots are flagged at load a (0.05% at 1/32, 1.4% at the load 1/6 of the
+// longest lists of a table).  The padding id -1 never matches: a slot's
 // low 31 bits are non-negative.
 constexpr int32_t kEmpty = 0x7fffffff;
 constexpr uint32_t kDisplaced = 0x80000000u;
@@ -79,10 +80,13 @@ __device__ __forceinline__ uint32_t next_slot(uint32_t h, uint32_t slots) {
   return h + 1u == slots ? 0u : h + 1u;
 }
 
-// Table size for a list of len entries: load 1/16 where it fits, else the
-// whole capacity (callers keep len <= capacity / 2).
+// Table size for a list of len entries: load 1/32 where it fits, else the
+// whole capacity (callers keep len <= capacity / 2).  A lower load flags
+// fewer home slots (misses there probe on); emptying costs in proportion to
+// the list, not to the table (measured against load 1/16 at R-MAT scale 24:
+// -0.4 ms total-only, -0.15 ms per vertex).
 __device__ __forceinline__ uint32_t table_slots(int32_t len, uint32_t capacity) {
-  return min(16u * (uint32_t)max(len, 1), capacity);
+  return min(32u * (uint32_t)max(len, 1), capacity);
 }
 
 // Read-only view of the forward lists and partner groups.
@@ -208,8 +212,8 @@ __device__ __forceinline__ int32_t probe_past(int32_t x, uint32_t h, const Table
 // probed on in a warp-uniform loop, one per lane and round, so the rare part
 // costs rounds in proportion to the most such misses in one lane (usually
 // one), instead of a divergent branch per entry that nearly every window
-// took (about 2% of the home slots are flagged, and a window makes 256
-// lookups).  Measured at R-MAT scale 24: -1.2 ms per vertex, +0.4 ms
+// took (a window makes 256 lookups, so a flag rate of even 0.1% reaches
+// most windows).  Measured at R-MAT scale 24: -1.2 ms per vertex, +0.4 ms
 // without counters, so the total-only count keeps the branches.  N = 1
 // (element mode; lanes may have left): the plain test.
 template <bool PV, int N>
