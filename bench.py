@@ -435,7 +435,9 @@ def run_reference(args, world, rank, pg):
             "ms_per_step": mean * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": graphgen.WORKLOADS[args.workload][0], "n": n,
-                       "m_in": int(len(src))},
+                       "m_in": int(len(src)), "sample_pairs_per_step": pairs,
+                       "sample": "each step counts only the first %d of the %d pairs"
+                                 % (pairs, len(src))},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,

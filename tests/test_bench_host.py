@@ -1,0 +1,88 @@
+"""Host logic of bench.py, on the CPU: the roofline arithmetic of the
+counting phase, the committed traffic figure keyed by the kernel sources,
+the clock sampler's parsing, and the reference arm's JSON line (the CPU
+oracle on a bounded sample)."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _prof(count_ms, other_ms, steps):
+    names = ("canon", "rank", "orient", "sort", "offsets", "lists", "groups")
+    prof = {k: (other_ms * steps, 3 * steps) for k in names}
+    prof["count"] = (count_ms * steps, 4 * steps)
+    return prof
+
+
+def test_counting_roofline_bytes_rule():
+    work = {"lookups": 10 ** 9, "inserts": 2 * 10 ** 8, "merge_work": 5 * 10 ** 9}
+    m_in, m, n, steps = 4 * 10 ** 6, 3 * 10 ** 6, 1 << 20, 2
+    r = bench.roofline(_prof(2.0, 1.0, steps), steps, m_in, m, n, "none", work)
+    assert r["kernel"] == "k_count+k_count_big" and r["bound"] == "hbm"
+    want = 4 * (10 ** 9 + 2 * 10 ** 8) + 4 * m + 8 * (n + 1) + 28 * n
+    assert r["algorithmic_bytes_per_launch"] == want
+    assert r["ms_per_launch"] == pytest.approx(2.0)
+    assert r["achieved"] == pytest.approx(want / 2e-3 / 1e9, rel=1e-3)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"], rel=1e-3)
+    assert r["launches_timed"] == steps
+    # total-only: no per-vertex array
+    t = bench.roofline(_prof(2.0, 1.0, steps), steps, m_in, m, n, "none", work, total_only=True)
+    assert t["algorithmic_bytes_per_launch"] == want - 28 * n
+
+
+def test_roofline_picks_the_dominant_kernel():
+    work = {"lookups": 1, "inserts": 1, "merge_work": 1}
+    r = bench.roofline(_prof(0.1, 5.0, 1), 1, 4096, 4096, 1 << 12, "none", work)
+    assert r["kernel"] != "k_count+k_count_big"
+
+
+def test_committed_traffic_needs_the_current_sources(monkeypatch):
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        rec = json.load(f)["rmat24"]["k_count+k_count_big"]
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: rec["source_hash"])
+    assert bench.committed_traffic("k_count+k_count_big", "rmat24") == rec["dram_bytes_per_launch"]
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
+    assert bench.committed_traffic("k_count+k_count_big", "rmat24") is None
+    assert bench.committed_traffic("k_count+k_count_big", "er16k") is None
+
+
+def test_clock_sampler_parses_samples(tmp_path):
+    path = tmp_path / "clocks.csv"
+    path.write_text("GPU-1, 2070, 2070, 900.5, Not Active, Not Active, Not Active, Active\n"
+                    "GPU-1, 2060, 2070, 901.0, Not Active, Not Active, Not Active, Not Active\n"
+                    "GPU-2, 1000, 2070, 100.0, Active, Not Active, Not Active, Not Active\n")
+
+    class Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    c = bench.ClockSampler("GPU-1")
+    c.proc, c.path = Done(), str(path)
+    got = c.stop()
+    assert got["sm_mhz"] == pytest.approx(2065.0) and got["sm_max_mhz"] == 2070.0
+    assert got["reasons"] == ["sw_power_cap"] and got["samples"] == 2
+
+
+def test_reference_arm_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "er16k", "--steps", "2", "--warmup", "1"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["steps"] == 2
+    assert d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["config"]["sample_pairs_per_step"] == d["config"]["m_in"] == 131072
