@@ -488,7 +488,7 @@ __device__ __forceinline__ void split_edge(int32_t u, int32_t v, int64_t du, int
 // in N+(u): nothing to skip.)
 __global__ void __launch_bounds__(kGroupThreads)
 k_group_keys(const int32_t *__restrict__ row, const int32_t *__restrict__ col4,
-             const int32_t *__restrict__ off, const int32_t *__restrict__ voff,
+             const int32_t *__restrict__ off, const int2 *__restrict__ ldesc,
              int b, int passes, int32_t heavy_ratio_pct,
              const Ctrl *__restrict__ ctrl, uint64_t *__restrict__ gkeys,
              uint32_t *__restrict__ hist) {
@@ -514,8 +514,9 @@ k_group_keys(const int32_t *__restrict__ row, const int32_t *__restrict__ col4,
 #pragma unroll
     for (int q = 0; q < kGroupUnroll; ++q) {
       ub[q] = __ldg(off + u[q]);
-      ue[q] = __ldg(off + u[q] + 1);
-      uw[q] = __ldg(voff + u[q]);
+      const int2 ld = __ldg(ldesc + u[q]);  // {first col4 word, length}
+      ue[q] = ub[q] + ld.y;
+      uw[q] = ld.x;
     }
     int32_t v[kGroupUnroll], vd[kGroupUnroll];
 #pragma unroll
@@ -524,7 +525,7 @@ k_group_keys(const int32_t *__restrict__ row, const int32_t *__restrict__ col4,
       v[q] = e < m ? __ldg(col4 + 4ll * uw[q] + ((int32_t)e - ub[q])) : 0;
     }
 #pragma unroll
-    for (int q = 0; q < kGroupUnroll; ++q) vd[q] = __ldg(off + v[q] + 1) - __ldg(off + v[q]);
+    for (int q = 0; q < kGroupUnroll; ++q) vd[q] = __ldg(ldesc + v[q]).y;
 #pragma unroll
     for (int q = 0; q < kGroupUnroll; ++q) {
       const uint32_t e = e0 + q * stride;
@@ -647,10 +648,10 @@ void launch_fix_repeats(const int32_t *off, int32_t n, const int32_t *dcorr, con
 }
 
 void launch_group_keys(const int32_t *row, const int32_t *col4, const int32_t *off,
-                       const int32_t *voff, uint32_t m_bound, int b,
+                       const int2 *ldesc, uint32_t m_bound, int b,
                        int passes, int32_t heavy_ratio_pct, Ctrl *ctrl, uint64_t *gkeys,
                        uint32_t *hist, cudaStream_t st) {
-  k_group_keys<<<group_grid(m_bound), kGroupThreads, 0, st>>>(row, col4, off, voff, b,
+  k_group_keys<<<group_grid(m_bound), kGroupThreads, 0, st>>>(row, col4, off, ldesc, b,
                                                               passes, heavy_ratio_pct, ctrl,
                                                               gkeys, hist);
   note_launch();

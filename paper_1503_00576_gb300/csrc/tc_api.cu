@@ -340,7 +340,7 @@ tc_status enqueue_core(const int32_t *src, const int32_t *dst, int64_t m_in, int
   // into gcnt (the out-degree array's space) and writing the skipped blocks
   // of each partner's stream beside the partner array.
   pt.start(TC_PHASE_GROUPS);
-  launch_group_keys(row, col4, off, voff, m, b, passes3, tune.heavy_ratio_pct, ctrl, in,
+  launch_group_keys(row, col4, off, ldesc, m, b, passes3, tune.heavy_ratio_pct, ctrl, in,
                     hist + 256 * kGroupSlot, st);
   int32_t *gcnt = outdeg;
   TC_CUDA(cudaMemsetAsync(gcnt, 0, sizeof(int32_t) * (size_t)n, st), "memset groups");

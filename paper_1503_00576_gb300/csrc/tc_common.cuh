@@ -347,9 +347,10 @@ void launch_fix_repeats(const int32_t *off, int32_t n, const int32_t *dcorr, con
 // endpoint with the longer forward list, l: the other one, s: the leading
 // blocks of N+(l) the intersection skips, 0 when 2b > kSkipShift), with the
 // digit histograms of the h field for the group sort.  Reads the sorted
-// lists (col4) in owner order (row).
+// lists (col4; their first words and lengths from ldesc, see
+// launch_list_desc) in owner order (row, node array off).
 void launch_group_keys(const int32_t *row, const int32_t *col4, const int32_t *off,
-                       const int32_t *voff, uint32_t m_bound, int b,
+                       const int2 *ldesc, uint32_t m_bound, int b,
                        int passes, int32_t heavy_ratio_pct, Ctrl *ctrl, uint64_t *gkeys,
                        uint32_t *hist, cudaStream_t st);
 // Instrumentation: adds the counting phase's work into ctrl->work (from the
