@@ -5,9 +5,14 @@
  * Graphs on GPU" (arXiv 1503.00576), Sec. II-B/II-C: order the vertices by
  * (degree, id), keep each undirected edge only in the forward list N+(u) of
  * its lower endpoint, sort every forward list, and add |N+(u) & N+(v)| for
- * every forward edge (u, v).  Preprocessing follows Sec. III-B (sort the
- * edges as 64-bit keys, build the node array, drop backward edges, unzip);
- * counting follows Sec. III-C.  All arithmetic is exact integer.
+ * every forward edge (u, v).  Preprocessing reaches the sorted forward lists
+ * of Sec. III-B by its own steps (degrees by atomics, backward edges dropped
+ * while orienting, one sort of the oriented 64-bit keys by owner whose last
+ * pass unzips, node arrays by scans, every list then sorted on its own);
+ * counting computes the sum of Sec. III-C by hashing.  The order uses the
+ * degree with repeated pairs counted as given (any order counts every
+ * triangle once; without repeats it is the paper's).  All arithmetic is
+ * exact integer.
  *
  * Input format (Sec. III-A, relaxed): an edge array given as two int32 arrays
  * src[0..m) and dst[0..m), pair i being the edge {src[i], dst[i]}.  The paper
@@ -264,7 +269,8 @@ tc_status tc_engine_destroy(tc_engine *engine);
  *   inserts        sum over partner groups of the hashed list length
  *   merge_work     W = sum over forward edges of d+(u) + d+(v): the elements
  *                  a sorted-list merge of Sec. II-B would read
- *   max_out_degree the largest d+(v), at most sqrt(2m) (Sec. II-B)
+ *   max_out_degree the largest d+(v), at most sqrt(2m) (Sec. II-B; sqrt of
+ *                  twice the input pairs when some pair is repeated)
  *   triangles      T
  *   hub_lookups[i] the lookups of the forward edges whose endpoints both
  *                  lie in the hub set H_i of the 2^(12+i) vertices highest
