@@ -242,6 +242,31 @@ def test_relabel_invariance(tc):
     assert a == b == oracle.forward(s, d, n, per_vertex=False)["T"]
 
 
+def spread(s, d, n_small, n, seed):
+    """The graph (s, d) on [0, n_small) with its ids sent to distinct random
+    ids of [0, n), n - 1 among them; every other id of [0, n) is isolated."""
+    rng = np.random.default_rng(seed)
+    ids = np.empty(n_small, np.int64)
+    ids[:-1] = rng.choice(n - 1, size=n_small - 1, replace=False)
+    ids[-1] = n - 1
+    ids = ids[rng.permutation(n_small)].astype(np.int32)
+    return ids[s], ids[d]
+
+
+@pytest.mark.parametrize("n", [1 << 24, (1 << 24) + 1, (1 << 26) + 777])
+def test_wide_id_ranges(tc, n):
+    """Ids of 24, 25 and 27 bits: past 24 bits the keys leave no room for the
+    skipped blocks (every list is streamed whole), the dense hub block is off,
+    and every sort takes a fourth radix pass; 2^24 and 2^24 + 1 hold the same
+    edges on either side of that line (the extra vertex is isolated)."""
+    import graphgen
+
+    s, d = graphgen.rmat(17, 24 << 17, 47)
+    S, D = spread(s, d, 1 << 17, n, 9)
+    r = assert_same(tc, S, D, n)
+    assert r["T"] == oracle.forward(s, d, 1 << 17, per_vertex=False)["T"]
+
+
 def test_clustering_and_transitivity(tc):
     import graphgen
 
