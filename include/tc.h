@@ -33,8 +33,9 @@
  * synchronises that stream before returning.
  *
  * Errors: every call sets a thread-local status readable with
- * tc_last_error(); tc_status_string() names it.  Limits: n <= 2^31 - 1,
- * m <= 2^31 - 1 pairs (larger m gives TC_ERR_OVERFLOW).
+ * tc_last_error(); tc_status_string() names it.  Limits: n <= 2^31 - 2^10
+ * vertices and m <= 2^31 - 2^10 pairs (beyond them TC_ERR_OVERFLOW; the
+ * margin keeps every int32 index a warp advances past an end from wrapping).
  */
 #ifndef TC_H
 #define TC_H
@@ -206,7 +207,7 @@ tc_status tc_get_tuning(tc_tuning *out);
  *   edge_offsets    HOST int64[G+1], edge_offsets[0] = 0, non-decreasing
  *   vertex_counts   HOST int32[G]
  *   totals_out      HOST uint64[G]: triangles of each graph
- * Limits: total pairs and total vertices <= 2^31 - 1 (TC_ERR_OVERFLOW).  An
+ * Limits: total pairs and total vertices <= 2^31 - 2^10 (TC_ERR_OVERFLOW).  An
  * id out of range fails only the graph that holds it: the call returns
  * TC_ERR_ID_RANGE, that graph's total is TC_COUNT_ERROR and every other
  * total is still written and exact.  Synchronises.
@@ -220,7 +221,8 @@ tc_status tc_count_batch(const int32_t *src, const int32_t *dst, int32_t num_gra
  * union vertices and max_graphs graphs, allocated once, and the whole batch
  * pipeline captured once as a CUDA graph and replayed for every batch
  * (padding pairs past a batch's end are skipped, so the shape never changes).
- *   tc_engine_create   tuning NULL: the process default at creation.
+ *   tc_engine_create   tuning NULL: the process default at creation;
+ *                      max_pairs and max_vertices at most 2^31 - 2^10.
  *   tc_engine_submit   copies the batch's pairs (host or device memory, per
  *                      inputs_on_host) into the engine and launches the graph
  *                      on the engine's own stream; returns without waiting.

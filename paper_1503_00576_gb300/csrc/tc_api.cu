@@ -161,6 +161,11 @@ Ctrl *host_ctrl() {
   return h;
 }
 
+// Largest m (pairs) and n (vertices) a run accepts: 2^31 less a margin, so
+// that no int32 index a warp advances past the end of a list, a partner
+// range or a graph's vertex range (by at most a few hundred) can wrap.
+constexpr int64_t kMaxItems = ((int64_t)1 << 31) - ((int64_t)1 << 10);
+
 // The padded column array holds at most m + 7 min(n, m) entries, indexed
 // by int32 16-byte words.
 bool padded_fits(int64_t m, int64_t n) {
@@ -169,8 +174,9 @@ bool padded_fits(int64_t m, int64_t n) {
 
 tc_status check_args(const int32_t *src, const int32_t *dst, int64_t m, int32_t n) {
   if (m < 0 || n < 0) return set_status(TC_ERR_INVALID_ARG, "m=%lld n=%d", (long long)m, n);
-  if (m > (int64_t)INT32_MAX)
-    return set_status(TC_ERR_OVERFLOW, "m=%lld exceeds 2^31-1 pairs", (long long)m);
+  if (m > kMaxItems || (int64_t)n > kMaxItems)
+    return set_status(TC_ERR_OVERFLOW, "m=%lld, n=%d: beyond 2^31 - 2^10 pairs or vertices",
+                      (long long)m, n);
   if (!padded_fits(m, n))
     return set_status(TC_ERR_OVERFLOW, "m=%lld, n=%d: padded lists exceed 2^31 16-byte words",
                       (long long)m, n);
@@ -680,7 +686,7 @@ tc_status batch_id_status(const uint64_t *totals, int32_t G) {
 tc_status batch_impl(const int32_t *src, const int32_t *dst, int32_t G, const int64_t *eo,
                      const int32_t *vn, cudaStream_t st, uint64_t *totals_out) {
   BatchPlan p;
-  tc_status s = plan_batch(G, eo, vn, INT32_MAX, INT32_MAX, &p);
+  tc_status s = plan_batch(G, eo, vn, kMaxItems, kMaxItems, &p);
   if (s != TC_OK) return s;
   if (G > 0 && !totals_out) return set_status(TC_ERR_INVALID_ARG, "totals_out is NULL");
   if (p.pairs > 0 && (!src || !dst)) return set_status(TC_ERR_INVALID_ARG, "src/dst is NULL");
@@ -898,7 +904,7 @@ tc_status tc_count_per_vertex_host(const int32_t *src_host, const int32_t *dst_h
 }
 
 size_t tc_workspace_bytes(int64_t m, int32_t n) {
-  if (m < 0 || n < 0 || m > (int64_t)INT32_MAX) return 0;
+  if (m < 0 || n < 0 || m > kMaxItems || (int64_t)n > kMaxItems) return 0;
   return make_layout(m, n, true, current_tuning().hub_vertices).total;
 }
 
@@ -946,7 +952,8 @@ tc_status tc_engine_create(int64_t max_pairs, int32_t max_vertices, int32_t max_
   *out = nullptr;
   if (max_pairs < 1 || max_vertices < 1 || max_graphs < 1)
     return set_status(TC_ERR_INVALID_ARG, "capacities must be positive");
-  if (max_pairs > (int64_t)INT32_MAX) return set_status(TC_ERR_OVERFLOW, "max_pairs > 2^31-1");
+  if (max_pairs > kMaxItems || (int64_t)max_vertices > kMaxItems)
+    return set_status(TC_ERR_OVERFLOW, "max_pairs or max_vertices beyond 2^31 - 2^10");
   if (!padded_fits(max_pairs, max_vertices))
     return set_status(TC_ERR_OVERFLOW, "padded lists of the capacities exceed 2^31 words");
   tc_engine *e = new tc_engine;

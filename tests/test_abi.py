@@ -68,6 +68,12 @@ def test_pure_host_entry_points(lib):
     assert big >= 2 * 8 * 10 ** 8  # two key buffers of 8 bytes per pair
     assert lib.tc_workspace_bytes(-1, 5) == 0
     assert lib.tc_workspace_bytes(1 << 31, 5) == 0
+    # the limits: 2^31 - 2^10 pairs and vertices, one more is refused
+    top = (1 << 31) - (1 << 10)
+    assert lib.tc_workspace_bytes(top, 5) > 16 * top
+    assert lib.tc_workspace_bytes(top + 1, 5) == 0
+    assert lib.tc_workspace_bytes(5, top) > lib.tc_workspace_bytes(5, 1 << 20)
+    assert lib.tc_workspace_bytes(5, top + 1) == 0
 
 
 def test_missing_library_fails_loudly(tmp_path):
