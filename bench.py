@@ -20,6 +20,10 @@ every rank preprocesses its own copy, counts its share of the partner groups
 (tc_count_per_vertex_part) and one sum all-reduce joins the shares
 (Sec. III-E, strong scaling); `--replicas` lets each rank count its own copy
 instead (weak scaling).
+Beside the main line: the same graph in the paper's input format (every
+edge in both directions, Sec. III-A; `paper_format`), end to end through the
+host-buffer call (`e2e`), the CPU oracle on a sample (`cpu_baseline`) and
+the 4096-graph batch (`batched`).
 `--impl reference` times the CPU oracle (the paper's own baseline is a
 single-threaded CPU forward algorithm, Sec. IV) on a bounded sample of the
 same workload, on the host cores.
@@ -62,6 +66,9 @@ def parse_args():
                    help="time the CPU oracle on the WHOLE workload (rmat24: about ten "
                         "minutes on one core) instead of the bounded sample")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-paper-format", action="store_true",
+                   help="skip timing the same graph in the paper's input format (every edge "
+                        "in both directions, 2m pairs), checked against the main run")
     p.add_argument("--total-only", action="store_true",
                    help="time tc_count (T only) instead of tc_count_per_vertex")
     p.add_argument("--no-batched", action="store_true",
@@ -415,6 +422,44 @@ def run_served(gb, want, G: int, plain_rate: float, tuning) -> dict:
 
 
 # ---------------------------------------------------------------- arms
+def run_paper_format(steps: int, tc, s, d, n: int, m: int, T: int, t_ref, deg_ref,
+                     stream) -> dict:
+    """The graph in the paper's input format (Sec. III-A): every edge listed in
+    both directions, 2m pairs.  Each key then comes twice, so the degrees
+    count every edge twice (the order stays the same) and the list sort drops
+    one copy of every edge; the counts must equal the main run's."""
+    import torch
+
+    s2 = torch.cat([s, d])
+    d2 = torch.cat([d, s])
+    t2 = torch.empty_like(t_ref)
+    deg2 = torch.empty_like(deg_ref)
+
+    def step():
+        return tc.tc_count_per_vertex(s2, d2, n, stream=stream, t_out=t2, deg_out=deg2)[0]
+
+    for _ in range(3):
+        Tp = step()
+    torch.cuda.synchronize()
+    identical = Tp == T and bool(torch.equal(t2, t_ref)) and bool(torch.equal(deg2, deg_ref))
+    assert identical, "the paper's input format changed a count"
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dt = ev0.elapsed_time(ev1) / 1e3 / steps
+    pairs = int(s2.numel())
+    del s2, d2, t2, deg2
+    torch.cuda.empty_cache()
+    return {"input": "each edge of the workload twice: the pairs, then the same pairs "
+                     "reversed", "pairs": pairs, "edges": m, "steps": steps,
+            "ms_per_step": dt * 1e3, "pairs_per_s": pairs / dt, "edges_per_s": m / dt,
+            "identical_to_main_run": identical}
+
+
 def run_reference(args, world, rank, pg):
     import graphgen
 
@@ -575,6 +620,9 @@ def run_ours(args, world, rank, local, pg):
                 "value": 4.87e5, "unit": UNIT, "seconds": 369.6, "cores": 1,
                 "source": "profiles/cpu_oracle_rmat24.md (bench.py --cpu-full on the GB300 "
                           "host, the same oracle)"}
+    paper_format = None
+    if not args.no_paper_format and world == 1:
+        paper_format = run_paper_format(args.steps, tc, s, d, n, m, T, t_out, deg_out, stream)
     batched = None
     if not args.no_batched and world == 1:
         del s, d, t_out, deg_out
@@ -597,7 +645,7 @@ def run_ours(args, world, rank, local, pg):
         "roofline": roofline(prof, args.steps, m_in, m, n, args.workload, work,
                              args.total_only),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-        "phase_ms_per_step": steps_ms, "batched": batched,
+        "phase_ms_per_step": steps_ms, "batched": batched, "paper_format": paper_format,
         "counting_work": {"lookups": work["lookups"], "inserts": work["inserts"],
                           "merge_work_W": work["merge_work"],
                           "max_out_degree": work["max_out_degree"],
