@@ -18,6 +18,9 @@ are not available, so seeded synthetic graphs of the same families stand in):
   rgg4m     random geometric graph, n=4,194,304, r=sqrt(32/(pi n))
   rmat24    R-MAT scale 24, draws until 180,000,000 distinct edges
   rmat22    R-MAT scale 22, draws until 45,000,000 distinct edges (profiling)
+  ba200k    Barabasi-Albert n=200,000, 50 edges per new vertex (9,998,725)
+  ws1m      Watts-Strogatz n=1,000,000, 25 neighbours on either side,
+            rewiring probability 0.1 (25,000,000 pairs)
   batch4096 4096 graphs, half Erdos-Renyi, half R-MAT (a,b,c = .57,.19,.19),
             n log-uniform in [2^8, 2^18], mean degree uniform in [4, 64]
             (graph_batch(4096, 1005))
@@ -81,6 +84,11 @@ def _load():
             lib.gg_rgg_point_coords.restype = None
             lib.gg_rgg_permutation.argtypes = [ctypes.c_int32, ctypes.c_uint64, i32p]
             lib.gg_rgg_permutation.restype = None
+            lib.gg_ba.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, i32p, i32p]
+            lib.gg_ba.restype = ctypes.c_int64
+            lib.gg_ws.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                  ctypes.c_uint64, i32p, i32p]
+            lib.gg_ws.restype = ctypes.c_int64
             _lib = lib
     return _lib
 
@@ -238,6 +246,31 @@ def rgg_points(n: int, seed: int):
     return x, y, perm
 
 
+def ba(n: int, k: int, seed: int):
+    """Barabasi-Albert: a clique on k + 1 vertices, then each new vertex joins
+    k distinct earlier ones drawn in proportion to their degree; permuted ids."""
+    m = k * (k + 1) // 2 + (n - k - 1) * k
+    src = np.empty(m, np.int32)
+    dst = np.empty(m, np.int32)
+    rc = _load().gg_ba(n, k, seed, _ptr(src), _ptr(dst))
+    if rc != m:
+        raise ValueError("gg_ba(n=%d, k=%d) failed: %d" % (n, k, rc))
+    return src, dst
+
+
+def ws(n: int, k: int, p: float, seed: int):
+    """Watts-Strogatz: a ring with k neighbours on either side, each edge's far
+    end moved with probability p to a vertex outside u's lattice
+    neighbourhood; permuted ids; n k pairs (rare coinciding moves repeat)."""
+    m = n * k
+    src = np.empty(m, np.int32)
+    dst = np.empty(m, np.int32)
+    rc = _load().gg_ws(n, k, p, seed, _ptr(src), _ptr(dst))
+    if rc != m:
+        raise ValueError("gg_ws(n=%d, k=%d, p=%g) failed: %d" % (n, k, p, rc))
+    return src, dst
+
+
 # name -> (description, builder)
 def _w_er16k():
     return er(16384, 131072, 1001) + (16384,)
@@ -260,6 +293,14 @@ def _w_rmat22():
     return rmat_distinct(22, 45_000_000, 1005) + (1 << 22,)
 
 
+def _w_ba200k():
+    return ba(200_000, 50, 1006) + (200_000,)
+
+
+def _w_ws1m():
+    return ws(1_000_000, 25, 0.1, 1007) + (1_000_000,)
+
+
 WORKLOADS = {
     "er16k": ("Erdos-Renyi G(n=16384, m=131072), seed 1001", _w_er16k),
     "rmat20": ("R-MAT scale 20, 16,777,216 raw draws, permuted ids, seed 1002", _w_rmat20),
@@ -267,6 +308,11 @@ WORKLOADS = {
     "rmat24": ("R-MAT scale 24, draws until 180,000,000 distinct edges, seed 1004", _w_rmat24),
     # same density as rmat24 at a quarter of the size: profiling captures
     "rmat22": ("R-MAT scale 22, draws until 45,000,000 distinct edges, seed 1005", _w_rmat22),
+    # the paper's two synthetic networks besides the Kronecker graphs, at its
+    # sizes (Table 1: 0.2M nodes / 20M directed edges; 1M nodes / 50M)
+    "ba200k": ("Barabasi-Albert n=200,000, 50 edges per new vertex, seed 1006", _w_ba200k),
+    "ws1m": ("Watts-Strogatz n=1,000,000, 25 neighbours on either side, rewiring "
+             "probability 0.1, seed 1007", _w_ws1m),
 }
 
 

@@ -31,6 +31,9 @@
  *   gg_rgg           random geometric graph in the unit square: an edge iff
  *                    the Euclidean distance is < r; ids shuffled; each edge
  *                    once, random direction, random order.
+ *   gg_ba            Barabasi-Albert preferential attachment; ids shuffled.
+ *   gg_ws            Watts-Strogatz ring lattice with rewired edges; ids
+ *                    shuffled.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -70,6 +73,10 @@ enum {
   GG_S_RGG_PERM = 5,
   GG_S_RGG_DIR = 6,
   GG_S_RGG_SHUFFLE = 7,
+  GG_S_BA = 8,
+  GG_S_BA_PERM = 9,
+  GG_S_WS = 10,
+  GG_S_WS_PERM = 11,
 };
 
 /* ------------------------------------------------------------------ */
@@ -586,4 +593,139 @@ void gg_rgg_point_coords(int32_t n, uint64_t seed, double *x, double *y) {
 /* The id permutation gg_rgg applies: point i gets vertex id perm[i]. */
 void gg_rgg_permutation(int32_t n, uint64_t seed, int32_t *perm) {
   gg_permutation(perm, n, gg_key(seed, GG_S_RGG_PERM));
+}
+
+/* ------------------------------------------------------------------ */
+/* Barabasi-Albert                                                      */
+/* ------------------------------------------------------------------ */
+/* Preferential attachment (Barabasi & Albert, Science 286, 1999): a clique
+ * on k + 1 vertices, then each further vertex v = k+1 .. n-1 joins k
+ * distinct earlier vertices, each drawn with probability proportional to its
+ * degree at that moment: a uniform draw from the list of all edge endpoints
+ * so far, drawn again if it repeats one of v's earlier picks.  The draws are
+ * one stream, consumed in order (the process is sequential).  Ids go through
+ * one seeded permutation; the pairs are listed in creation order as (new
+ * vertex, its pick).  Writes k(k+1)/2 + (n-k-1)k pairs and returns that
+ * count, or -1 (bad arguments) / -2 (allocation failure). */
+int64_t gg_ba(int32_t n, int32_t k, uint64_t seed, int32_t *src, int32_t *dst) {
+  if (k < 1 || n < k + 1) return -1;
+  const int64_t m = (int64_t)k * (k + 1) / 2 + (int64_t)(n - k - 1) * k;
+  if (2 * m >= ((int64_t)1 << 32)) return -1;
+  int32_t *ends = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * m));
+  int32_t *perm = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t *pick = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+  if (!ends || !perm || !pick) {
+    free(ends); free(perm); free(pick);
+    return -2;
+  }
+  int64_t e = 0, nends = 0;
+  for (int32_t u = 0; u <= k; ++u)
+    for (int32_t v = u + 1; v <= k; ++v) {
+      src[e] = v;
+      dst[e] = u;
+      ++e;
+      ends[nends++] = u;
+      ends[nends++] = v;
+    }
+  const uint64_t key = gg_key(seed, GG_S_BA);
+  uint64_t ctr = 0;
+  for (int32_t v = k + 1; v < n; ++v) {
+    const uint32_t bound = (uint32_t)nends;  /* endpoints before v's edges */
+    int got = 0;
+    while (got < k) {
+      const uint64_t r = gg_rand(key, ctr++);
+      int32_t w = ends[gg_below((uint32_t)r, bound)];
+      int fresh = 1;
+      for (int i = 0; i < got; ++i)
+        if (pick[i] == w) { fresh = 0; break; }
+      if (fresh) pick[got++] = w;
+      if (got < k) {  /* the high half of the word is a second draw */
+        w = ends[gg_below((uint32_t)(r >> 32), bound)];
+        fresh = 1;
+        for (int i = 0; i < got; ++i)
+          if (pick[i] == w) { fresh = 0; break; }
+        if (fresh) pick[got++] = w;
+      }
+    }
+    for (int i = 0; i < k; ++i) {
+      src[e] = v;
+      dst[e] = pick[i];
+      ++e;
+      ends[nends++] = pick[i];
+      ends[nends++] = v;
+    }
+  }
+  gg_permutation(perm, n, gg_key(seed, GG_S_BA_PERM));
+  for (int64_t i = 0; i < m; ++i) {
+    src[i] = perm[src[i]];
+    dst[i] = perm[dst[i]];
+  }
+  free(ends); free(perm); free(pick);
+  return m;
+}
+
+/* ------------------------------------------------------------------ */
+/* Watts-Strogatz                                                       */
+/* ------------------------------------------------------------------ */
+/* Small world (Watts & Strogatz, Nature 393, 1998): vertices 0 .. n-1 on a
+ * ring, each joined to its k nearest neighbours on either side (n k edges,
+ * edge (u, u+j mod n) for j = 1..k has index u k + j - 1).  With probability
+ * p (a 32-bit word below p_threshold = p 2^32) an edge's far end moves to a
+ * uniform vertex w whose ring distance to u exceeds k (so w is neither u nor
+ * one of u's lattice neighbours); up to seven candidates are drawn, and the
+ * edge stays if all seven fail.  Every decision and candidate depends only on
+ * (seed, edge index), so the loop runs in parallel.  Two moved edges may
+ * coincide (about (n k p)^2 / n^2 of them): such repeats stay in the output,
+ * as in raw R-MAT draws.  Ids go through one seeded permutation.  Writes
+ * n k pairs and returns that count, or -1 / -2. */
+typedef struct {
+  int32_t n, k;
+  uint64_t thr, key;
+  const int32_t *perm;
+  int32_t *src, *dst;
+} gg_ws_ctx;
+
+static void gg_ws_body(void *p, int64_t lo, int64_t hi, int tid) {
+  (void)tid;
+  const gg_ws_ctx *c = (const gg_ws_ctx *)p;
+  const uint32_t n = (uint32_t)c->n;
+  for (int64_t e = lo; e < hi; ++e) {
+    const uint32_t u = (uint32_t)(e / c->k);
+    const uint32_t j = (uint32_t)(e % c->k) + 1;
+    uint32_t v = (u + j) % n;
+    const uint64_t base = (uint64_t)e * 8;
+    if ((gg_rand(c->key, base) & 0xffffffffULL) < c->thr) {
+      for (uint64_t a = 1; a < 8; ++a) {
+        const uint32_t w = gg_below((uint32_t)(gg_rand(c->key, base + a) >> 32), n);
+        const uint32_t d = w >= u ? w - u : w + n - u;
+        const uint32_t ring = d < n - d ? d : n - d;
+        if (ring > (uint32_t)c->k) {
+          v = w;
+          break;
+        }
+      }
+    }
+    c->src[e] = c->perm[u];
+    c->dst[e] = c->perm[v];
+  }
+}
+
+int64_t gg_ws(int32_t n, int32_t k, double p, uint64_t seed, int32_t *src, int32_t *dst) {
+  if (k < 1 || n < 2 * k + 2 || !(p >= 0.0 && p <= 1.0)) return -1;
+  const int64_t m = (int64_t)n * k;
+  if (m > (int64_t)0x7fffffff) return -1;
+  int32_t *perm = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  if (!perm) return -2;
+  gg_permutation(perm, n, gg_key(seed, GG_S_WS_PERM));
+  gg_ws_ctx c;
+  c.n = n;
+  c.k = k;
+  c.thr = (uint64_t)(p * 4294967296.0);
+  c.key = gg_key(seed, GG_S_WS);
+  c.perm = perm;
+  c.src = src;
+  c.dst = dst;
+  gg_parallel(m, gg_nthreads(), gg_ws_body, &c);
+  free(perm);
+  return m;
 }

@@ -267,6 +267,19 @@ def test_wide_id_ranges(tc, n):
     assert r["T"] == oracle.forward(s, d, 1 << 17, per_vertex=False)["T"]
 
 
+@pytest.mark.parametrize("n,k", [(1000, 5), (300_001, 25)])
+def test_ring_lattice_closed_form(tc, n, k):
+    """The Watts-Strogatz lattice before rewiring: n C(k, 2) triangles, 3 C(k, 2)
+    at every vertex, every degree 2k (all degrees equal: the order is the
+    permuted ids alone)."""
+    import graphgen
+
+    s, d = graphgen.ws(n, k, 0.0, 12)
+    T, t, deg = run_pv(tc, s, d, n)
+    assert T == n * math.comb(k, 2) == tc.tc_count(dev(s), dev(d), n)
+    assert np.all(t == 3 * math.comb(k, 2)) and np.all(deg == 2 * k)
+
+
 def test_clustering_and_transitivity(tc):
     import graphgen
 
@@ -390,7 +403,7 @@ def test_er16k_full(tc):
     assert r["T"] == g["T"]
 
 
-@pytest.mark.parametrize("name", ["rmat20", "rgg4m", "rmat24"])
+@pytest.mark.parametrize("name", ["rmat20", "rgg4m", "rmat24", "ba200k", "ws1m"])
 def test_workload_full(tc, name):
     """Full-size workloads against the oracle's stored results: T, the SHA-256
     of all per-vertex counts and degrees, sampled t(v), sum t = 3T."""

@@ -81,7 +81,7 @@ def test_thread_count_independent(threads):
     code = ("import hashlib, graphgen as g\n"
             "h = hashlib.sha256()\n"
             "for a in (g.rmat(14, 300000, 5), g.rmat_distinct(14, 100000, 6), "
-            "g.rgg(20000, g.rgg_radius(20000), 7)):\n"
+            "g.rgg(20000, g.rgg_radius(20000), 7), g.ws(20000, 5, 0.3, 8)):\n"
             "    h.update(a[0].tobytes()); h.update(a[1].tobytes())\n"
             "print(h.hexdigest())\n")
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -92,7 +92,7 @@ def test_thread_count_independent(threads):
     assert outs[0] == outs[1]
 
 
-@pytest.mark.parametrize("name", ["er16k", "rmat20", "rgg4m"])
+@pytest.mark.parametrize("name", ["er16k", "rmat20", "rgg4m", "ba200k", "ws1m"])
 def test_workload_hash_matches_golden(name):
     """The stored input hashes pin the generator across hosts."""
     with open(GOLDEN) as f:
@@ -133,3 +133,63 @@ def test_batch_params_ranges():
     d = 2 * m / n
     assert d.min() >= 3.9 and d.max() <= 64.0
     assert kinds.count("er") == kinds.count("rmat") == 2048
+
+
+# ------------------------------------------------------------ Barabasi-Albert
+def test_ba_structure():
+    n, k = 3000, 7
+    s, d = graphgen.ba(n, k, 21)
+    assert len(s) == k * (k + 1) // 2 + (n - k - 1) * k
+    assert np.all(s != d)
+    assert len(np.unique(_canon(s, d))) == len(s)  # picks of a vertex are distinct
+    assert s.min() >= 0 and max(s.max(), d.max()) < n
+    deg = np.bincount(np.concatenate([s, d]), minlength=n)
+    assert deg.min() >= k
+    # preferential attachment: a few early vertices collect far more than k
+    assert deg.max() > 6 * k
+    s2, d2 = graphgen.ba(n, k, 21)
+    assert np.array_equal(s, s2) and np.array_equal(d, d2)
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 12])
+def test_ba_first_vertices_closed_form(k):
+    """n = k + 1 is the seed clique; one more vertex joins k of its k + 1
+    vertices and closes C(k, 2) more triangles."""
+    import oracle
+
+    s, d = graphgen.ba(k + 1, k, 3)
+    assert oracle.forward(s, d, k + 1, per_vertex=False)["T"] == math.comb(k + 1, 3)
+    s, d = graphgen.ba(k + 2, k, 3)
+    assert oracle.forward(s, d, k + 2, per_vertex=False)["T"] == math.comb(k + 1, 3) + math.comb(k, 2)
+
+
+# ------------------------------------------------------------ Watts-Strogatz
+@pytest.mark.parametrize("n,k", [(16, 5), (1000, 5), (4001, 13)])
+def test_ws_lattice_closed_form(n, k):
+    """p = 0 leaves the ring lattice: with n >= 3k + 1 each triangle lies
+    within k + 1 consecutive vertices, n C(k, 2) of them, 3 C(k, 2) at each
+    vertex, every degree 2k."""
+    import oracle
+
+    s, d = graphgen.ws(n, k, 0.0, 5)
+    assert len(s) == n * k and len(np.unique(_canon(s, d))) == n * k
+    r = oracle.forward(s, d, n)
+    assert r["T"] == n * math.comb(k, 2)
+    assert np.all(r["t"] == 3 * math.comb(k, 2)) and np.all(r["deg"] == 2 * k)
+
+
+def test_ws_rewiring():
+    import oracle
+
+    n, k = 20000, 10
+    s, d = graphgen.ws(n, k, 0.1, 6)
+    assert len(s) == n * k and np.all(s != d)
+    r = oracle.forward(s, d, n)
+    # clustering of the lattice, 3(k-1) / (2(2k-1)), thinned by (1-p)^3
+    want = 3 * (k - 1) / (2 * (2 * k - 1)) * 0.9 ** 3
+    assert abs(oracle.transitivity(r["T"], r["deg"]) - want) < 0.02
+    # every edge moved: a sparse random graph keeps few triangles
+    s, d = graphgen.ws(n, k, 1.0, 6)
+    assert oracle.forward(s, d, n, per_vertex=False)["T"] < 3000
+    with pytest.raises(ValueError):
+        graphgen.ws(2 * k + 1, k, 0.1, 6)
