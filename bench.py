@@ -22,8 +22,9 @@ every rank preprocesses its own copy, counts its share of the partner groups
 instead (weak scaling).
 Beside the main line: the same graph in the paper's input format (every
 edge in both directions, Sec. III-A; `paper_format`), end to end through the
-host-buffer call (`e2e`), the CPU oracle on a sample (`cpu_baseline`) and
-the 4096-graph batch (`batched`).
+host-buffer call (`e2e`), the CPU oracle on a sample (`cpu_baseline`),
+stand-ins of the paper's synthetic Table 1 graphs timed as the paper times
+them (`paper_table1`) and the 4096-graph batch (`batched`).
 `--impl reference` times the CPU oracle (the paper's own baseline is a
 single-threaded CPU forward algorithm, Sec. IV) on a bounded sample of the
 same workload, on the host cores.
@@ -66,6 +67,9 @@ def parse_args():
                    help="time the CPU oracle on the WHOLE workload (rmat24: about ten "
                         "minutes on one core) instead of the bounded sample")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-paper-table", action="store_true",
+                   help="skip the stand-ins of the paper's synthetic Table 1 graphs (T only, "
+                        "host to host, the paper's timing protocol)")
     p.add_argument("--no-paper-format", action="store_true",
                    help="skip timing the same graph in the paper's input format (every edge "
                         "in both directions, 2m pairs), checked against the main run")
@@ -422,6 +426,89 @@ def run_served(gb, want, G: int, plain_rate: float, tuning) -> dict:
 
 
 # ---------------------------------------------------------------- arms
+# The synthetic rows of the paper's Table 1: row, input, the row's edge
+# entries (every edge listed twice), triangles, CPU ms and GTX 980 ms.  The
+# inputs are stand-ins of the same family and size: R-MAT with the Graph500
+# parameters drawn until half the row's edge entries are distinct edges
+# (the row's Kronecker graphs are not available), and the Barabasi-Albert
+# and Watts-Strogatz generators at the rows' sizes.
+PAPER_TABLE1 = [
+    ("Kronecker 16", ("rmat", 16), 5e6, 119e6, 2810, 82),
+    ("Kronecker 17", ("rmat", 17), 10e6, 288e6, 6957, 219),
+    ("Kronecker 18", ("rmat", 18), 21e6, 688e6, 17808, 558),
+    ("Kronecker 19", ("rmat", 19), 44e6, 1626e6, 45947, 1443),
+    ("Kronecker 20", ("rmat", 20), 89e6, 3804e6, 116811, 3942),
+    ("Kronecker 21", ("rmat", 21), 182e6, 8816e6, 297426, 12009),
+    ("Barabasi-Albert", ("ba200k",), 20e6, 3e6, 5508, 155),
+    ("Watts-Strogatz", ("ws1m",), 50e6, 219e6, 9627, 324),
+]
+
+
+def paper_table_input(spec, edges):
+    import graphgen
+
+    if spec[0] == "rmat":
+        scale = spec[1]
+        src, dst = graphgen.rmat_distinct(scale, int(edges // 2), 1100 + scale)
+        return src, dst, 1 << scale
+    return graphgen.workload(spec[0])
+
+
+def run_paper_table(tc, rows=PAPER_TABLE1, repeats: int = 5) -> list:
+    """T only, as the paper counts, on stand-ins of its synthetic graphs.  Its
+    protocol (Sec. IV): wall clock from the inputs in host memory to the
+    total back on the host, after a warm-up, mean of five runs; here through
+    tc_count_host with page-locked buffers.  The device-resident time (CUDA
+    events, tc_count) is given beside it.  Context only: other graphs of the
+    same families and sizes, other hardware."""
+    import torch
+
+    out = []
+    stream = torch.cuda.current_stream()
+    for name, spec, edges, tri, cpu_ms, gtx_ms in rows:
+        src, dst, n = paper_table_input(spec, edges)
+        hs = torch.from_numpy(src).pin_memory()
+        hd = torch.from_numpy(dst).pin_memory()
+        T = tc.tc_count_host(hs, hd, n)  # warm-up
+        wall = []
+        for _ in range(repeats):
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            Th = tc.tc_count_host(hs, hd, n)
+            wall.append(time.perf_counter() - a)
+            assert Th == T
+        ds, dd = hs.cuda(), hd.cuda()
+        assert tc.tc_count(ds, dd, n, stream=stream) == T
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(repeats):
+            tc.tc_count(ds, dd, n, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_dev = ev0.elapsed_time(ev1) / repeats
+        ms = statistics.mean(wall) * 1e3
+        out.append({"graph": name, "input": graphgen_name(spec, edges), "n": int(n),
+                    "pairs": int(len(src)), "triangles": int(T),
+                    "ms_host_to_host": round(ms, 3),
+                    "ms_host_to_host_std": round(statistics.pstdev(wall) * 1e3, 3),
+                    "ms_device_resident": round(ms_dev, 3),
+                    "paper": {"edge_entries": edges, "triangles": tri, "cpu_ms": cpu_ms,
+                              "gtx980_ms": gtx_ms}})
+        del hs, hd, ds, dd
+        torch.cuda.empty_cache()
+    return out
+
+
+def graphgen_name(spec, edges) -> str:
+    if spec[0] == "rmat":
+        return ("R-MAT scale %d (a,b,c = .57,.19,.19), draws until %d distinct edges, seed %d"
+                % (spec[1], int(edges // 2), 1100 + spec[1]))
+    import graphgen
+
+    return graphgen.WORKLOADS[spec[0]][0]
+
+
 def run_paper_format(steps: int, tc, s, d, n: int, m: int, T: int, t_ref, deg_ref,
                      stream) -> dict:
     """The graph in the paper's input format (Sec. III-A): every edge listed in
@@ -623,6 +710,9 @@ def run_ours(args, world, rank, local, pg):
     paper_format = None
     if not args.no_paper_format and world == 1:
         paper_format = run_paper_format(args.steps, tc, s, d, n, m, T, t_out, deg_out, stream)
+    paper_table = None
+    if not args.no_paper_table and world == 1:
+        paper_table = run_paper_table(tc)
     batched = None
     if not args.no_batched and world == 1:
         del s, d, t_out, deg_out
@@ -646,6 +736,7 @@ def run_ours(args, world, rank, local, pg):
                              args.total_only),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "phase_ms_per_step": steps_ms, "batched": batched, "paper_format": paper_format,
+        "paper_table1": paper_table,
         "counting_work": {"lookups": work["lookups"], "inserts": work["inserts"],
                           "merge_work_W": work["merge_work"],
                           "max_out_degree": work["max_out_degree"],
