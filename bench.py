@@ -306,10 +306,13 @@ def stored_batch_totals(count: int):
     return np.array(gold["T"], np.uint64)
 
 
-def run_batched(args, tc) -> dict:
+def run_batched(args, tc, rank: int = 0, world: int = 1, pg=None, dev=None) -> dict:
     """Graphs/s of the persistent CUDA-graph batch engines (autotuned) against
     the per-graph launch loop, on the same device-resident graphs; the
-    per-graph counts must be identical."""
+    per-graph counts must be identical.  With several ranks each one counts
+    the graphs dealt to it (batching.deal_graphs, by size), whole and alone:
+    no collective; every rank checks its own totals, and the times are the
+    maximum over the ranks."""
     import numpy as np
     import torch
 
@@ -317,7 +320,15 @@ def run_batched(args, tc) -> dict:
     from paper_1503_00576_gb300 import autotune, batching
 
     t0 = time.time()
-    gb = graphgen.graph_batch(args.batch_graphs, 1005)
+    G_all = args.batch_graphs
+    mine = None
+    if world > 1:
+        _, m_all, _, _ = graphgen.batch_params(G_all, 1005)
+        mine = batching.deal_graphs(np.concatenate([[0], np.cumsum(m_all)]), world)[rank]
+        gb = graphgen.graph_batch(G_all, 1005, only=mine,
+                                  threads=max(1, (os.cpu_count() or 4) // world))
+    else:
+        gb = graphgen.graph_batch(G_all, 1005)
     gen_s = time.time() - t0
     G = len(gb)
     m_total = int(gb.edge_offsets[-1])
@@ -330,10 +341,11 @@ def run_batched(args, tc) -> dict:
     # per-graph launch loop (one warm pass over a prefix first)
     batching.count_plain(s, d, eo[:65], vn[:64])
     torch.cuda.synchronize()
+    barrier(pg, dev)
     t0 = time.perf_counter()
     plain = batching.count_plain(s, d, eo, vn)
     torch.cuda.synchronize()
-    plain_s = time.perf_counter() - t0
+    plain_s = max_over_ranks(pg, time.perf_counter() - t0, dev)
 
     t0 = time.time()
     tuned = autotune.tune_batches(s, d, eo, vn, cap)
@@ -343,26 +355,43 @@ def run_batched(args, tc) -> dict:
         times = []
         for _ in range(2):
             torch.cuda.synchronize()
+            barrier(pg, dev)
             t0 = time.perf_counter()
             got = bc.count(s, d, eo, vn)
             torch.cuda.synchronize()
-            times.append(time.perf_counter() - t0)
+            times.append(max_over_ranks(pg, time.perf_counter() - t0, dev))
             assert np.array_equal(got, ref)
     batched_s = min(times)
     exact = bool(np.array_equal(ref, plain))
     oracle_identical = None
-    gold = stored_batch_totals(args.batch_graphs)
+    gold = stored_batch_totals(G_all)
     if gold is not None:
+        if mine is not None:
+            gold = gold[mine]
         oracle_identical = bool(np.array_equal(ref, gold) and np.array_equal(plain, gold))
+    if world > 1:  # every rank's verdict, and the whole batch's triangles
+        flags = torch.tensor([int(exact), int(bool(oracle_identical)), int(ref.sum())],
+                             dtype=torch.int64, device="cuda" if dev is not None else "cpu")
+        parts = [torch.zeros_like(flags) for _ in range(world)]
+        pg.all_gather(parts, flags)
+        exact = all(int(p[0]) for p in parts)
+        if gold is not None:
+            oracle_identical = all(int(p[1]) for p in parts)
+        tri = sum(int(p[2]) for p in parts)
+    else:
+        tri = int(ref.sum())
     plan = batching.plan_subbatches(eo, vn, cap)
     del s, d
     served = None
-    if args.serve_graphs > 0:
+    if args.serve_graphs > 0 and world == 1:
         torch.cuda.empty_cache()
         served = run_served(gb, ref, min(args.serve_graphs, G), G / plain_s, tuned["tuning"])
-    return {"graphs": G, "pairs": m_total, "triangles": int(ref.sum()),
-            "graphs_per_s": G / batched_s, "edges_per_s": m_total / batched_s,
-            "plain_graphs_per_s": G / plain_s, "plain_edges_per_s": m_total / plain_s,
+    if world > 1:
+        m_total = int(graphgen.batch_params(G_all, 1005)[1].sum())
+    return {"graphs": G_all, "pairs": m_total, "triangles": tri,
+            "graphs_per_s": G_all / batched_s, "edges_per_s": m_total / batched_s,
+            "plain_graphs_per_s": G_all / plain_s, "plain_edges_per_s": m_total / plain_s,
+            "ranks": world, "graphs_per_rank": G if world == 1 else "dealt by size",
             "speedup_vs_plain": plain_s / batched_s, "counts_identical": exact,
             "oracle_identical": oracle_identical,
             "oracle_totals": "tests/golden/batch4096.json (CPU oracle, one graph per core)"
@@ -681,6 +710,10 @@ def run_ours(args, world, rank, local, pg):
                "api": ("tc_count_host" if args.total_only else "tc_count_per_vertex_host")
                       + " (pinned host buffers)"}
 
+    # the 4096-graph batch: every rank counts the graphs dealt to it
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(args, tc, rank, world, pg, dev)
     if rank != 0:
         return
     cpu = None
@@ -713,11 +746,6 @@ def run_ours(args, world, rank, local, pg):
     paper_table = None
     if not args.no_paper_table and world == 1:
         paper_table = run_paper_table(tc)
-    batched = None
-    if not args.no_batched and world == 1:
-        del s, d, t_out, deg_out
-        torch.cuda.empty_cache()
-        batched = run_batched(args, tc)
     steps_ms = {k: round(v[0] / args.steps, 4) for k, v in prof.items()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

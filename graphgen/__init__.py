@@ -184,19 +184,22 @@ def batch_graph(count: int, seed: int, g: int, log2_n=(8, 18), degree=(4.0, 64.0
 
 
 def graph_batch(count: int, seed: int, log2_n=(8, 18), degree=(4.0, 64.0),
-                threads: int = 0) -> GraphBatch:
-    """Generate a batch of `count` graphs (in parallel; deterministic)."""
+                threads: int = 0, only=None) -> GraphBatch:
+    """Generate a batch of `count` graphs (in parallel; deterministic).  With
+    `only` (graph indices), just those graphs of the batch, in that order."""
     import concurrent.futures as cf
 
     n, m, kinds, seeds = batch_params(count, seed, log2_n, degree)
-    eo = np.zeros(count + 1, np.int64)
-    eo[1:] = np.cumsum(m)
+    idx = np.arange(count) if only is None else np.asarray(only, np.int64)
+    eo = np.zeros(len(idx) + 1, np.int64)
+    eo[1:] = np.cumsum(m[idx])
     src = np.empty(int(eo[-1]), np.int32)
     dst = np.empty(int(eo[-1]), np.int32)
     lib = _load()
 
-    def one(g):
-        a, b = int(eo[g]), int(eo[g + 1])
+    def one(j):
+        g = int(idx[j])
+        a, b = int(eo[j]), int(eo[j + 1])
         ps = src[a:b].ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         pd = dst[a:b].ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         if kinds[g] == "er":
@@ -209,8 +212,8 @@ def graph_batch(count: int, seed: int, log2_n=(8, 18), degree=(4.0, 64.0),
 
     workers = threads or (os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
-        list(ex.map(one, range(count)))
-    return GraphBatch(src, dst, eo, n, kinds, seeds)
+        list(ex.map(one, range(len(idx))))
+    return GraphBatch(src, dst, eo, n[idx], [kinds[g] for g in idx], [seeds[g] for g in idx])
 
 
 def rgg_radius(n: int, mean_degree: float = 32.0) -> float:

@@ -10,6 +10,7 @@ dispatches.
 """
 from __future__ import annotations
 
+import heapq
 from dataclasses import dataclass
 
 import numpy as np
@@ -47,6 +48,48 @@ def plan_subbatches(edge_offsets, vertex_counts, cap: Capacity):
         out.append((g, hi, True))
         g = hi
     return out
+
+
+def deal_graphs(edge_offsets, parts: int):
+    """Graphs of a batch dealt to `parts` devices: largest first, each to the
+    part with the fewest pairs so far (ties: the lower part).  Every graph is
+    counted whole on one device, so the parts need no collective; the
+    largest graph bounds how even they can be.  Returns one ascending index
+    array per part."""
+    if parts < 1:
+        raise ValueError("parts must be >= 1")
+    m = np.diff(np.asarray(edge_offsets, np.int64))
+    heap = [(0, p) for p in range(parts)]
+    out = [[] for _ in range(parts)]
+    for g in np.argsort(-m, kind="stable"):
+        load, p = heapq.heappop(heap)
+        out[p].append(int(g))
+        heapq.heappush(heap, (load + int(m[g]), p))
+    return [np.array(sorted(x), np.int64) for x in out]
+
+
+def gather_graphs(src, dst, edge_offsets, vertex_counts, idx):
+    """The graphs `idx` of a batch, back to back: (src, dst, edge_offsets,
+    vertex_counts) of the smaller batch.  src/dst may be numpy arrays or
+    torch tensors (on any device); the pairs are copied, not renumbered
+    (ids are local to each graph)."""
+    eo = np.asarray(edge_offsets, np.int64)
+    vn = np.asarray(vertex_counts, np.int32)
+    idx = np.asarray(idx, np.int64)
+    spans = [(int(eo[g]), int(eo[g + 1])) for g in idx]
+    sub_eo = np.zeros(len(idx) + 1, np.int64)
+    sub_eo[1:] = np.cumsum([b - a for a, b in spans])
+    if isinstance(src, np.ndarray):
+        cat = np.concatenate
+        empty = src[:0]
+    else:
+        import torch
+
+        cat = torch.cat
+        empty = src[:0]
+    s = cat([src[a:b] for a, b in spans]) if spans else empty
+    d = cat([dst[a:b] for a, b in spans]) if spans else dst[:0]
+    return s, d, sub_eo, vn[idx]
 
 
 class BatchCounter:

@@ -193,3 +193,15 @@ def test_ws_rewiring():
     assert oracle.forward(s, d, n, per_vertex=False)["T"] < 3000
     with pytest.raises(ValueError):
         graphgen.ws(2 * k + 1, k, 0.1, 6)
+
+
+def test_graph_batch_subset_equals_the_whole():
+    full = graphgen.graph_batch(64, 77, log2_n=(6, 12))
+    pick = [5, 0, 63, 17]
+    sub = graphgen.graph_batch(64, 77, log2_n=(6, 12), only=pick)
+    assert len(sub) == len(pick)
+    for j, g in enumerate(pick):
+        a, b, n = sub.graph(j)
+        x, y, m = full.graph(g)
+        assert n == m and np.array_equal(a, x) and np.array_equal(b, y)
+        assert sub.kinds[j] == full.kinds[g] and sub.seeds[j] == full.seeds[g]
