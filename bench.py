@@ -115,6 +115,20 @@ def barrier(pg, dev=None):
             pg.barrier()
 
 
+def gather_over_ranks(pg, values, dev=None) -> list:
+    """Every rank's list of integers (same length on all ranks), on every
+    rank; [values] alone without a process group."""
+    if pg is None:
+        return [list(values)]
+    import torch
+
+    t = torch.tensor([int(v) for v in values], dtype=torch.int64,
+                     device="cuda" if dev is not None else "cpu")
+    parts = [torch.zeros_like(t) for _ in range(pg.get_world_size())]
+    pg.all_gather(parts, t)
+    return [[int(x) for x in p.tolist()] for p in parts]
+
+
 def max_over_ranks(pg, x: float, dev=None) -> float:
     if pg is None:
         return x
@@ -369,17 +383,12 @@ def run_batched(args, tc, rank: int = 0, world: int = 1, pg=None, dev=None) -> d
         if mine is not None:
             gold = gold[mine]
         oracle_identical = bool(np.array_equal(ref, gold) and np.array_equal(plain, gold))
-    if world > 1:  # every rank's verdict, and the whole batch's triangles
-        flags = torch.tensor([int(exact), int(bool(oracle_identical)), int(ref.sum())],
-                             dtype=torch.int64, device="cuda" if dev is not None else "cpu")
-        parts = [torch.zeros_like(flags) for _ in range(world)]
-        pg.all_gather(parts, flags)
-        exact = all(int(p[0]) for p in parts)
-        if gold is not None:
-            oracle_identical = all(int(p[1]) for p in parts)
-        tri = sum(int(p[2]) for p in parts)
-    else:
-        tri = int(ref.sum())
+    # every rank's verdict, and the whole batch's triangles
+    parts = gather_over_ranks(pg, [exact, bool(oracle_identical), int(ref.sum())], dev)
+    exact = all(p[0] for p in parts)
+    if gold is not None:
+        oracle_identical = all(p[1] for p in parts)
+    tri = sum(p[2] for p in parts)
     plan = batching.plan_subbatches(eo, vn, cap)
     del s, d
     served = None

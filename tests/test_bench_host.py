@@ -86,3 +86,12 @@ def test_reference_arm_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["sample_pairs_per_step"] == d["config"]["m_in"] == 131072
+
+
+def test_gather_over_ranks_alone():
+    import bench
+
+    assert bench.gather_over_ranks(None, [True, False, 7]) == [[True, False, 7]]
+    parts = bench.gather_over_ranks(None, [True, bool(None), 12])
+    assert all(p[0] for p in parts) and not all(p[1] for p in parts)
+    assert sum(p[2] for p in parts) == 12

@@ -70,3 +70,44 @@ def test_two_gloo_ranks_sum_their_shares(per_vertex):
     mp = pytest.importorskip("torch.multiprocessing")
     mp.start_processes(_worker, args=(_free_port(), per_vertex), nprocs=WORLD, join=True,
                        start_method="spawn")
+
+
+def _batch_worker(rank: int, port: int):
+    """Two ranks deal a batch by size, each generates and counts only its
+    graphs (the oracle stands in for the GPU engines) and the verdicts and
+    triangle sums are joined as bench.py joins them."""
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import bench
+    import graphgen
+    import oracle
+    from paper_1503_00576_gb300.batching import deal_graphs
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=WORLD)
+    try:
+        G, seed, sizes = 48, 91, (5, 10)
+        _, m, _, _ = graphgen.batch_params(G, seed, log2_n=sizes)
+        shares = deal_graphs(np.concatenate([[0], np.cumsum(m)]), WORLD)
+        mine = shares[rank]
+        gb = graphgen.graph_batch(G, seed, log2_n=sizes, only=mine, threads=2)
+        got = [oracle.forward(*gb.graph(j), per_vertex=False)["T"] for j in range(len(gb))]
+        full = graphgen.graph_batch(G, seed, log2_n=sizes, threads=2)
+        want = [oracle.forward(*full.graph(g), per_vertex=False)["T"] for g in range(G)]
+        ok = got == [want[g] for g in mine]
+        parts = bench.gather_over_ranks(dist, [ok, sum(got), len(mine)])
+        assert [p[0] for p in parts] == [1, 1]
+        assert sum(p[1] for p in parts) == sum(want)
+        assert sum(p[2] for p in parts) == G
+        assert parts[rank] == [1, sum(got), len(mine)]
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_count_their_graphs():
+    mp = pytest.importorskip("torch.multiprocessing")
+    mp.start_processes(_batch_worker, args=(_free_port(),), nprocs=WORLD, join=True,
+                       start_method="spawn")
