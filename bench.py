@@ -115,6 +115,15 @@ def barrier(pg, dev=None):
             pg.barrier()
 
 
+def step_stats(ms: list) -> dict:
+    """Mean, standard deviation, median and range of per-step times (this
+    rank's), as the paper reports its repeats (Sec. IV: mean of five runs,
+    deviation within 5%)."""
+    return {"mean": round(statistics.mean(ms), 4), "std": round(statistics.pstdev(ms), 4),
+            "median": round(statistics.median(ms), 4), "min": round(min(ms), 4),
+            "max": round(max(ms), 4), "steps": len(ms)}
+
+
 def gather_over_ranks(pg, values, dev=None) -> list:
     """Every rank's list of integers (same length on all ranks), on every
     rank; [values] alone without a process group."""
@@ -671,12 +680,11 @@ def run_ours(args, world, rank, local, pg):
     time.sleep(0.4)  # let the sampler take a first reading
     barrier(pg, dev)
     torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record(stream)
+    for i in range(args.steps):
         T2 = step()
-    ev1.record(stream)
+        evs[i + 1].record(stream)
     torch.cuda.synchronize()
     barrier(pg, dev)
     clk = clocks.stop()
@@ -684,8 +692,9 @@ def run_ours(args, world, rank, local, pg):
     tc.tc_profile_enable(False)
     prof = tc.tc_profile_read(reset=True)
     assert T2 == T, "count changed between steps"
-    elapsed = ev0.elapsed_time(ev1) / 1e3
+    elapsed = evs[0].elapsed_time(evs[-1]) / 1e3
     elapsed = max_over_ranks(pg, elapsed, dev)
+    step_ms = step_stats([evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)])
     ms_per_step = elapsed / args.steps * 1e3
     # replicas: every rank counted its own copy; shards: all ranks one graph
     value = (1 if sharded else world) * m_in * args.steps / elapsed
@@ -772,7 +781,8 @@ def run_ours(args, world, rank, local, pg):
         "roofline": roofline(prof, args.steps, m_in, m, n, args.workload, work,
                              args.total_only),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-        "phase_ms_per_step": steps_ms, "batched": batched, "paper_format": paper_format,
+        "step_ms": step_ms, "phase_ms_per_step": steps_ms, "batched": batched,
+        "paper_format": paper_format,
         "paper_table1": paper_table,
         "counting_work": {"lookups": work["lookups"], "inserts": work["inserts"],
                           "merge_work_W": work["merge_work"],

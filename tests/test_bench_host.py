@@ -95,3 +95,13 @@ def test_gather_over_ranks_alone():
     parts = bench.gather_over_ranks(None, [True, bool(None), 12])
     assert all(p[0] for p in parts) and not all(p[1] for p in parts)
     assert sum(p[2] for p in parts) == 12
+
+
+def test_step_stats():
+    import bench
+
+    st = bench.step_stats([40.0, 42.0, 44.0, 42.0])
+    assert st["mean"] == 42.0 and st["median"] == 42.0
+    assert st["min"] == 40.0 and st["max"] == 44.0 and st["steps"] == 4
+    assert abs(st["std"] - 2 ** 0.5) < 1e-4
+    assert bench.step_stats([5.0])["std"] == 0.0
