@@ -3,9 +3,12 @@ library accepts (tc_set_tuning checks the ranges without a device), and the
 workload key is coarse (graphs, log2 of the median edges and of the mean
 degree) and independent of the order of the graphs."""
 import numpy as np
+import pytest
 
 import paper_1503_00576_gb300 as tc
 from paper_1503_00576_gb300 import autotune
+
+pytestmark = pytest.mark.usefixtures("libtc")
 
 
 def test_candidates_are_valid_tunings():
