@@ -334,8 +334,9 @@ def run_batched(args, tc, rank: int = 0, world: int = 1, pg=None, dev=None) -> d
     the per-graph launch loop, on the same device-resident graphs; the
     per-graph counts must be identical.  With several ranks each one counts
     the graphs dealt to it (batching.deal_graphs, by size), whole and alone:
-    no collective; every rank checks its own totals, and the times are the
-    maximum over the ranks."""
+    no collective on the data path; every rank checks its own totals, one
+    all-gather joins the verdicts, and the times are the maximum over the
+    ranks."""
     import numpy as np
     import torch
 
