@@ -105,3 +105,133 @@ def test_step_stats():
     assert st["min"] == 40.0 and st["max"] == 44.0 and st["steps"] == 4
     assert abs(st["std"] - 2 ** 0.5) < 1e-4
     assert bench.step_stats([5.0])["std"] == 0.0
+
+
+def test_run_batched_plumbing(monkeypatch):
+    """run_batched's host logic with the device work faked (counts = pairs
+    per graph): one rank, and two ranks of which this process is rank 0,
+    through a stand-in process group whose collectives see both ranks as
+    this one."""
+    import types
+
+    import numpy as np
+    import torch
+
+    import bench
+    from paper_1503_00576_gb300 import autotune, batching
+
+    def fake_count(s, d, eo, vn):
+        return np.diff(np.asarray(eo, np.int64)).astype(np.uint64)
+
+    class FakeCounter:
+        def __init__(self, cap, tuning=None):
+            pass
+
+        def __enter__(self):
+            return self
+
+        def __exit__(self, *exc):
+            return False
+
+        def count(self, s, d, eo, vn):
+            return fake_count(s, d, eo, vn)
+
+    monkeypatch.setattr(torch.Tensor, "cuda", lambda self, *a, **k: self)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    monkeypatch.setattr(batching, "count_plain", fake_count)
+    monkeypatch.setattr(batching, "BatchCounter", FakeCounter)
+    monkeypatch.setattr(autotune, "tune_batches",
+                        lambda *a, **k: {"tuning": {"t": 1}, "cached": False, "ms": {}})
+    args = types.SimpleNamespace(batch_graphs=24, serve_graphs=0)
+    r = bench.run_batched(args, None)
+    import graphgen
+
+    m = graphgen.batch_params(24, 1005)[1]
+    assert r["graphs"] == 24 and r["pairs"] == int(m.sum()) and r["triangles"] == int(m.sum())
+    assert r["counts_identical"] is True and r["oracle_identical"] is None
+    assert r["ranks"] == 1 and r["graphs_per_rank"] == 24 and r["served"] is None
+
+    def all_gather(parts, t):
+        for p in parts:
+            p.copy_(t)
+
+    pg = types.SimpleNamespace(get_world_size=lambda: 2, all_gather=all_gather,
+                               all_reduce=lambda t, op=None: None, barrier=lambda **k: None,
+                               ReduceOp=types.SimpleNamespace(MAX="max"))
+    r2 = bench.run_batched(args, None, rank=0, world=2, pg=pg, dev=None)
+    mine = batching.deal_graphs(np.concatenate([[0], np.cumsum(m)]), 2)[0]
+    assert r2["ranks"] == 2 and r2["graphs"] == 24 and r2["pairs"] == int(m.sum())
+    assert r2["triangles"] == 2 * int(m[mine].sum())  # both stand-in ranks are this one
+    assert r2["counts_identical"] is True
+
+
+class _FakeEvent:
+    def __init__(self, enable_timing=False):
+        pass
+
+    def record(self, stream=None):
+        pass
+
+    def elapsed_time(self, other):
+        return 2.0
+
+
+def _fake_cuda(monkeypatch):
+    import types
+
+    import torch
+
+    monkeypatch.setattr(torch.Tensor, "cuda", lambda self, *a, **k: self)
+    monkeypatch.setattr(torch.Tensor, "pin_memory", lambda self, *a, **k: self)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "Event", _FakeEvent)
+    monkeypatch.setattr(torch.cuda, "current_stream", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "empty_cache", lambda: None)
+    return types
+
+
+def test_run_paper_table_plumbing(monkeypatch):
+    import bench
+
+    types = _fake_cuda(monkeypatch)
+    tc = types.SimpleNamespace(tc_count_host=lambda s, d, n: 11,
+                               tc_count=lambda s, d, n, stream=None: 11)
+    rows = [r for r in bench.PAPER_TABLE1 if r[0] in ("Kronecker 16", "Watts-Strogatz")]
+    out = bench.run_paper_table(tc, rows, repeats=3)
+    assert [r["graph"] for r in out] == ["Kronecker 16", "Watts-Strogatz"]
+    k16, ws = out
+    assert k16["n"] == 1 << 16 and k16["pairs"] == 2_500_000 and k16["triangles"] == 11
+    assert k16["ms_device_resident"] == round(2.0 / 3, 3)
+    assert k16["paper"] == {"edge_entries": 5e6, "triangles": 119e6, "cpu_ms": 2810,
+                            "gtx980_ms": 82}
+    assert ws["n"] == 1_000_000 and ws["pairs"] == 25_000_000
+    assert "seed 1116" in k16["input"] and "Watts-Strogatz" in ws["input"]
+
+
+def test_run_paper_format_plumbing(monkeypatch):
+    import numpy as np
+    import torch
+
+    import bench
+
+    types = _fake_cuda(monkeypatch)
+    n = 5
+    t_ref = torch.arange(n, dtype=torch.int64)
+    deg_ref = torch.arange(n, dtype=torch.int32) + 1
+    seen = []
+
+    def per_vertex(s, d, nn, stream=None, t_out=None, deg_out=None):
+        seen.append(int(s.numel()))
+        t_out.copy_(t_ref)
+        deg_out.copy_(deg_ref)
+        return 7, t_out, deg_out
+
+    tc = types.SimpleNamespace(tc_count_per_vertex=per_vertex)
+    s = torch.tensor([0, 1, 2], dtype=torch.int32)
+    d = torch.tensor([1, 2, 0], dtype=torch.int32)
+    r = bench.run_paper_format(4, tc, s, d, n, 3, 7, t_ref, deg_ref, None)
+    assert set(seen) == {6} and len(seen) == 3 + 4
+    assert r["pairs"] == 6 and r["edges"] == 3 and r["identical_to_main_run"] is True
+    assert abs(r["ms_per_step"] - 0.5) < 1e-9 and r["pairs_per_s"] == 6 / 0.0005
+    with np.testing.assert_raises(AssertionError):
+        bench.run_paper_format(1, tc, s, d, n, 3, 8, t_ref, deg_ref, None)  # T differs
