@@ -23,10 +23,15 @@ Functions mirror the C ABI names:
 
 ``src`` / ``dst`` are int32 CUDA tensors of the same length (pair i is the
 undirected edge {src[i], dst[i]}); ``n`` is the vertex count.
+
+Environment: ``TC_TUNING``, a JSON object of tc_tuning fields (for example
+``{"heavy_ratio_pct": 150}``), sets the process-wide tuning when the library
+is loaded; a value the library refuses raises TCError there.
 """
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 import threading
 
@@ -143,6 +148,7 @@ def _bind(lib):
 def load_library(path: str = LIB_PATH):
     """Load libtc.so (build it with ``python -m paper_1503_00576_gb300.build``)."""
     global _lib
+    fresh = False
     with _lock:
         if _lib is None:
             if not os.path.exists(path):
@@ -151,6 +157,9 @@ def load_library(path: str = LIB_PATH):
                     "`python -m paper_1503_00576_gb300.build` (nvcc, sm_103a). "
                     "There is no CPU fallback." % path)
             _lib = _bind(ctypes.CDLL(path))
+            fresh = True
+    if fresh and os.environ.get("TC_TUNING"):
+        tc_set_tuning(json.loads(os.environ["TC_TUNING"]))
     return _lib
 
 

@@ -73,3 +73,26 @@ def test_workspace_bytes_through_the_binding():
     assert tc.tc_workspace_bytes(0, 0) > 0
     assert tc.tc_workspace_bytes(10 ** 6, 10 ** 5) > 16 * 10 ** 6
     assert tc.tc_workspace_bytes(1 << 31, 5) == 0
+
+
+@pytest.mark.parametrize("spec,want", [('{"heavy_ratio_pct": 150, "warp_max_list": 64}', 0),
+                                       ('{"hub_vertices": 1000}', 1)])
+def test_tuning_from_the_environment(spec, want):
+    """TC_TUNING sets the process-wide tuning when the library loads; a
+    value the library refuses raises there."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import paper_1503_00576_gb300 as tc\n"
+            "try:\n"
+            "    tc.load_library()\n"
+            "except tc.TCError as e:\n"
+            "    raise SystemExit(e.code)\n"
+            "t = tc.tc_get_tuning()\n"
+            "assert t['heavy_ratio_pct'] == 150 and t['warp_max_list'] == 64, t\n"
+            "assert t['hub_vertices'] == tc.DEFAULT_TUNING['hub_vertices']\n")
+    env = dict(os.environ, TC_TUNING=spec)
+    rc = subprocess.run([sys.executable, "-c", code], cwd=root, env=env).returncode
+    assert rc == want
